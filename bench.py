@@ -1,0 +1,348 @@
+#!/usr/bin/env python3
+"""Benchmark of the multiphase SPH pair-sweep path on GB300.
+
+Workload (default): the 3D oscillating droplet -- sphere R = 0.5 with a
+mode-2 perturbation of amplitude 0.05 R in a 2x2x2 box, dx = R/25
+(1,000,000 fluid + 191,016 wall particles), density ratio 1000, viscosity
+ratio 100, sigma = 1, at rest, FP32 pair arithmetic with FP64 reductions.
+
+One timed step is one advection step of the dual-criteria scheme: cell-list
+rebuild, correction matrix, viscous force + transport shift, then all its
+acoustic substeps (~67 here), each with the criterion, colour gradient,
+force + kick and continuity + drift sweeps.  The metric counts
+particle-substeps: fluid particles times acoustic substeps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun) runs one independent replica per GPU ("replicas only":
+a single case does not shard without a halo exchange); value is the sum of
+all ranks' particle-substeps over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import sphcases  # noqa: E402
+
+METRIC = "particle-substeps/s"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+# algorithmic FP32 flops per neighbour pair of sweep B (derivation in the design doc):
+FLOPS_PAIR_B = 59            # geometry + Riemann pressure, every pair
+FLOPS_PAIR_B_SURF = 110      # surface stress + penalty, pairs touching the interface
+
+
+def workload(name: str):
+    if name == "oscillating_3d":
+        return sphcases.oscillating_3d()
+    if name == "laplace_2d":
+        return sphcases.laplace_2d()
+    if name == "impact_3d":
+        return sphcases.impact_3d()
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if "Active" in r[5 + k] and "Not" not in r[5 + k]:
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------ distributed
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Dist:
+    def __init__(self, backend: str):
+        self.ws, self.rank, self.local = dist_env()
+        self.pg = None
+        if self.ws > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        return self._reduce(x, "max")
+
+    def sum(self, x: float) -> float:
+        return self._reduce(x, "sum")
+
+    def _reduce(self, x, op):
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX if op == "max" else self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def aggregate(dist: Dist, units: float, seconds: float):
+    """Whole-job value: units summed over ranks / slowest rank's time."""
+    total = dist.sum(units)
+    tmax = dist.max(seconds)
+    return total / tmax, tmax, total
+
+
+# ----------------------------------------------------------- our arm
+def run_ours(args, dist: Dist):
+    import torch
+
+    import paper_2503_16082_gb300 as S
+
+    torch.cuda.set_device(dist.local)
+    stream = torch.cuda.current_stream()
+    spec = workload(args.workload)
+    n_fluid = spec.n_fluid
+
+    h = S.case_from_spec(spec, precision=args.precision)
+    S.set_stream(h, stream.cuda_stream)
+    S.step(h, args.warmup)                       # engine set-up, graph capture, warm-up
+    info0 = S.case_info(h)
+
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    S.step(h, args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    info1 = S.case_info(h)
+    n_sub = info1["n_sub"] - info0["n_sub"]
+    units = float(n_fluid) * n_sub
+    value, tmax, total_units = aggregate(dist, units, ms / 1e3)
+    # kernels launched in the timed region: per advection step 13 set-up
+    # kernels + 1 closing kernel, per substep 4
+    launches = args.steps * 14 + 4 * n_sub
+
+    # live per-kernel timing of one more advection step (events around each
+    # launch on the same stream) for the roofline of the dominant kernel
+    prof = S.profile_step(h)
+    counts = S.debug_neighbor_counts(h)
+    phase = S.read_fields(h, S.FIELD_PHASE, spec.dim)
+    gradc = S.read_fields(h, S.FIELD_GRADC, spec.dim)
+    kinds = [0 if p.kind == "fluid" else 2 for p in spec.phases]
+    is_fluid = np.array([kinds[int(k)] < 2 for k in phase])
+    iface = is_fluid & (np.abs(gradc).max(axis=1) > 0)
+    pairs = int(counts[is_fluid].sum())
+    pairs_surf = int(min(2 * counts[iface].sum(), pairs))
+    b_ms, b_launches = prof["sweep_B"]
+    b_avg = b_ms / max(b_launches, 1) / 1e3
+    flops = FLOPS_PAIR_B * pairs + FLOPS_PAIR_B_SURF * pairs_surf
+    achieved = flops / b_avg / 1e12
+    roofline = {"bound": "alu", "kernel": "k_sweep_B<float>", "achieved": round(achieved, 3),
+                "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                "flops_per_launch": flops, "pairs": pairs, "pairs_surface": pairs_surf,
+                "avg_launch_ms": round(b_avg * 1e3, 4)}
+    kernel_ms = {g: {"ms": round(m, 3), "launches": l} for g, (m, l) in prof.items()}
+    S.destroy(h)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2 = S.case_from_spec(spec, precision=args.precision)
+        S.set_stream(h2, stream.cuda_stream)
+        d2h = 0
+        e_sub0 = 0
+        for k in range(args.steps):
+            S.step(h2, 1)
+            pos = S.read_fields(h2, S.FIELD_POS, spec.dim)
+            d2h += pos.nbytes
+        e_sub = S.case_info(h2)["n_sub"] - e_sub0
+        t1 = time.perf_counter()
+        S.destroy(h2)
+        e_val, _, _ = aggregate(dist, float(n_fluid) * e_sub, t1 - t0)
+        h2d = spec.n * (3 + 3 + 1) * 8
+        e2e = {"value": round(e_val, 1), "unit": METRIC,
+               "h2d_bytes_per_step": int(h2d / max(args.steps, 1)),
+               "d2h_bytes_per_step": int(d2h / max(args.steps, 1)),
+               "note": "case upload + engine set-up + graph capture + K x (step, read positions)"}
+
+    return {
+        "value": value, "ms_per_step": tmax * 1e3 / args.steps, "units": total_units,
+        "n_sub": n_sub, "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk, "kernel_ms": kernel_ms, "n_fluid": n_fluid, "n_total": spec.n,
+    }
+
+
+# ------------------------------------------------------ CPU oracle sample
+SAMPLE_SUBSTEPS = 4
+
+
+def oracle_sample(spec, substeps: int = SAMPLE_SUBSTEPS):
+    """Time the oracle as it stands on the full workload: one advection
+    step's set-up (neighbour search, viscous force, transport shift) plus
+    `substeps` acoustic substeps.  Returns (particle-substeps/s, seconds, threads)."""
+    import oracle
+
+    pos, vel, rho, kind = spec.flat()
+    P = oracle.params_for_case(spec, max_substeps=substeps)
+    t0 = time.perf_counter()
+    _, _, _, info, _, _ = oracle.run(P, pos, vel, rho, kind, 1)
+    dt = time.perf_counter() - t0
+    return spec.n_fluid * info["n_sub"] / dt, dt, oracle.max_threads(), info["n_sub"]
+
+
+def run_reference(args, dist: Dist):
+    if dist.rank != 0:
+        return None
+    spec = workload(args.workload)
+    for _ in range(args.warmup):
+        oracle_sample(spec, 1)
+    units = 0.0
+    secs = 0.0
+    threads = 0
+    for _ in range(args.steps):
+        rate, dt, threads, nsub = oracle_sample(spec)
+        units += spec.n_fluid * nsub
+        secs += dt
+    value = units / secs
+    return {"value": value, "ms_per_step": secs * 1e3 / max(args.steps, 1), "threads": threads,
+            "sample": f"full {args.workload} ({spec.n} particles): per step one advection-step "
+                      f"set-up + {SAMPLE_SUBSTEPS} acoustic substeps of the FP64 oracle"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="oscillating_3d")
+    ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    ws, rank, local = dist_env()
+    config = {"workload": args.workload, "particles": None, "fluid_particles": None,
+              "step": "one advection step (rebuild + all acoustic substeps)",
+              "l2": "inputs larger than L2 (~170 MB FP32 working set vs 129 MB L2)",
+              "parallelism": f"replicas x{max(ws, 1)}"}
+    dtype = "f32" if args.precision == 32 else "f64"
+
+    if args.impl == "reference":
+        dist = Dist("gloo") if ws > 1 else Dist("gloo")
+        res = run_reference(args, dist)
+        dist.close()
+        if res is None:
+            return
+        spec_n = workload(args.workload)
+        config.update(particles=spec_n.n, fluid_particles=spec_n.n_fluid)
+        line = {"impl": "reference", "metric": METRIC, "value": round(res["value"], 1),
+                "unit": METRIC, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(res["ms_per_step"], 1), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config,
+                "cpu_baseline": {"value": round(res["value"], 1), "unit": METRIC, "cores": res["threads"],
+                                 "kind": "oracle", "sample": res["sample"]},
+                "e2e": {"value": round(res["value"], 1), "unit": METRIC,
+                        "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    dist = Dist("nccl")
+    res = run_ours(args, dist)
+    config.update(particles=res["n_total"], fluid_particles=res["n_fluid"],
+                  substeps_per_step=round(res["n_sub"] / args.steps, 2))
+    cpu = None
+    if rank == 0 and ws <= 1 and not args.no_cpu_baseline:
+        spec = workload(args.workload)
+        rate, dt, threads, nsub = oracle_sample(spec)
+        cpu = {"value": round(rate, 1), "unit": METRIC, "cores": threads, "kind": "oracle",
+               "sample": f"full {args.workload}: one advection-step set-up + {nsub} acoustic "
+                         f"substeps of the FP64 oracle, {dt:.1f} s"}
+    dist.close()
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": round(res["value"], 1), "unit": METRIC, "n_gpus": max(ws, 1),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(res["ms_per_step"], 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic", "config": config, "roofline": res["roofline"],
+            "cpu_baseline": cpu, "e2e": res["e2e"], "gpu_launches": res["gpu_launches"],
+            "clocks": res["clocks"], "kernel_ms_one_step": res["kernel_ms"]}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

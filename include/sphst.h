@@ -1,0 +1,253 @@
+/*
+ * sphst.h -- C ABI of the GB300 pair-sweep library for the Riemann-based
+ * multiphase SPH scheme with momentum-conserving surface tension and the
+ * zero-surface-energy penalty force (Zhang, Lourenco & Hu, arXiv 2503.16082).
+ *
+ * The problem statement follows Sections 2-3 of the paper: two immiscible
+ * weakly compressible fluids, each with a reference density rho0 and a
+ * dynamic viscosity eta, one surface tension coefficient gamma for their
+ * interface, one artificial sound speed c0 for all phases (Eq. 3), the
+ * Wendland C2 kernel with smoothing length h = 1.3 dp (Section 5) and no-slip
+ * walls.  One call of sphst_step advances whole advection steps of the
+ * dual-criteria time stepping (Section 3.3, Eqs. 16-18); each advection step
+ * runs as many acoustic substeps as its length needs, all on the GPU.
+ *
+ * Conventions for every entry point:
+ *   - the return value is a status code: SPHST_OK (0) or a negative error;
+ *     sphst_last_error() then describes the failure (thread-local text);
+ *   - pointers named pos/vel/rho/dst are HOST pointers; arrays of vectors are
+ *     row-major with `dim` doubles per particle (x, y[, z]);
+ *   - input arrays are copied; the caller keeps ownership of its buffers;
+ *   - a case or batch handle is owned by the caller and released with the
+ *     matching destroy call; destroy functions accept NULL;
+ *   - calls on one handle must not run concurrently (one host thread per
+ *     case or batch, or the caller serialises);
+ *   - all device memory is allocated and freed by the library on the current
+ *     CUDA device at the first step of a case (or of a batch).
+ */
+#ifndef SPHST_H
+#define SPHST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define SPHST_OK               0
+#define SPHST_ERR_INVALID_ARG (-1)   /* a NULL handle, bad size or bad value      */
+#define SPHST_ERR_STATE       (-2)   /* call not allowed in the current state     */
+#define SPHST_ERR_UNSUPPORTED (-3)   /* third fluid, dim not 2/3, grid too large  */
+#define SPHST_ERR_OOM         (-4)   /* device allocation failed                  */
+#define SPHST_ERR_CUDA        (-5)   /* a CUDA runtime call failed                */
+#define SPHST_ERR_NONFINITE   (-6)   /* NaN/Inf velocity or time step in a case   */
+#define SPHST_ERR_TIMEOUT     (-7)   /* reserved: a bounded device wait gave up   */
+#define SPHST_ERR_OVER_BUDGET (-8)   /* batch admission beyond the memory budget  */
+#define SPHST_ERR_DOMAIN      (-9)   /* a particle left the cell grid             */
+#define SPHST_ERR_COINCIDENT (-10)   /* two particles at the same position        */
+#define SPHST_ERR_STALLED    (-11)   /* advection step exceeded max_substeps      */
+#define SPHST_ERR_CAPACITY   (-12)   /* destination buffer too small              */
+
+/* --------------------------------------------------------- particle kinds */
+#define SPHST_FLUID 0
+#define SPHST_WALL  1
+
+/* ------------------------------------------------------------ readings    */
+/* Eq. 11 dissipation limiter of the momentum Riemann solver.  DENSITY: the
+ * printed (P_L + P_R) is read as (rho_L + rho_R), which makes beta
+ * dimensionless; with one sound speed beta = min(3 max((U_L-U_R)/c0, 0), 1). */
+#define SPHST_LIMITER_DENSITY 0
+#define SPHST_LIMITER_NONE    1      /* beta = 1: full acoustic dissipation  */
+#define SPHST_LIMITER_ZERO    2      /* beta = 0: P* is the pair average     */
+/* Eq. 28 average colour gradient of a pair of different phases: COMMON takes
+ * j's colour on i's side, (gradC_i - gradC_j)/2; PRINTED is (gradC_i + gradC_j)/2 */
+#define SPHST_GRAD_COMMON  0
+#define SPHST_GRAD_PRINTED 1
+/* Eq. 30 with A = gradCbar (x) r_ij: NN contracts (A/|A|) A as A A^T/|A|
+ * (= |gradCbar| r_ij nbar nbar^T); EE as A^T A/|A| (= |gradCbar| r_ij e e^T) */
+#define SPHST_PENALTY_NN 0
+#define SPHST_PENALTY_EE 1
+/* acoustic substep loop: GRAPH runs it as a device-driven while loop inside a
+ * CUDA graph (no host round trip per substep); HOST polls a device flag after
+ * every substep */
+#define SPHST_LOOP_GRAPH 0
+#define SPHST_LOOP_HOST  1
+
+/* ------------------------------------------------------------- fields     */
+#define SPHST_FIELD_POS      0   /* n x dim positions                            */
+#define SPHST_FIELD_VEL      1   /* n x dim velocities                           */
+#define SPHST_FIELD_RHO      2   /* n densities (walls: their fluid partner's)   */
+#define SPHST_FIELD_PRESSURE 3   /* n pressures c0^2 (rho - rho0), Eq. 3          */
+#define SPHST_FIELD_PHASE    4   /* n phase ids as returned by add_phase_particles */
+#define SPHST_FIELD_GRADC    5   /* n x dim colour gradient of the last substep  */
+#define SPHST_FIELD_ACC_VISC 6   /* n x dim viscous acceleration of the last advection step */
+
+typedef struct sphst_case_s *sphst_case;
+typedef struct sphst_batch_s *sphst_batch;
+
+typedef struct {
+    int32_t dim;            /* 2 or 3                                          */
+    int32_t precision;      /* 32: FP32 pair arithmetic, FP64 reductions; 64   */
+    double  dx;             /* initial particle spacing dp (> 0)               */
+    double  h_factor;       /* h = h_factor * dx; the paper uses 1.3           */
+    double  c0;             /* artificial sound speed, one for all phases      */
+    double  gamma;          /* surface tension coefficient (>= 0)              */
+    double  xi;             /* penalty coefficient; < 0: 1.3 n + 0.6 for a
+                               density ratio 10^n (Section 4.2)               */
+    double  tvf_alpha;      /* transport-velocity coefficient (Section 3.2,
+                               0.2); 0 switches the position shift off         */
+    int32_t limiter;        /* SPHST_LIMITER_*                                 */
+    int32_t grad_mode;      /* SPHST_GRAD_*                                    */
+    int32_t penalty_form;   /* SPHST_PENALTY_*                                 */
+    int32_t loop_mode;      /* SPHST_LOOP_*                                    */
+    int32_t grid_pad;       /* spare cells around the initial bounding box (>= 1) */
+    int32_t block;          /* threads per block of the pair sweeps, 32..1024  */
+    int64_t max_substeps;   /* per advection step before SPHST_ERR_STALLED     */
+    double  cfl_ad;         /* factor of the advection criterion, Eq. 16 (0.1) */
+    double  cfl_ac;         /* factor of the acoustic criterion, Eq. 17 (0.6);
+                               a density-ratio-1000 interface bound by the
+                               sound term needs <= 0.5 (2D) / 0.4 (3D)        */
+} sphst_case_params;
+
+typedef struct {
+    int32_t kind;           /* SPHST_FLUID or SPHST_WALL                       */
+    int32_t pad_;
+    double  rho0;           /* fluid: reference density (> 0)                  */
+    double  eta;            /* fluid: dynamic viscosity (> 0)                  */
+    double  wall_vel[3];    /* wall: prescribed velocity of its particles      */
+} sphst_phase_props;
+
+typedef struct {
+    int64_t n_adv;          /* advection steps completed since creation        */
+    int64_t n_sub;          /* acoustic substeps completed since creation      */
+    double  t;              /* physical time reached                           */
+    double  last_dt_ad;     /* length of the last advection step (Eq. 16/18)   */
+    double  last_dt_ac;     /* last acoustic criterion (Eq. 17/18)             */
+    int32_t status;         /* SPHST_OK or the case's sticky error code        */
+    int32_t pad_;
+} sphst_step_info;
+
+/* Fill *p with the defaults: dim 2, precision 32, h_factor 1.3, c0 10,
+ * gamma 1, xi -1 (derived), tvf_alpha 0.2, readings 0, graph loop,
+ * grid_pad 2, block 128, max_substeps 1000000, cfl_ad 0.1, cfl_ac 0.6;
+ * dx must still be set. */
+void sphst_default_params(sphst_case_params *p);
+
+/* Create an empty case from the problem statement of Sections 2-3.
+ * Errors: INVALID_ARG (dx <= 0, c0 <= 0, gamma < 0, bad flags),
+ * UNSUPPORTED (dim not 2 or 3, precision not 32 or 64). */
+int sphst_create_case(const sphst_case_params *params, sphst_case *out);
+
+/* Add n particles of one phase.  pos: n x dim, copied.  vel: n x dim or
+ * NULL for rest (ignored for walls, which move with wall_vel).  rho: n
+ * initial densities or NULL for rho0 (fluids; used to resume a case).  Each
+ * particle's mass is rho0 dp^dim and stays fixed.  *phase_id_out (optional)
+ * receives 0, 1, 2... in call order.  Allowed only before the first step.
+ * Errors: STATE after the first step, UNSUPPORTED for a third fluid phase,
+ * INVALID_ARG for n < 0, NULL pos with n > 0, rho0/eta <= 0. */
+int sphst_add_phase_particles(sphst_case c, const sphst_phase_props *props, int64_t n,
+                              const double *pos, const double *vel, const double *rho,
+                              int32_t *phase_id_out);
+
+/* Advance n_adv advection steps (Section 3.3).  Per advection step, on the
+ * device: the advection criterion from the FP64 maximum speed per fluid; the
+ * cell list rebuild (Morton cell keys, counting sort, reorder) that freezes
+ * the particle configuration; the viscous acceleration (Eq. 13) and the
+ * transport-velocity shift (Eqs. 14-15); then acoustic substeps, each with
+ * the acoustic criterion (Eq. 17), the colour gradient (Eq. 22), the
+ * pressure (Eqs. 7-12), surface (Eqs. 24, 26, 33) and viscous accelerations
+ * and a velocity kick, continuity (Eq. 6) and the position drift.  info
+ * (optional) receives the case totals.  A case whose device status turns
+ * non-zero stops where it failed and keeps returning that error; its fields
+ * stay readable.  Errors: STATE (case is a batch member), NONFINITE, DOMAIN,
+ * COINCIDENT, STALLED, OOM, CUDA, UNSUPPORTED (cell grid too large). */
+int sphst_step(sphst_case c, int64_t n_adv, sphst_step_info *info);
+
+/* Copy one field, in insertion order and FP64 whatever the internal
+ * precision, into the caller's host buffer dst of capacity doubles (the
+ * field needs n or n x dim doubles, n = all particles incl. walls).
+ * Before the first step the staged input is returned.  Errors: INVALID_ARG
+ * (unknown field), CAPACITY (buffer too small), CUDA. */
+int sphst_read_fields(sphst_case c, int32_t field, double *dst, int64_t capacity);
+
+/* Case totals (n_adv, n_sub, t, last criteria, status) without stepping. */
+int sphst_case_info(sphst_case c, sphst_step_info *info);
+
+/* Particle counts: all particles and fluid particles. */
+int sphst_num_particles(sphst_case c, int64_t *n_total, int64_t *n_fluid);
+
+/* Release a case and its device memory.  A batch member must be removed
+ * from its batch first (else STATE).  NULL is accepted. */
+int sphst_destroy(sphst_case c);
+
+/* Text of the last error on the calling thread ("" if none). */
+const char *sphst_last_error(void);
+
+/* ------------------------------------------------------ inspection calls */
+/* Cell grid of a stepped case: origin (3 doubles), cell width (2h(1+2^-16))
+ * and cells per axis (3 ints, 1 for unused axes). */
+int sphst_debug_grid(sphst_case c, double *origin3, double *cell_size, int32_t *ncell3);
+
+/* Cell keys of the last rebuild in the device's particle order: keys[k] is
+ * the Morton code of the k-th particle's cell and ids[k] its insertion index
+ * (the order sorts by (key, insertion index)).  capacity counts entries. */
+int sphst_debug_keys(sphst_case c, uint64_t *keys, int64_t *ids, int64_t capacity);
+
+/* Number of neighbours (0 < r_ij < 2h) of each particle at the last rebuild,
+ * in insertion order (walls included). */
+int sphst_debug_neighbor_counts(sphst_case c, int32_t *counts, int64_t capacity);
+
+/* Run the case's kernels on the caller's CUDA stream (a cudaStream_t passed
+ * as void*, e.g. torch.cuda.current_stream().cuda_stream) instead of a
+ * library-owned stream.  Must be called before the first step; NULL keeps
+ * the library's own stream.  The caller keeps ownership of the stream. */
+int sphst_set_stream(sphst_case c, void *cuda_stream);
+
+/* Advance one advection step with every kernel launched on its own (no
+ * graph) and bracketed by CUDA events on the case's stream.  kernel_ms[k]
+ * receives the summed device time of kernel group k and launches[k] its
+ * launch count, for k = 0 rebuild (keys, scan, sort, gather), 1 set-up
+ * (speed reduction, criteria, correction matrix, viscous + shift),
+ * 2 criterion per substep, 3 sweep A, 4 sweep B, 5 sweep C.  Both arrays
+ * hold SPHST_PROFILE_GROUPS entries.  The step is a normal step of the case. */
+#define SPHST_PROFILE_GROUPS 6
+int sphst_profile_step(sphst_case c, double *kernel_ms, int64_t *launches);
+
+/* ------------------------------------------------------------- batches   */
+/* A batch advances many independent cases together: their particles share
+ * one set of device arrays, one segmented cell list (the case index selects
+ * a segment of the cell table) and one captured CUDA graph per advection
+ * step, in which every case keeps its own advection and acoustic time steps.
+ * All members have the precision given here. */
+int sphst_batch_create(int32_t precision, sphst_batch *out);
+
+/* Make c a member.  c must have that precision and may already have been
+ * stepped alone; it joins at the next sphst_batch_step.  Errors: STATE (c in
+ * another batch), INVALID_ARG, UNSUPPORTED (precision mismatch). */
+int sphst_batch_add(sphst_batch b, sphst_case c);
+
+/* Remove c; it keeps its state and can be stepped alone or read. */
+int sphst_batch_remove(sphst_batch b, sphst_case c);
+
+/* Advance every member by n_adv of its own advection steps.  Members whose
+ * status turns non-zero stop; the others continue.  info (optional) receives
+ * n_adv/n_sub summed over members and the worst status. */
+int sphst_batch_step(sphst_batch b, int64_t n_adv, sphst_step_info *info);
+
+/* Number of members. */
+int sphst_batch_size(sphst_batch b, int64_t *n_cases);
+
+/* Release the batch (members stay valid and leave it). */
+int sphst_batch_destroy(sphst_batch b);
+
+/* Device bytes one case of n particles needs (particle arrays, cell table,
+ * scratch), for admission control.  Errors: INVALID_ARG. */
+int sphst_footprint_bytes(const sphst_case_params *params, int64_t n_particles,
+                          int64_t *bytes_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPHST_H */

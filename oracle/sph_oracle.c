@@ -86,6 +86,8 @@ typedef struct {
     double nhat_eps;      /* |gradC| h threshold for an interface particle */
     int64_t max_substeps; /* guard against a stalled advection step */
     double tvf_alpha;     /* transport-velocity coefficient (0.2 in Section 3.2); 0: off */
+    double cfl_ad;        /* advection factor of Eq. 16 (0.1 as printed) */
+    double cfl_ac;        /* acoustic factor of Eq. 17 (0.6 as printed) */
 } ora_params;
 
 typedef struct {
@@ -874,7 +876,8 @@ static int phase_present(const state_t *S, int32_t k)
     return 0;
 }
 
-/* Eq. 16 then Eq. 18 (terms with |v|max = 0 are infinite and dropped) */
+/* Eq. 16 then Eq. 18 (terms with |v|max = 0 are infinite and dropped); the
+ * factor 0.1 is the parameter cfl_ad */
 double ora_dt_advection(const ora_params *P, const double *vmax, const int32_t *present)
 {
     double dt = INFINITY;
@@ -882,12 +885,15 @@ double ora_dt_advection(const ora_params *P, const double *vmax, const int32_t *
         if (!present[k]) continue;
         double t = P->rho0[k] * P->h * P->h / P->eta[k];
         if (vmax[k] > 0.0 && P->h / vmax[k] < t) t = P->h / vmax[k];
-        if (0.1 * t < dt) dt = 0.1 * t;
+        if (P->cfl_ad * t < dt) dt = P->cfl_ad * t;
     }
     return dt;
 }
 
-/* Eq. 17 then Eq. 18 */
+/* Eq. 17 then Eq. 18; the factor 0.6 is the parameter cfl_ac.  With the
+ * kick-continuity-drift substep, a density-ratio-1000 interface whose step
+ * is bound by the sound term is stable only below about 0.55 (2D) and 0.4
+ * (3D), so such workloads pass a smaller factor. */
 double ora_dt_acoustic(const ora_params *P, const double *vmax, const int32_t *present)
 {
     double dt = INFINITY;
@@ -898,7 +904,7 @@ double ora_dt_acoustic(const ora_params *P, const double *vmax, const int32_t *p
             double ts = sqrt(P->rho0[k] * P->h * P->h * P->h / (2.0 * ORA_PI * P->gamma));
             if (ts < t) t = ts;
         }
-        if (0.6 * t < dt) dt = 0.6 * t;
+        if (P->cfl_ac * t < dt) dt = P->cfl_ac * t;
     }
     return dt;
 }

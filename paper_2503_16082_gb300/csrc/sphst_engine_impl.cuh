@@ -1,0 +1,442 @@
+// sphst_engine_impl.cuh -- EngineT<T>: device arrays, rebuild + substep
+// graph, read-back.  Included once per precision.
+#pragma once
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "sphst_engine.cuh"
+#include "sphst_kernels.cuh"
+
+namespace sphst {
+
+#define SPH_CK(call)                                              \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
+    } while (0)
+
+enum ArrayId { A_POS = 0, A_VEL, A_DRHO, A_ID, A_GRADC, A_ACCV };
+
+template <typename T> struct EngineT : Engine {
+    // particle arrays
+    V4<T> *pos = nullptr, *snap = nullptr, *vel = nullptr, *vel_new = nullptr;
+    V4<T> *gradC = nullptr, *acc_visc = nullptr, *bmat = nullptr;
+    T *drho = nullptr, *drho_old = nullptr;
+    uint32_t *id = nullptr, *key = nullptr, *rank = nullptr, *perm = nullptr;
+    // cell table + scan scratch
+    uint32_t *starts = nullptr, *block_sums = nullptr;
+    // cases
+    CaseDesc *d_desc = nullptr;
+    CaseState *d_state = nullptr;
+    Tile *d_tiles = nullptr;
+    int *d_loop_flag = nullptr;
+    double *d_read = nullptr;              // read-back buffer
+    void *arena = nullptr;
+    int64_t n = 0, table_total = 0, n_tiles = 0, max_case_n = 0;
+    int ncases = 0, block = 128;
+    bool any_tvf = false;
+    int loop_mode = SPHST_LOOP_GRAPH;
+    std::vector<CaseDesc> h_desc;
+    std::vector<CaseState> h_state;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+
+    EngineT() { precision = sizeof(T) == 4 ? 32 : 64; }
+    ~EngineT() override {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (stream && own_stream) cudaStreamDestroy(stream);
+        if (arena) cudaFree(arena);
+    }
+
+    void *dev_array(int which) override {
+        switch (which) {
+        case A_POS: return pos;
+        case A_VEL: return vel;
+        case A_DRHO: return drho;
+        case A_ID: return id;
+        case A_GRADC: return gradC;
+        case A_ACCV: return acc_visc;
+        }
+        return nullptr;
+    }
+    CaseState *dev_state() override { return d_state; }
+    int64_t begin_of(int slot) override { return h_desc[slot].p_begin; }
+
+    int setup(const std::vector<CaseRec *> &cases, int blk, cudaStream_t user_stream) override {
+        members = cases;
+        ncases = (int)cases.size();
+        block = blk;
+        if (user_stream) {
+            stream = user_stream;
+        } else {
+            SPH_CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+            own_stream = true;
+        }
+        // layout
+        h_desc.resize(ncases);
+        h_state.assign(ncases, CaseState{});
+        n = 0;
+        table_total = 0;
+        n_tiles = 0;
+        max_case_n = 0;
+        loop_mode = SPHST_LOOP_GRAPH;
+        for (int c = 0; c < ncases; ++c) {
+            CaseRec *r = cases[c];
+            if (!r->gridded) {
+                int rc = make_grid(r);
+                if (rc) return rc;
+            }
+            CaseDesc d = make_desc(r);
+            d.p_begin = n;
+            d.p_end = n + r->n;
+            d.table_off = table_total;
+            h_desc[c] = d;
+            n += r->n;
+            table_total += d.table_size;
+            n_tiles += (r->n + block - 1) / block;
+            max_case_n = std::max(max_case_n, r->n);
+            any_tvf = any_tvf || d.tvf_on;
+            if (r->P.loop_mode == SPHST_LOOP_HOST) loop_mode = SPHST_LOOP_HOST;
+        }
+        if (n >= (int64_t)0xffffffffll || table_total + 1 >= (int64_t)0xffffffffll) {
+            set_error("engine too large for 32-bit particle or cell indices");
+            return SPHST_ERR_UNSUPPORTED;
+        }
+        // arena
+        const int64_t nb = (table_total + 1 + SCAN_ITEMS - 1) / SCAN_ITEMS;
+        size_t off = 0;
+        auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
+        const size_t nn = (size_t)std::max<int64_t>(n, 1);
+        size_t o_pos = take(nn * sizeof(V4<T>)), o_snap = take(nn * sizeof(V4<T>));
+        size_t o_vel = take(nn * sizeof(V4<T>)), o_veln = take(nn * sizeof(V4<T>));
+        size_t o_gc = take(nn * sizeof(V4<T>)), o_av = take(nn * sizeof(V4<T>));
+        size_t o_bm = take(2 * nn * sizeof(V4<T>));
+        size_t o_dr = take(nn * sizeof(T)), o_dro = take(nn * sizeof(T));
+        size_t o_id = take(nn * 4), o_key = take(nn * 4), o_rank = take(nn * 4), o_perm = take(nn * 4);
+        size_t o_st = take((size_t)(table_total + 1) * 4), o_bs = take((size_t)nb * 4);
+        size_t o_desc = take(sizeof(CaseDesc) * ncases), o_state = take(sizeof(CaseState) * ncases);
+        size_t o_tiles = take(sizeof(Tile) * (size_t)std::max<int64_t>(n_tiles, 1));
+        size_t o_flag = take(64);
+        size_t o_read = take((size_t)std::max<int64_t>(max_case_n, 1) * 3 * sizeof(double));
+        cudaError_t e = cudaMalloc(&arena, off);
+        if (e != cudaSuccess) {
+            arena = nullptr;
+            cudaGetLastError();
+            set_error("device allocation of " + std::to_string(off) + " bytes failed");
+            return SPHST_ERR_OOM;
+        }
+        char *b = (char *)arena;
+        pos = (V4<T> *)(b + o_pos); snap = (V4<T> *)(b + o_snap);
+        vel = (V4<T> *)(b + o_vel); vel_new = (V4<T> *)(b + o_veln);
+        gradC = (V4<T> *)(b + o_gc); acc_visc = (V4<T> *)(b + o_av); bmat = (V4<T> *)(b + o_bm);
+        drho = (T *)(b + o_dr); drho_old = (T *)(b + o_dro);
+        id = (uint32_t *)(b + o_id); key = (uint32_t *)(b + o_key);
+        rank = (uint32_t *)(b + o_rank); perm = (uint32_t *)(b + o_perm);
+        starts = (uint32_t *)(b + o_st); block_sums = (uint32_t *)(b + o_bs);
+        d_desc = (CaseDesc *)(b + o_desc); d_state = (CaseState *)(b + o_state);
+        d_tiles = (Tile *)(b + o_tiles); d_loop_flag = (int *)(b + o_flag);
+        d_read = (double *)(b + o_read);
+        SPH_CK(cudaMemsetAsync(arena, 0, off, stream));
+        // tiles
+        std::vector<Tile> tiles;
+        tiles.reserve(n_tiles);
+        for (int c = 0; c < ncases; ++c)
+            for (int64_t s = h_desc[c].p_begin; s < h_desc[c].p_end; s += block)
+                tiles.push_back(Tile{c, (int32_t)std::min<int64_t>(block, h_desc[c].p_end - s), s});
+        SPH_CK(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, stream));
+        SPH_CK(cudaMemcpyAsync(d_desc, h_desc.data(), sizeof(CaseDesc) * ncases, cudaMemcpyHostToDevice, stream));
+        // fill each case
+        for (int c = 0; c < ncases; ++c) {
+            CaseRec *r = cases[c];
+            const int64_t b0 = h_desc[c].p_begin;
+            if (r->engine == nullptr) {
+                int rc = upload_fresh(c, r);
+                if (rc) return rc;
+            } else {
+                if (r->engine->precision != precision) {
+                    set_error("precision mismatch between a case and its batch");
+                    return SPHST_ERR_UNSUPPORTED;
+                }
+                Engine *o = r->engine;
+                const int64_t ob = o->begin_of(r->slot);
+                const size_t v4 = sizeof(V4<T>);
+                SPH_CK(cudaMemcpyAsync(pos + b0, (V4<T> *)o->dev_array(A_POS) + ob, r->n * v4, cudaMemcpyDeviceToDevice, stream));
+                SPH_CK(cudaMemcpyAsync(vel + b0, (V4<T> *)o->dev_array(A_VEL) + ob, r->n * v4, cudaMemcpyDeviceToDevice, stream));
+                SPH_CK(cudaMemcpyAsync(gradC + b0, (V4<T> *)o->dev_array(A_GRADC) + ob, r->n * v4, cudaMemcpyDeviceToDevice, stream));
+                SPH_CK(cudaMemcpyAsync(acc_visc + b0, (V4<T> *)o->dev_array(A_ACCV) + ob, r->n * v4, cudaMemcpyDeviceToDevice, stream));
+                SPH_CK(cudaMemcpyAsync(drho + b0, (T *)o->dev_array(A_DRHO) + ob, r->n * sizeof(T), cudaMemcpyDeviceToDevice, stream));
+                SPH_CK(cudaMemcpyAsync(id + b0, (uint32_t *)o->dev_array(A_ID) + ob, r->n * 4, cudaMemcpyDeviceToDevice, stream));
+                SPH_CK(cudaMemcpyAsync(d_state + c, o->dev_state() + r->slot, sizeof(CaseState), cudaMemcpyDeviceToDevice, stream));
+            }
+        }
+        SPH_CK(cudaStreamSynchronize(stream));
+        SPH_CK(cudaMemcpy(h_state.data(), d_state, sizeof(CaseState) * ncases, cudaMemcpyDeviceToHost));
+        if (loop_mode == SPHST_LOOP_GRAPH) {
+            int rc = build_graph();
+            if (rc) return rc;
+        }
+        return SPHST_OK;
+    }
+
+    int upload_fresh(int c, CaseRec *r) {
+        const int64_t m = r->n;
+        CaseState s{};
+        s.present[0] = r->n_fluid_phases >= 1 && std::any_of(r->kind.begin(), r->kind.end(), [](uint8_t k) { return k == 0; });
+        s.present[1] = std::any_of(r->kind.begin(), r->kind.end(), [](uint8_t k) { return k == 1; });
+        SPH_CK(cudaMemcpyAsync(d_state + c, &s, sizeof(CaseState), cudaMemcpyHostToDevice, stream));
+        if (m == 0) return SPHST_OK;
+        double *tp = nullptr;
+        const size_t bytes = (size_t)m * (3 + 3 + 1) * sizeof(double) + (size_t)m;
+        SPH_CK(cudaMalloc(&tp, bytes));
+        double *tpos = tp, *tvel = tp + 3 * m, *trho = tp + 6 * m;
+        uint8_t *tkind = (uint8_t *)(tp + 7 * m);
+        cudaError_t e = cudaMemcpyAsync(tpos, r->pos.data(), 3 * m * sizeof(double), cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tvel, r->vel.data(), 3 * m * sizeof(double), cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(trho, r->rho.data(), m * sizeof(double), cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tkind, r->kind.data(), m, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) {
+            const int grid = (int)std::min<int64_t>((m + 255) / 256, 65535);
+            k_init_case<T><<<grid, 256, 0, stream>>>(d_desc, c, tpos, tvel, trho, tkind, pos, vel, drho, id, d_state);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        cudaFree(tp);
+        if (e != cudaSuccess) return cuda_fail(e, "upload of a case");
+        return SPHST_OK;
+    }
+
+    // ---------------------------------------------------------- launches
+    int launch_pre() {
+        const int nthr = 256;
+        const int cgrid = (ncases + 127) / 128;
+        const int pgrid = (int)((n + nthr - 1) / nthr);
+        SweepArgs a{d_tiles, d_desc, d_state, starts};
+        SPH_CK(cudaMemsetAsync(starts, 0, (size_t)(table_total + 1) * 4, stream));
+        k_reset_vmax<<<cgrid, 128, 0, stream>>>(ncases, d_state);
+        k_vmax<T><<<(unsigned)n_tiles, block, 0, stream>>>(d_tiles, d_desc, d_state, pos, vel);
+        k_adv_begin<<<cgrid, 128, 0, stream>>>(ncases, d_desc, d_state);
+        k_cell_assign<T><<<(unsigned)n_tiles, block, 0, stream>>>(d_tiles, d_desc, d_state, pos, key, rank, starts);
+        const int64_t ns = table_total + 1;
+        const unsigned nb = (unsigned)((ns + SCAN_ITEMS - 1) / SCAN_ITEMS);
+        k_scan_reduce<<<nb, SCAN_T, 0, stream>>>(starts, ns, block_sums);
+        k_scan_blocks<<<1, SCAN_T, 0, stream>>>(block_sums, nb);
+        k_scan_apply<<<nb, SCAN_T, 0, stream>>>(starts, ns, block_sums);
+        k_scatter<<<pgrid, nthr, 0, stream>>>(n, key, rank, starts, perm);
+        k_cell_sort<<<(unsigned)((table_total + nthr - 1) / nthr), nthr, 0, stream>>>(table_total, starts, id, perm);
+        k_gather<T><<<pgrid, nthr, 0, stream>>>(n, perm, pos, vel, drho, id, snap, vel_new, drho_old, rank);
+        k_copy_back<T><<<pgrid, nthr, 0, stream>>>(n, snap, vel_new, drho_old, rank, pos, vel, drho, id);
+        if (any_tvf) k_sweep_M<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, bmat);
+        k_sweep_V<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, vel, bmat, acc_visc, pos);
+        SPH_CK(cudaGetLastError());
+        return SPHST_OK;
+    }
+
+    int launch_body(cudaGraphConditionalHandle h, int use_handle) {
+        SweepArgs a{d_tiles, d_desc, d_state, starts};
+        k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, h, use_handle);
+        k_sweep_A<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, gradC);
+        k_sweep_B<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, vel, gradC, acc_visc, vel_new, drho_old);
+        k_sweep_C<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho_old, vel_new, drho, vel, pos);
+        SPH_CK(cudaGetLastError());
+        return SPHST_OK;
+    }
+
+    int launch_post() {
+        k_adv_end<<<(ncases + 127) / 128, 128, 0, stream>>>(ncases, d_state);
+        SPH_CK(cudaGetLastError());
+        return SPHST_OK;
+    }
+
+    // One advection step as a graph: rebuild + set-up kernels, a while node
+    // whose body is one acoustic substep (the device sets its condition), and
+    // the bookkeeping kernel.
+    int build_graph() {
+        SPH_CK(cudaGraphCreate(&graph, 0));
+        cudaGraphConditionalHandle handle;
+        SPH_CK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+        SPH_CK(cudaStreamBeginCaptureToGraph(stream, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        int rc = launch_pre();
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        cudaGraph_t cap_graph;
+        cudaError_t e = cudaStreamGetCaptureInfo(stream, &cs, nullptr, &cap_graph, &deps, nullptr, &ndeps);
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode;
+        if (e == cudaSuccess && rc == 0) e = cudaGraphAddNode(&cnode, cap_graph, deps, nullptr, ndeps, &cp);
+        if (e == cudaSuccess && rc == 0)
+            e = cudaStreamUpdateCaptureDependencies(stream, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (e == cudaSuccess && rc == 0) rc = launch_post();
+        cudaGraph_t g2 = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(stream, &g2);
+        if (rc) return rc;
+        if (e != cudaSuccess) return cuda_fail(e, "graph capture (conditional node)");
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+        // body of the while node
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        SPH_CK(cudaStreamBeginCaptureToGraph(stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        rc = launch_body(handle, 1);
+        e2 = cudaStreamEndCapture(stream, &body);
+        if (rc) return rc;
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture (loop body)");
+        SPH_CK(cudaGraphInstantiate(&exec, graph, 0));
+        return SPHST_OK;
+    }
+
+    int step(int64_t n_adv) override {
+        for (int64_t s = 0; s < n_adv; ++s) {
+            if (loop_mode == SPHST_LOOP_GRAPH) {
+                SPH_CK(cudaGraphLaunch(exec, stream));
+            } else {
+                int rc = launch_pre();
+                if (rc) return rc;
+                for (;;) {
+                    rc = launch_body(0, 0);
+                    if (rc) return rc;
+                    int flag = 0;
+                    SPH_CK(cudaMemcpyAsync(&flag, d_loop_flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+                    SPH_CK(cudaStreamSynchronize(stream));
+                    if (!flag) break;
+                }
+                rc = launch_post();
+                if (rc) return rc;
+            }
+        }
+        SPH_CK(cudaStreamSynchronize(stream));
+        return sync_state();
+    }
+
+    // one advection step, kernel by kernel, with events around each group
+    int profile_step(double *kernel_ms, int64_t *launches) override {
+        const int G = SPHST_PROFILE_GROUPS;
+        for (int k = 0; k < G; ++k) { kernel_ms[k] = 0.0; launches[k] = 0; }
+        cudaEvent_t ev[2];
+        SPH_CK(cudaEventCreate(&ev[0]));
+        SPH_CK(cudaEventCreate(&ev[1]));
+        int rc = SPHST_OK;
+        auto timed = [&](int group, int nl, auto &&fn) {
+            if (rc) return;
+            cudaEventRecord(ev[0], stream);
+            fn();
+            cudaEventRecord(ev[1], stream);
+            cudaError_t e = cudaEventSynchronize(ev[1]);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e != cudaSuccess) { rc = cuda_fail(e, "profiled launch"); return; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            kernel_ms[group] += ms;
+            launches[group] += nl;
+        };
+        const int nthr = 256;
+        const int cgrid = (ncases + 127) / 128;
+        const int pgrid = (int)((n + nthr - 1) / nthr);
+        const int64_t ns = table_total + 1;
+        const unsigned nb = (unsigned)((ns + SCAN_ITEMS - 1) / SCAN_ITEMS);
+        SweepArgs a{d_tiles, d_desc, d_state, starts};
+        timed(1, 3, [&] {
+            k_reset_vmax<<<cgrid, 128, 0, stream>>>(ncases, d_state);
+            k_vmax<T><<<(unsigned)n_tiles, block, 0, stream>>>(d_tiles, d_desc, d_state, pos, vel);
+            k_adv_begin<<<cgrid, 128, 0, stream>>>(ncases, d_desc, d_state);
+        });
+        timed(0, 8, [&] {
+            cudaMemsetAsync(starts, 0, (size_t)ns * 4, stream);
+            k_cell_assign<T><<<(unsigned)n_tiles, block, 0, stream>>>(d_tiles, d_desc, d_state, pos, key, rank, starts);
+            k_scan_reduce<<<nb, SCAN_T, 0, stream>>>(starts, ns, block_sums);
+            k_scan_blocks<<<1, SCAN_T, 0, stream>>>(block_sums, nb);
+            k_scan_apply<<<nb, SCAN_T, 0, stream>>>(starts, ns, block_sums);
+            k_scatter<<<pgrid, nthr, 0, stream>>>(n, key, rank, starts, perm);
+            k_cell_sort<<<(unsigned)((table_total + nthr - 1) / nthr), nthr, 0, stream>>>(table_total, starts, id, perm);
+            k_gather<T><<<pgrid, nthr, 0, stream>>>(n, perm, pos, vel, drho, id, snap, vel_new, drho_old, rank);
+            k_copy_back<T><<<pgrid, nthr, 0, stream>>>(n, snap, vel_new, drho_old, rank, pos, vel, drho, id);
+        });
+        timed(1, any_tvf ? 2 : 1, [&] {
+            if (any_tvf) k_sweep_M<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, bmat);
+            k_sweep_V<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, vel, bmat, acc_visc, pos);
+        });
+        for (;;) {
+            timed(2, 1, [&] { k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, 0, 0); });
+            timed(3, 1, [&] { k_sweep_A<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, gradC); });
+            timed(4, 1, [&] { k_sweep_B<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, vel, gradC, acc_visc, vel_new, drho_old); });
+            timed(5, 1, [&] { k_sweep_C<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho_old, vel_new, drho, vel, pos); });
+            if (rc) break;
+            int flag = 0;
+            cudaError_t e = cudaMemcpy(&flag, d_loop_flag, sizeof(int), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "loop flag"); break; }
+            if (!flag) break;
+        }
+        if (!rc) rc = launch_post();
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+        if (rc) return rc;
+        SPH_CK(cudaStreamSynchronize(stream));
+        return sync_state();
+    }
+
+    int sync_state() override {
+        SPH_CK(cudaMemcpyAsync(h_state.data(), d_state, sizeof(CaseState) * ncases, cudaMemcpyDeviceToHost, stream));
+        SPH_CK(cudaStreamSynchronize(stream));
+        for (int c = 0; c < ncases; ++c) {
+            CaseRec *r = members[c];
+            if (!r || r->engine != this || r->slot != c) continue;
+            const CaseState &s = h_state[c];
+            r->info.n_adv = s.n_adv;
+            r->info.n_sub = s.n_sub;
+            r->info.t = s.t;
+            r->info.last_dt_ad = s.dt_ad;
+            r->info.last_dt_ac = s.last_dt_ac;
+            r->info.status = map_status(s.status);
+        }
+        return SPHST_OK;
+    }
+
+    int read_field(int slot, int field, double *host) override {
+        const CaseDesc &d = h_desc[slot];
+        const int64_t m = d.p_end - d.p_begin;
+        if (m == 0) return SPHST_OK;
+        const int grid = (int)std::min<int64_t>((m + 255) / 256, 65535);
+        k_read_field<T><<<grid, 256, 0, stream>>>(d_desc, slot, field, pos, vel, drho, gradC, acc_visc, id, d_read);
+        SPH_CK(cudaGetLastError());
+        const int w = (field == 0 || field == 1 || field == 5 || field == 6) ? d.dim : 1;
+        SPH_CK(cudaMemcpyAsync(host, d_read, (size_t)m * w * sizeof(double), cudaMemcpyDeviceToHost, stream));
+        SPH_CK(cudaStreamSynchronize(stream));
+        return SPHST_OK;
+    }
+
+    int debug_keys(int slot, uint64_t *keys, int64_t *ids) override {
+        const CaseDesc &d = h_desc[slot];
+        const int64_t m = d.p_end - d.p_begin;
+        if (m == 0) return SPHST_OK;
+        unsigned long long *dk = (unsigned long long *)d_read;
+        long long *di = (long long *)(d_read + m);
+        const int grid = (int)std::min<int64_t>((m + 255) / 256, 65535);
+        k_debug_keys<T><<<grid, 256, 0, stream>>>(d_desc, slot, snap, id, dk, di);
+        SPH_CK(cudaGetLastError());
+        SPH_CK(cudaMemcpyAsync(keys, dk, m * 8, cudaMemcpyDeviceToHost, stream));
+        SPH_CK(cudaMemcpyAsync(ids, di, m * 8, cudaMemcpyDeviceToHost, stream));
+        SPH_CK(cudaStreamSynchronize(stream));
+        return SPHST_OK;
+    }
+
+    int debug_counts(int slot, int32_t *counts) override {
+        const CaseDesc &d = h_desc[slot];
+        const int64_t m = d.p_end - d.p_begin;
+        if (m == 0) return SPHST_OK;
+        int *dc = (int *)d_read;
+        k_debug_counts<T><<<(unsigned)((m + 127) / 128), 128, 0, stream>>>(d_desc, slot, starts, snap, id, dc);
+        SPH_CK(cudaGetLastError());
+        SPH_CK(cudaMemcpyAsync(counts, dc, m * 4, cudaMemcpyDeviceToHost, stream));
+        SPH_CK(cudaStreamSynchronize(stream));
+        return SPHST_OK;
+    }
+};
+
+}  // namespace sphst

@@ -1,0 +1,909 @@
+// sphst_kernels.cuh -- CUDA kernels of the pair-sweep library (sm_103a).
+//
+// Rebuild (once per advection step, Section 3.3): cell assignment with Morton
+// keys, a counting sort over the dense cell table (histogram by atomics,
+// exclusive scan, scatter), a per-cell sort by insertion index that makes the
+// order canonical, and a gather of the particle arrays.
+//
+// Pair sweeps (gather-only: every thread owns one particle and sums over its
+// neighbours, so there are no atomics on particle data):
+//   M  correction matrix B_i (Eq. 15)                     once per advection step
+//   V  viscous acceleration (Eq. 13) + transport shift (Eq. 14)  once per advection step
+//   A  colour gradient (Eq. 22)                           every acoustic substep
+//   B  pressure (Eqs. 7-12) + surface (Eqs. 24, 26, 33) + kick   every substep
+//   C  continuity (Eq. 6) + drift                         every substep
+// Time-step control (Eqs. 16-18) runs in FP64 in one-thread-per-case kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include "sphst_internal.cuh"
+
+namespace sphst {
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+
+template <typename T> __device__ __forceinline__ V4<T> ld4(const V4<T> *p) { return *p; }
+template <> __device__ __forceinline__ V4<float> ld4<float>(const V4<float> *p) {
+    float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    return V4<float>{v.x, v.y, v.z, v.w};
+}
+
+__device__ __forceinline__ double bits_to_d(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// |v|^2 in FP64 with a fixed operation order and no contraction
+template <typename T> __device__ __forceinline__ double speed2(const V4<T> &v, int dim) {
+    double x = (double)v.x, y = (double)v.y, z = (double)v.z;
+    double s = __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
+    if (dim == 3) s = __dadd_rn(s, __dmul_rn(z, z));
+    return s;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+// Eq. 11 dissipation limiter (readings selected by the case)
+template <typename T> __device__ __forceinline__ T limiter_beta(int mode, T dU, T inv_c0) {
+    if (mode == 1) return T(1);
+    if (mode == 2) return T(0);
+    T b = T(3) * dU * inv_c0;
+    return b < T(0) ? T(0) : (b > T(1) ? T(1) : b);
+}
+
+// --------------------------------------------------------------- cell walk
+// Calls f(j, snap_j, r_ij vector, r^2) for every j != i with 0 < r_ij < 2h in
+// the 3^D cells around i's cell.  r_ij = s_i - s_j - o cs, where o is the
+// neighbour cell's offset, because both offsets are taken from their own
+// cell origins.  Returns true when a coincident particle was met.
+template <typename T, int D, typename F>
+__device__ __forceinline__ bool walk(const CaseDesc &d, const CasePhys<T> &cp,
+                                     const uint32_t *__restrict__ starts,
+                                     const V4<T> *__restrict__ snap, int64_t i,
+                                     const V4<T> &si, uint32_t pki, F &&f) {
+    const int cx = cell_x<D>(pki), cy = cell_y<D>(pki), cz = cell_z<D>(pki);
+    const uint32_t toff = (uint32_t)d.table_off;
+    const T cs = cp.cs, R2 = cp.four_h2;
+    bool coincident = false;
+    for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz) {
+        const int nz = cz + oz;
+        if (D == 3 && (nz < 0 || nz >= d.ncell[2])) continue;
+        const T sz = D == 3 ? si.z - T(oz) * cs : T(0);
+        for (int oy = -1; oy <= 1; ++oy) {
+            const int ny = cy + oy;
+            if (ny < 0 || ny >= d.ncell[1]) continue;
+            const T sy = si.y - T(oy) * cs;
+            for (int ox = -1; ox <= 1; ++ox) {
+                const int nx = cx + ox;
+                if (nx < 0 || nx >= d.ncell[0]) continue;
+                const T sx = si.x - T(ox) * cs;
+                const uint32_t m = toff + morton<D>(nx, ny, nz);
+                const uint32_t b = __ldg(starts + m), e = __ldg(starts + m + 1);
+                for (uint32_t j = b; j < e; ++j) {
+                    const V4<T> sj = ld4(snap + j);
+                    const T rx = sx - sj.x, ry = sy - sj.y;
+                    const T rz = D == 3 ? sz - sj.z : T(0);
+                    const T r2 = D == 3 ? rx * rx + ry * ry + rz * rz : rx * rx + ry * ry;
+                    if (r2 < R2 && j != (uint32_t)i) {
+                        if (r2 > T(0)) f(j, sj, rx, ry, rz, r2);
+                        else coincident = true;
+                    }
+                }
+            }
+        }
+    }
+    return coincident;
+}
+
+// kernel radial derivative and unit vector of one pair
+template <typename T> struct PairGeo { T inv_r, r, dW; };
+template <typename T>
+__device__ __forceinline__ PairGeo<T> geo(const CasePhys<T> &cp, T r2) {
+    PairGeo<T> g;
+    g.inv_r = rsq(r2);
+    g.r = r2 * g.inv_r;
+    const T q = g.r * cp.inv_h;
+    const T u = T(1) - T(0.5) * q;
+    g.dW = cp.kcoef * q * u * u * u;
+    return g;
+}
+
+// ================================================================ rebuild
+// First placement of a freshly uploaded case: absolute FP64 positions ->
+// cell coordinates (floor((x - origin)/cs) in FP64, as the key definition
+// states) and offsets from the cell origin.
+template <typename T, int D>
+__device__ __forceinline__ void init_one(const CaseDesc &d, int c, int64_t k, const double *apos,
+                                         const double *avel, const double *arho, const uint8_t *akind,
+                                         V4<T> *pos, V4<T> *vel, T *drho, uint32_t *id, CaseState *st) {
+    int cc[3] = {0, 0, 0};
+    double off[3] = {0.0, 0.0, 0.0};
+    bool bad = false;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const double rel = __dsub_rn(apos[3 * k + a], d.origin[a]);
+        double f = floor(__ddiv_rn(rel, d.cs));
+        if (!(f >= 0.0 && f < (double)d.ncell[a])) {
+            bad = true;
+            f = f < 0.0 || f != f ? 0.0 : (double)(d.ncell[a] - 1);
+        }
+        cc[a] = (int)f;
+        off[a] = __dsub_rn(rel, __dmul_rn(f, d.cs));
+    }
+    if (bad) atomicCAS(&st[c].status, 0, DEV_ERR_DOMAIN);
+    const uint32_t ph = akind[k];
+    V4<T> p;
+    p.x = (T)off[0]; p.y = (T)off[1]; p.z = (T)off[2];
+    p.w = bits_w(pack_cell<D>(cc[0], cc[1], cc[2], ph), T());
+    const int64_t i = d.p_begin + k;
+    pos[i] = p;
+    V4<T> v;
+    v.x = (T)avel[3 * k]; v.y = (T)avel[3 * k + 1]; v.z = (T)avel[3 * k + 2]; v.w = T(0);
+    vel[i] = v;
+    drho[i] = ph < 2 ? (T)(arho[k] - d.rho0[ph]) : T(0);
+    id[i] = (uint32_t)k;
+}
+
+template <typename T>
+__global__ void k_init_case(const CaseDesc *__restrict__ desc, int c, const double *apos,
+                            const double *avel, const double *arho, const uint8_t *akind,
+                            V4<T> *pos, V4<T> *vel, T *drho, uint32_t *id, CaseState *st) {
+    const CaseDesc &d = desc[c];
+    const int64_t n = d.p_end - d.p_begin;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        if (d.dim == 3) init_one<T, 3>(d, c, k, apos, avel, arho, akind, pos, vel, drho, id, st);
+        else init_one<T, 2>(d, c, k, apos, avel, arho, akind, pos, vel, drho, id, st);
+    }
+}
+
+// New cell of every particle from its offset (which may have drifted out of
+// the cell since the last rebuild), histogram of the cell table.
+template <typename T, int D>
+__device__ __forceinline__ void assign_one(const CaseDesc &d, CaseState *st, int c, int64_t i,
+                                           V4<T> *pos, uint32_t *key, uint32_t *rank,
+                                           uint32_t *counts) {
+    const CasePhys<T> &cp = phys<T>(d);
+    V4<T> p = pos[i];
+    const uint32_t pk = w_bits(p.w);
+    int cc[3] = {cell_x<D>(pk), cell_y<D>(pk), cell_z<D>(pk)};
+    T off[3] = {p.x, p.y, p.z};
+    bool bad = false;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        T f = floor(off[a] / cp.cs);
+        if (!(f == f) || f > T(4096) || f < T(-4096)) { f = T(0); bad = true; }
+        int nc = cc[a] + (int)f;
+        if (nc < 0 || nc >= d.ncell[a]) {
+            bad = true;
+            nc = nc < 0 ? 0 : d.ncell[a] - 1;
+            f = T(nc - cc[a]);
+        }
+        off[a] = off[a] - f * cp.cs;
+        cc[a] = nc;
+    }
+    if (bad) atomicCAS(&st[c].status, 0, DEV_ERR_DOMAIN);
+    p.x = off[0]; p.y = off[1]; p.z = off[2];
+    p.w = bits_w(pack_cell<D>(cc[0], cc[1], cc[2], phase_of(pk)), T());
+    pos[i] = p;
+    const uint32_t k = (uint32_t)d.table_off + morton<D>(cc[0], cc[1], cc[2]);
+    key[i] = k;
+    rank[i] = atomicAdd(counts + k, 1u);
+}
+
+template <typename T>
+__global__ void k_cell_assign(const Tile *__restrict__ tiles, const CaseDesc *__restrict__ desc,
+                              CaseState *st, V4<T> *pos, uint32_t *key, uint32_t *rank,
+                              uint32_t *counts) {
+    const Tile t = tiles[blockIdx.x];
+    if ((int)threadIdx.x >= t.n) return;
+    const CaseDesc &d = desc[t.c];
+    const int64_t i = t.begin + threadIdx.x;
+    if (d.dim == 3) assign_one<T, 3>(d, st, t.c, i, pos, key, rank, counts);
+    else assign_one<T, 2>(d, st, t.c, i, pos, key, rank, counts);
+}
+
+// ---- exclusive scan of the cell histogram (in place, n+1 entries) ----
+constexpr int SCAN_T = 1024;            // threads per block
+constexpr int SCAN_ITEMS = 2 * SCAN_T;  // entries per block
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t warp_sums[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t before = (w > 0 ? warp_sums[w - 1] : 0u) + x - v;
+    *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before;
+}
+
+static __global__ void k_scan_reduce(const uint32_t *data, int64_t n, uint32_t *block_sums) {
+    const int64_t base = (int64_t)blockIdx.x * SCAN_ITEMS + 2 * threadIdx.x;
+    uint32_t v = 0;
+    if (base < n) v += data[base];
+    if (base + 1 < n) v += data[base + 1];
+    uint32_t total;
+    block_exclusive_scan(v, &total);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+static __global__ void k_scan_blocks(uint32_t *block_sums, int64_t nb) {
+    uint32_t carry = 0;
+    for (int64_t base = 0; base < nb; base += SCAN_T) {
+        const int64_t k = base + threadIdx.x;
+        const uint32_t v = k < nb ? block_sums[k] : 0u;
+        uint32_t total;
+        const uint32_t ex = block_exclusive_scan(v, &total);
+        if (k < nb) block_sums[k] = carry + ex;
+        carry += total;
+    }
+}
+
+static __global__ void k_scan_apply(uint32_t *data, int64_t n, const uint32_t *block_sums) {
+    const int64_t base = (int64_t)blockIdx.x * SCAN_ITEMS + 2 * threadIdx.x;
+    const uint32_t a = base < n ? data[base] : 0u;
+    const uint32_t b = base + 1 < n ? data[base + 1] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_exclusive_scan(a + b, &total) + block_sums[blockIdx.x];
+    if (base < n) data[base] = ex;
+    if (base + 1 < n) data[base + 1] = ex + a;
+}
+
+static __global__ void k_scatter(int64_t n, const uint32_t *key, const uint32_t *rank,
+                          const uint32_t *starts, uint32_t *perm) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    perm[starts[key[i]] + rank[i]] = (uint32_t)i;
+}
+
+// canonical order inside each cell: ascending insertion index
+static __global__ void k_cell_sort(int64_t ncells, const uint32_t *starts, const uint32_t *id,
+                            uint32_t *perm) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    const uint32_t b = starts[c], e = starts[c + 1];
+    if (e - b < 2) return;
+    for (uint32_t k = b + 1; k < e; ++k) {
+        const uint32_t pk = perm[k];
+        const uint32_t ik = id[pk];
+        uint32_t m = k;
+        while (m > b && id[perm[m - 1]] > ik) {
+            perm[m] = perm[m - 1];
+            --m;
+        }
+        perm[m] = pk;
+    }
+}
+
+template <typename T>
+__global__ void k_gather(int64_t n, const uint32_t *perm, const V4<T> *pos, const V4<T> *vel,
+                         const T *drho, const uint32_t *id, V4<T> *pos_t, V4<T> *vel_t,
+                         T *drho_t, uint32_t *id_t) {
+    const int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (d >= n) return;
+    const uint32_t s = perm[d];
+    pos_t[d] = pos[s];
+    vel_t[d] = vel[s];
+    drho_t[d] = drho[s];
+    id_t[d] = id[s];
+}
+
+template <typename T>
+__global__ void k_copy_back(int64_t n, const V4<T> *pos_t, const V4<T> *vel_t, const T *drho_t,
+                            const uint32_t *id_t, V4<T> *pos, V4<T> *vel, T *drho, uint32_t *id) {
+    const int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (d >= n) return;
+    pos[d] = pos_t[d];
+    vel[d] = vel_t[d];
+    drho[d] = drho_t[d];
+    id[d] = id_t[d];
+}
+
+// ================================================================ time step
+static __global__ void k_reset_vmax(int ncases, CaseState *st) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncases) return;
+    st[c].vmax2_acc[0] = 0ull;
+    st[c].vmax2_acc[1] = 0ull;
+}
+
+template <typename T>
+__global__ void k_vmax(const Tile *__restrict__ tiles, const CaseDesc *__restrict__ desc,
+                       CaseState *st, const V4<T> *pos, const V4<T> *vel) {
+    const Tile t = tiles[blockIdx.x];
+    const int dim = desc[t.c].dim;
+    unsigned long long m[2] = {0ull, 0ull};
+    if ((int)threadIdx.x < t.n) {
+        const int64_t i = t.begin + threadIdx.x;
+        const uint32_t ph = phase_of(w_bits(pos[i].w));
+        if (ph < 2) m[ph] = (unsigned long long)__double_as_longlong(speed2(vel[i], dim));
+    }
+    m[0] = warp_max_u64(m[0]);
+    m[1] = warp_max_u64(m[1]);
+    if ((threadIdx.x & 31) == 0) {
+        if (m[0]) atomicMax(&st[t.c].vmax2_acc[0], m[0]);
+        if (m[1]) atomicMax(&st[t.c].vmax2_acc[1], m[1]);
+    }
+}
+
+// Eq. 16 per fluid (factor cfl_ad), Eq. 18 minimum; speed terms with
+// |v|max = 0 are dropped.
+static __global__ void k_adv_begin(int ncases, const CaseDesc *desc, CaseState *st) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncases) return;
+    const CaseDesc &d = desc[c];
+    CaseState &s = st[c];
+    s.active = 0;
+    s.last = 0;
+    if (s.status) return;
+    double dt_ad = __longlong_as_double(0x7ff0000000000000ll);   // +inf
+    for (int k = 0; k < 2; ++k) {
+        if (!s.present[k]) continue;
+        const double vmax = sqrt(bits_to_d(s.vmax2_acc[k]));
+        double t = __ddiv_rn(__dmul_rn(__dmul_rn(d.rho0[k], d.h), d.h), d.eta[k]);
+        if (vmax > 0.0) {
+            const double tv = __ddiv_rn(d.h, vmax);
+            if (tv < t) t = tv;
+        }
+        const double cand = __dmul_rn(d.cfl_ad, t);
+        if (cand < dt_ad) dt_ad = cand;
+    }
+    if (!(dt_ad > 0.0) || !(dt_ad < 1e300)) {
+        s.status = DEV_ERR_NONFINITE;
+        return;
+    }
+    s.dt_ad = dt_ad;
+    s.t_in = 0.0;
+    s.n_sub_adv = 0;
+    s.active = 1;
+}
+
+// One acoustic substep criterion per case (Eq. 17 with factor cfl_ac, Eq. 18), clipped to end
+// exactly on the advection step; sets the while-loop condition to "some case
+// still has a substep after this one".
+static __global__ void k_dt(int ncases, const CaseDesc *desc, CaseState *st, int *loop_flag,
+                     cudaGraphConditionalHandle handle, int use_handle) {
+    int more = 0;
+    for (int c = threadIdx.x; c < ncases; c += blockDim.x) {
+        const CaseDesc &d = desc[c];
+        CaseState &s = st[c];
+        if (s.active && s.last) s.active = 0;
+        if (s.active && s.status) s.active = 0;
+        if (!s.active) continue;
+        if (s.n_sub_adv >= d.max_substeps) {
+            s.status = DEV_ERR_STALLED;
+            s.active = 0;
+            continue;
+        }
+        double vmax[2];
+        for (int k = 0; k < 2; ++k) {
+            s.vmax2_cur[k] = s.vmax2_acc[k];
+            s.vmax2_acc[k] = 0ull;
+            vmax[k] = sqrt(bits_to_d(s.vmax2_cur[k]));
+        }
+        double dt_ac = __longlong_as_double(0x7ff0000000000000ll);
+        bool finite = true;
+        for (int k = 0; k < 2; ++k) {
+            if (!s.present[k]) continue;
+            if (!(vmax[k] <= 1e300)) finite = false;
+            double t = __ddiv_rn(d.h, __dadd_rn(d.c0, vmax[k]));
+            if (d.gamma > 0.0) {
+                const double ts = sqrt(__ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(d.rho0[k], d.h), d.h), d.h),
+                                                 __dmul_rn(__dmul_rn(2.0, 3.14159265358979323846), d.gamma)));
+                if (ts < t) t = ts;
+            }
+            const double cand = __dmul_rn(d.cfl_ac, t);
+            if (cand < dt_ac) dt_ac = cand;
+        }
+        if (!finite || !(dt_ac > 0.0) || !(dt_ac < 1e300)) {
+            s.status = DEV_ERR_NONFINITE;
+            s.active = 0;
+            continue;
+        }
+        const double rem = __dsub_rn(s.dt_ad, s.t_in);
+        const int last = dt_ac >= rem;
+        const double dt = last ? rem : dt_ac;
+        s.last_dt_ac = dt_ac;
+        s.dt = dt;
+        s.last = last;
+        s.t_in = __dadd_rn(s.t_in, dt);
+        s.n_sub += 1;
+        s.n_sub_adv += 1;
+        if (!s.last) more = 1;
+    }
+    more = __syncthreads_or(more);
+    if (threadIdx.x == 0) {
+        *loop_flag = more;
+        if (use_handle) cudaGraphSetConditional(handle, more ? 1u : 0u);
+    }
+}
+
+static __global__ void k_adv_end(int ncases, CaseState *st) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncases) return;
+    CaseState &s = st[c];
+    if (s.active && s.last && !s.status) {
+        s.t = __dadd_rn(s.t, s.dt_ad);
+        s.n_adv += 1;
+    }
+    s.active = 0;
+}
+
+// ================================================================= sweeps
+// ---- M: correction matrix of Eq. 15, B_i = -(sum_j r_ij (x) grad_i W_ij V_j)^-1
+template <typename T, int D>
+__device__ __forceinline__ void sweep_M(const CaseDesc &d, const CasePhys<T> &cp, int64_t i,
+                                        const uint32_t *starts, const V4<T> *snap, const T *drho,
+                                        V4<T> *bmat, int32_t *status) {
+    const V4<T> si = ld4(snap + i);
+    const uint32_t pki = w_bits(si.w);
+    if (phase_of(pki) == PH_WALL) return;
+    T m00 = 0, m01 = 0, m02 = 0, m11 = 0, m12 = 0, m22 = 0;
+    const bool coinc = walk<T, D>(d, cp, starts, snap, i, si, pki,
+        [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
+            const PairGeo<T> g = geo(cp, r2);
+            const uint32_t kj = phase_of(w_bits(sj.w));
+            const T Vj = kj == PH_WALL ? cp.vol_wall : cp.mass[kj] / (cp.rho0[kj] + drho[j]);
+            // r (x) dW e V = (dW V / r) r_vec (x) r_vec
+            const T s = g.dW * Vj * g.inv_r;
+            m00 += s * rx * rx; m01 += s * rx * ry; m11 += s * ry * ry;
+            if (D == 3) { m02 += s * rx * rz; m12 += s * ry * rz; m22 += s * rz * rz; }
+        });
+    if (coinc) atomicCAS(status, 0, DEV_ERR_COINCIDENT);
+    T b00, b01, b02 = 0, b11, b12 = 0, b22 = 0;
+    T det;
+    if (D == 2) {
+        det = m00 * m11 - m01 * m01;
+        const T id = T(1) / det;
+        b00 = -m11 * id; b01 = m01 * id; b11 = -m00 * id;
+    } else {
+        const T c00 = m11 * m22 - m12 * m12, c01 = m02 * m12 - m01 * m22, c02 = m01 * m12 - m02 * m11;
+        det = m00 * c00 + m01 * c01 + m02 * c02;
+        const T id = T(1) / det;
+        b00 = -c00 * id; b01 = -c01 * id; b02 = -c02 * id;
+        b11 = -(m00 * m22 - m02 * m02) * id;
+        b12 = -(m02 * m01 - m00 * m12) * id;
+        b22 = -(m00 * m11 - m01 * m01) * id;
+    }
+    if (!(fabs(det) >= T(1e-3))) {
+        b00 = 1; b01 = 0; b02 = 0; b11 = 1; b12 = 0; b22 = D == 3 ? T(1) : T(0);
+    }
+    bmat[2 * i] = V4<T>{b00, b01, b02, b11};
+    bmat[2 * i + 1] = V4<T>{b12, b22, T(0), T(0)};
+}
+
+// ---- V: viscous acceleration (Eq. 13) and transport shift (Eq. 14)
+template <typename T, int D>
+__device__ __forceinline__ void sweep_V(const CaseDesc &d, const CasePhys<T> &cp, int64_t i,
+                                        const uint32_t *starts, const V4<T> *snap, const T *drho,
+                                        const V4<T> *vel, const V4<T> *bmat, V4<T> *acc_visc,
+                                        V4<T> *pos, int32_t *status) {
+    const V4<T> si = ld4(snap + i);
+    const uint32_t pki = w_bits(si.w);
+    const uint32_t ki = phase_of(pki);
+    if (ki == PH_WALL) return;
+    const T rho_i = cp.rho0[ki] + drho[i];
+    const T eta_i = cp.eta[ki];
+    const V4<T> vi = vel[i];
+    const bool tvf = d.tvf_on != 0;
+    V4<T> Bi0 = {0, 0, 0, 0}, Bi1 = {0, 0, 0, 0};
+    if (tvf) { Bi0 = bmat[2 * i]; Bi1 = bmat[2 * i + 1]; }
+    T ax = 0, ay = 0, az = 0, sx = 0, sy = 0, sz = 0;
+    const bool coinc = walk<T, D>(d, cp, starts, snap, i, si, pki,
+        [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
+            const PairGeo<T> g = geo(cp, r2);
+            const uint32_t kj = phase_of(w_bits(sj.w));
+            const V4<T> vj = vel[j];
+            T eta_bar, Vj;
+            V4<T> Bj0 = Bi0, Bj1 = Bi1;
+            if (kj == PH_WALL) {
+                eta_bar = eta_i;
+                Vj = cp.vol_wall;
+            } else {
+                const T eta_j = cp.eta[kj];
+                eta_bar = T(2) * eta_i * eta_j / (eta_i + eta_j);
+                Vj = cp.mass[kj] / (cp.rho0[kj] + drho[j]);
+                if (tvf) { Bj0 = bmat[2 * j]; Bj1 = bmat[2 * j + 1]; }
+            }
+            const T f = eta_bar * g.dW * Vj * g.inv_r;     // eta (v_ij / r) dW V
+            ax += f * (vi.x - vj.x);
+            ay += f * (vi.y - vj.y);
+            if (D == 3) az += f * (vi.z - vj.z);
+            if (tvf) {
+                const T w = g.dW * Vj * g.inv_r;             // grad W V = w r_vec
+                const T gx = w * rx, gy = w * ry, gz = w * rz;
+                // (B_i + B_j) grad W V with symmetric B = [b00 b01 b02; b01 b11 b12; b02 b12 b22]
+                const T s00 = Bi0.x + Bj0.x, s01 = Bi0.y + Bj0.y, s02 = Bi0.z + Bj0.z;
+                const T s11 = Bi0.w + Bj0.w, s12 = Bi1.x + Bj1.x, s22 = Bi1.y + Bj1.y;
+                sx += s00 * gx + s01 * gy + (D == 3 ? s02 * gz : T(0));
+                sy += s01 * gx + s11 * gy + (D == 3 ? s12 * gz : T(0));
+                if (D == 3) sz += s02 * gx + s12 * gy + s22 * gz;
+            }
+        });
+    if (coinc) atomicCAS(status, 0, DEV_ERR_COINCIDENT);
+    const T c = T(2) / rho_i;
+    acc_visc[i] = V4<T>{c * ax, c * ay, c * az, T(0)};
+    if (tvf) {
+        V4<T> p = pos[i];
+        p.x += cp.tvf_coef * sx;
+        p.y += cp.tvf_coef * sy;
+        if (D == 3) p.z += cp.tvf_coef * sz;
+        pos[i] = p;
+    }
+}
+
+// ---- A: colour gradient, Eq. 22 (only pairs of different fluids contribute)
+template <typename T, int D>
+__device__ __forceinline__ void sweep_A(const CaseDesc &d, const CasePhys<T> &cp, int64_t i,
+                                        const uint32_t *starts, const V4<T> *snap, const T *drho,
+                                        V4<T> *gradC) {
+    const V4<T> si = ld4(snap + i);
+    const uint32_t pki = w_bits(si.w);
+    const uint32_t ki = phase_of(pki);
+    V4<T> g = {0, 0, 0, 0};
+    if (ki != PH_WALL && d.n_fluid_phases == 2) {
+        const uint32_t other = ki ^ 1u;
+        const T two_phi = cp.two_phi[ki];
+        const T m_o = cp.mass[other], rho0_o = cp.rho0[other];
+        walk<T, D>(d, cp, starts, snap, i, si, pki,
+            [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
+                if (phase_of(w_bits(sj.w)) != other) return;
+                const PairGeo<T> gg = geo(cp, r2);
+                const T Vj = m_o / (rho0_o + drho[j]);
+                const T s = two_phi * gg.dW * Vj * gg.inv_r;
+                g.x += s * rx;
+                g.y += s * ry;
+                if (D == 3) g.z += s * rz;
+            });
+        g.w = sqrt(g.x * g.x + g.y * g.y + g.z * g.z);
+    }
+    gradC[i] = g;
+}
+
+// ---- B: pressure + surface tension + kick
+template <typename T, int D>
+__device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &cp, T dt,
+                                          int64_t i, const uint32_t *starts, const V4<T> *snap,
+                                          const T *drho, const V4<T> *vel, const V4<T> *gradC,
+                                          const V4<T> *acc_visc, V4<T> *vel_new, T *drho_old,
+                                          uint32_t *phase_out) {
+    const V4<T> si = ld4(snap + i);
+    const uint32_t pki = w_bits(si.w);
+    const uint32_t ki = phase_of(pki);
+    *phase_out = ki;
+    if (ki == PH_WALL) return 0.0;
+    const T dri = drho[i];
+    const T rho_i = cp.rho0[ki] + dri;
+    const T p_i = cp.c0sq * dri;
+    const V4<T> vi = vel[i];
+    const V4<T> gi = gradC[i];
+    const bool if_i = gi.w * cp.h > cp.nhat_eps;
+    const T inv_gi = if_i ? T(1) / gi.w : T(0);
+    const T nix = gi.x * inv_gi, niy = gi.y * inv_gi, niz = gi.z * inv_gi;
+    const T gam_gi = if_i ? cp.gamma * gi.w : T(0);
+    const int lim = d.limiter;
+    const bool surface_on = d.n_fluid_phases == 2;
+    const T c0 = cp.c0, inv_c0 = cp.inv_c0;
+    const T xg = cp.xi * cp.gamma;
+    T apx = 0, apy = 0, apz = 0, asx = 0, asy = 0, asz = 0;
+    walk<T, D>(d, cp, starts, snap, i, si, pki,
+        [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
+            const PairGeo<T> g = geo(cp, r2);
+            const T ex = rx * g.inv_r, ey = ry * g.inv_r, ez = D == 3 ? rz * g.inv_r : T(0);
+            const uint32_t kj = phase_of(w_bits(sj.w));
+            const V4<T> vj = vel[j];
+            const T UL = -(vi.x * ex + vi.y * ey + (D == 3 ? vi.z * ez : T(0)));
+            const T UR = -(vj.x * ex + vj.y * ey + (D == 3 ? vj.z * ez : T(0)));
+            if (kj == PH_WALL) {
+                // mirror state behind a wall moving with v_w: rho_i, p_i, 2 U_w - U_L
+                const T dU = T(2) * (UL - UR);
+                const T beta = limiter_beta(lim, dU, inv_c0);
+                const T Ps = p_i + beta * rho_i * c0 * dU * T(0.5);
+                const T f = Ps * g.dW * cp.vol_wall;
+                apx += f * ex; apy += f * ey; if (D == 3) apz += f * ez;
+                return;
+            }
+            const T drj = drho[j];
+            const T rho_j = cp.rho0[kj] + drj;
+            const T p_j = cp.c0sq * drj;
+            const T Vj = cp.mass[kj] / rho_j;
+            const T inv_rs = T(1) / (rho_i + rho_j);
+            const T pbar = (rho_i * p_j + rho_j * p_i) * inv_rs;     // Eq. 12
+            const T dU = UL - UR;
+            const T beta = limiter_beta(lim, dU, inv_c0);           // Eq. 11
+            const T Ps = pbar + beta * c0 * rho_i * rho_j * dU * inv_rs;   // Eq. 8
+            const T f = Ps * g.dW * Vj;
+            apx += f * ex; apy += f * ey; if (D == 3) apz += f * ez;
+            if (!surface_on) return;
+            const V4<T> gj = gradC[j];
+            if (gi.w == T(0) && gj.w == T(0)) return;                // every surface term vanishes
+            const bool if_j = gj.w * cp.h > cp.nhat_eps;
+            const T inv_gj = if_j ? T(1) / gj.w : T(0);
+            const T njx = gj.x * inv_gj, njy = gj.y * inv_gj, njz = gj.z * inv_gj;
+            const T gam_gj = if_j ? cp.gamma * gj.w : T(0);
+            const T nie = nix * ex + niy * ey + niz * ez;
+            const T nje = njx * ex + njy * ey + njz * ez;
+            // Pi e = gamma |gradC| (e - n (n.e))   (Eq. 24)
+            const T pix = gam_gi * (ex - nix * nie), piy = gam_gi * (ey - niy * nie), piz = gam_gi * (ez - niz * nie);
+            const T pjx = gam_gj * (ex - njx * nje), pjy = gam_gj * (ey - njy * nje), pjz = gam_gj * (ez - njz * nje);
+            const bool same = kj == ki;
+            const T sg = (same || d.grad_mode == 1) ? T(1) : T(-1);
+            const T bx = T(0.5) * (gi.x + sg * gj.x), by = T(0.5) * (gi.y + sg * gj.y),
+                    bz = T(0.5) * (gi.z + sg * gj.z);
+            const T bn = sqrt(bx * bx + by * by + bz * bz);
+            const T Cij = same ? T(0) : T(1);
+            // C-hat e (Eq. 30 with the selected contraction)
+            T cx, cy, cz;
+            if (d.penalty_form == 0) {
+                const T fac = bn > T(0) ? g.r * (bx * ex + by * ey + bz * ez) / bn : T(0);
+                cx = Cij * ex - fac * bx; cy = Cij * ey - fac * by; cz = Cij * ez - fac * bz;
+            } else {
+                const T s = Cij - bn * g.r;
+                cx = s * ex; cy = s * ey; cz = s * ez;
+            }
+            // N-bar C-hat e = (n_i (n_i.c) + n_j (n_j.c)) / 2
+            const T nic = nix * cx + niy * cy + niz * cz;
+            const T njc = njx * cx + njy * cy + njz * cz;
+            const T qx = T(0.5) * (nix * nic + njx * njc), qy = T(0.5) * (niy * nic + njy * njc),
+                    qz = T(0.5) * (niz * nic + njz * njc);
+            const T pen = xg * g.inv_r;
+            T sx, sy, sz;
+            if (same) {   // Eq. 33, first line; T-bar c = c - N-bar c
+                sx = pix + pjx + pen * (cx - qx);
+                sy = piy + pjy + pen * (cy - qy);
+                sz = piz + pjz + pen * (cz - qz);
+            } else {      // Eq. 33, second line
+                const T a = cp.two_phi[kj], b = cp.two_phi[ki], c = cp.four_phi_phi * pen;
+                sx = a * pix + b * pjx - c * qx;
+                sy = a * piy + b * pjy - c * qy;
+                sz = a * piz + b * pjz - c * qz;
+            }
+            const T w = g.dW * Vj;
+            asx += sx * w; asy += sy * w; if (D == 3) asz += sz * w;
+        });
+    const T inv_rho = T(1) / rho_i;
+    const V4<T> av = acc_visc[i];
+    V4<T> vn;
+    vn.x = vi.x + dt * (T(-2) * inv_rho * apx + inv_rho * asx + av.x);
+    vn.y = vi.y + dt * (T(-2) * inv_rho * apy + inv_rho * asy + av.y);
+    vn.z = D == 3 ? vi.z + dt * (T(-2) * inv_rho * apz + inv_rho * asz + av.z) : T(0);
+    vn.w = T(0);
+    vel_new[i] = vn;
+    drho_old[i] = dri;
+    return speed2(vn, D);
+}
+
+// ---- C: continuity (Eq. 6) with v* (normal component -U*) + drift
+template <typename T, int D>
+__device__ __forceinline__ void sweep_C(const CaseDesc &d, const CasePhys<T> &cp, T dt, int64_t i,
+                                        const uint32_t *starts, const V4<T> *snap,
+                                        const T *drho_old, const V4<T> *vel_new, T *drho,
+                                        V4<T> *vel, V4<T> *pos) {
+    const V4<T> si = ld4(snap + i);
+    const uint32_t pki = w_bits(si.w);
+    const uint32_t ki = phase_of(pki);
+    if (ki == PH_WALL) return;
+    const T dri = drho_old[i];
+    const T rho_i = cp.rho0[ki] + dri;
+    const T p_i = cp.c0sq * dri;
+    const V4<T> vi = vel_new[i];
+    const T c0 = cp.c0;
+    T s = 0;
+    walk<T, D>(d, cp, starts, snap, i, si, pki,
+        [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
+            const PairGeo<T> g = geo(cp, r2);
+            const uint32_t kj = phase_of(w_bits(sj.w));
+            const V4<T> vj = vel_new[j];
+            const T dvx = vi.x - vj.x, dvy = vi.y - vj.y, dvz = D == 3 ? vi.z - vj.z : T(0);
+            // (v_i - v_j).e = U_R - U_L
+            const T dve = (dvx * rx + dvy * ry + dvz * rz) * g.inv_r;
+            if (kj == PH_WALL) {          // v* = v_w
+                s += dve * g.dW * cp.vol_wall;
+                return;
+            }
+            const T drj = drho_old[j];
+            const T rho_j = cp.rho0[kj] + drj;
+            const T p_j = cp.c0sq * drj;
+            const T Vj = cp.mass[kj] / rho_j;
+            // (v_i - v*).e = U* - U_L = (Z_R (U_R - U_L) + p_i - p_j) / (Z_L + Z_R)
+            const T du = (rho_j * c0 * dve + (p_i - p_j)) / (c0 * (rho_i + rho_j));
+            s += du * g.dW * Vj;
+        });
+    drho[i] = dri + dt * (T(2) * rho_i * s);
+    V4<T> p = pos[i];
+    p.x += dt * vi.x;
+    p.y += dt * vi.y;
+    if (D == 3) p.z += dt * vi.z;
+    pos[i] = p;
+    vel[i] = vi;
+}
+
+// ---------------------------------------------------------- sweep kernels
+struct SweepArgs {
+    const Tile *tiles;
+    const CaseDesc *desc;
+    CaseState *st;
+    const uint32_t *starts;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_M(SweepArgs a, const V4<T> *snap, const T *drho, V4<T> *bmat) {
+    const Tile t = a.tiles[blockIdx.x];
+    if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
+    const CaseDesc &d = a.desc[t.c];
+    if (!d.tvf_on) return;
+    const int64_t i = t.begin + threadIdx.x;
+    if (d.dim == 3) sweep_M<T, 3>(d, phys<T>(d), i, a.starts, snap, drho, bmat, &a.st[t.c].status);
+    else sweep_M<T, 2>(d, phys<T>(d), i, a.starts, snap, drho, bmat, &a.st[t.c].status);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_V(SweepArgs a, const V4<T> *snap, const T *drho, const V4<T> *vel,
+                                                 const V4<T> *bmat, V4<T> *acc_visc, V4<T> *pos) {
+    const Tile t = a.tiles[blockIdx.x];
+    if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
+    const CaseDesc &d = a.desc[t.c];
+    const int64_t i = t.begin + threadIdx.x;
+    if (d.dim == 3) sweep_V<T, 3>(d, phys<T>(d), i, a.starts, snap, drho, vel, bmat, acc_visc, pos, &a.st[t.c].status);
+    else sweep_V<T, 2>(d, phys<T>(d), i, a.starts, snap, drho, vel, bmat, acc_visc, pos, &a.st[t.c].status);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_A(SweepArgs a, const V4<T> *snap, const T *drho, V4<T> *gradC) {
+    const Tile t = a.tiles[blockIdx.x];
+    if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
+    const CaseDesc &d = a.desc[t.c];
+    const int64_t i = t.begin + threadIdx.x;
+    if (d.dim == 3) sweep_A<T, 3>(d, phys<T>(d), i, a.starts, snap, drho, gradC);
+    else sweep_A<T, 2>(d, phys<T>(d), i, a.starts, snap, drho, gradC);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_B(SweepArgs a, const V4<T> *snap, const T *drho, const V4<T> *vel,
+                                                 const V4<T> *gradC, const V4<T> *acc_visc,
+                                                 V4<T> *vel_new, T *drho_old) {
+    const Tile t = a.tiles[blockIdx.x];
+    if (!a.st[t.c].active) return;                 // uniform per block
+    const CaseDesc &d = a.desc[t.c];
+    double v2 = 0.0;
+    uint32_t ph = PH_WALL;
+    if ((int)threadIdx.x < t.n) {
+        const int64_t i = t.begin + threadIdx.x;
+        const T dt = (T)a.st[t.c].dt;
+        if (d.dim == 3) v2 = sweep_B<T, 3>(d, phys<T>(d), dt, i, a.starts, snap, drho, vel, gradC, acc_visc, vel_new, drho_old, &ph);
+        else v2 = sweep_B<T, 2>(d, phys<T>(d), dt, i, a.starts, snap, drho, vel, gradC, acc_visc, vel_new, drho_old, &ph);
+    }
+    unsigned long long m0 = ph == 0 ? (unsigned long long)__double_as_longlong(v2) : 0ull;
+    unsigned long long m1 = ph == 1 ? (unsigned long long)__double_as_longlong(v2) : 0ull;
+    m0 = warp_max_u64(m0);
+    m1 = warp_max_u64(m1);
+    if ((threadIdx.x & 31) == 0) {
+        if (m0) atomicMax(&a.st[t.c].vmax2_acc[0], m0);
+        if (m1) atomicMax(&a.st[t.c].vmax2_acc[1], m1);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_C(SweepArgs a, const V4<T> *snap, const T *drho_old,
+                                                 const V4<T> *vel_new, T *drho, V4<T> *vel, V4<T> *pos) {
+    const Tile t = a.tiles[blockIdx.x];
+    if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
+    const CaseDesc &d = a.desc[t.c];
+    const int64_t i = t.begin + threadIdx.x;
+    const T dt = (T)a.st[t.c].dt;
+    if (d.dim == 3) sweep_C<T, 3>(d, phys<T>(d), dt, i, a.starts, snap, drho_old, vel_new, drho, vel, pos);
+    else sweep_C<T, 2>(d, phys<T>(d), dt, i, a.starts, snap, drho_old, vel_new, drho, vel, pos);
+}
+
+// ------------------------------------------------------------ read-back
+// field values of one case into a device buffer in insertion order (FP64)
+template <typename T>
+__global__ void k_read_field(const CaseDesc *desc, int c, int field, const V4<T> *pos,
+                             const V4<T> *vel, const T *drho, const V4<T> *gradC,
+                             const V4<T> *acc_visc, const uint32_t *id, double *out) {
+    const CaseDesc &d = desc[c];
+    const int64_t n = d.p_end - d.p_begin;
+    const int dim = d.dim;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = d.p_begin + k;
+        const int64_t o = id[i];
+        const V4<T> p = pos[i];
+        const uint32_t pk = w_bits(p.w);
+        const uint32_t ph = phase_of(pk);
+        switch (field) {
+        case 0: {
+            const int cc[3] = {dim == 3 ? cell_x<3>(pk) : cell_x<2>(pk),
+                               dim == 3 ? cell_y<3>(pk) : cell_y<2>(pk),
+                               dim == 3 ? cell_z<3>(pk) : 0};
+            const double off[3] = {(double)p.x, (double)p.y, (double)p.z};
+            for (int a = 0; a < dim; ++a)
+                out[o * dim + a] = d.origin[a] + (double)cc[a] * d.cs + off[a];
+            break;
+        }
+        case 1: {
+            const V4<T> v = vel[i];
+            const double vv[3] = {(double)v.x, (double)v.y, (double)v.z};
+            for (int a = 0; a < dim; ++a) out[o * dim + a] = vv[a];
+            break;
+        }
+        case 2: out[o] = ph < 2 ? d.rho0[ph] + (double)drho[i] : d.rho0[0]; break;
+        case 3: out[o] = ph < 2 ? d.c0 * d.c0 * (double)drho[i] : 0.0; break;
+        case 5: {
+            const V4<T> g = gradC[i];
+            const double gg[3] = {(double)g.x, (double)g.y, (double)g.z};
+            for (int a = 0; a < dim; ++a) out[o * dim + a] = gg[a];
+            break;
+        }
+        case 6: {
+            const V4<T> g = acc_visc[i];
+            const double gg[3] = {(double)g.x, (double)g.y, (double)g.z};
+            for (int a = 0; a < dim; ++a) out[o * dim + a] = gg[a];
+            break;
+        }
+        default: break;
+        }
+    }
+}
+
+// Morton key (from the packed cell of the last rebuild) and insertion id of
+// every particle of case c in device order
+template <typename T>
+__global__ void k_debug_keys(const CaseDesc *desc, int c, const V4<T> *snap, const uint32_t *id,
+                             unsigned long long *keys, long long *ids) {
+    const CaseDesc &d = desc[c];
+    const int64_t n = d.p_end - d.p_begin;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = d.p_begin + k;
+        const uint32_t pk = w_bits(snap[i].w);
+        keys[k] = d.dim == 3 ? morton_of_packed<3>(pk) : morton_of_packed<2>(pk);
+        ids[k] = id[i];
+    }
+}
+
+template <typename T, int D>
+__device__ void count_nbrs(const CaseDesc &d, int64_t i, const uint32_t *starts, const V4<T> *snap,
+                           const uint32_t *id, int *out) {
+    const V4<T> si = ld4(snap + i);
+    int cnt = 0;
+    walk<T, D>(d, phys<T>(d), starts, snap, i, si, w_bits(si.w),
+               [&](uint32_t, const V4<T> &, T, T, T, T) { ++cnt; });
+    out[id[i]] = cnt;
+}
+
+template <typename T>
+__global__ void k_debug_counts(const CaseDesc *desc, int c, const uint32_t *starts,
+                               const V4<T> *snap, const uint32_t *id, int *out) {
+    const CaseDesc &d = desc[c];
+    const int64_t n = d.p_end - d.p_begin;
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    if (d.dim == 3) count_nbrs<T, 3>(d, d.p_begin + k, starts, snap, id, out);
+    else count_nbrs<T, 2>(d, d.p_begin + k, starts, snap, id, out);
+}
+
+}  // namespace sphst

@@ -59,6 +59,7 @@ class Case:
     c0: float = 10.0
     h_factor: float = 1.3
     xi: float = -1.0              # < 0: derive from the density ratio
+    cfl_ac: float = 0.6           # factor of the acoustic time-step criterion
     phases: List[Phase] = dataclasses.field(default_factory=list)
     t_end: Optional[float] = None  # physical end time of the workload, if any
     meta: dict = dataclasses.field(default_factory=dict)
@@ -256,9 +257,11 @@ def impact_3d(dx: float = 1.0 / 60.0) -> Case:
     """Droplet D = 1 moving at U = 1 towards the wall z = 0, centred 0.6 above
     it in a 4x4x2 box; rho 1000/1, mu 0.1/0.001, sigma 0.04 (Re = 1e4,
     We = 2.5e4, Eq. 38); dx = D/60."""
-    return droplet_case("impact_3d", 3, [0, 0, 0], [4, 4, 2], dx, [2, 2, 0.6],
+    case = droplet_case("impact_3d", 3, [0, 0, 0], [4, 4, 2], dx, [2, 2, 0.6],
                         0.5, shape="circle", sigma=0.04,
                         drop_vel=[0, 0, -1.0], t_end=2.0)
+    case.cfl_ac = 0.4      # the sound term binds the acoustic step here
+    return case
 
 
 def small_droplet(dim: int = 2, n_side: int = 24, R_frac: float = 0.3,
@@ -278,6 +281,8 @@ def small_droplet(dim: int = 2, n_side: int = 24, R_frac: float = 0.3,
     case = droplet_case(f"small_{dim}d_{n_side}", dim, lo, hi, dx, [0.5] * dim,
                         R_frac, shape=shape, amp=amp, sigma=sigma, rho_l=rho_l,
                         rho_g=rho_g, mu_l=mu_l, mu_g=mu_g, c0=c0, walls=walls)
+    if dim == 3:
+        case.cfl_ac = 0.4      # coarse 3D cases are bound by the sound term
     if seed is not None and (jitter > 0 or vel_amp > 0):
         rng = np.random.default_rng(seed)
         for ph in case.phases:
@@ -341,6 +346,7 @@ class CaseSpec:
                             [0.0] * self.dim, [box] * self.dim, dx, c, self.R,
                             shape=self.shape, amp=self.amp, sigma=self.sigma)
         case.meta["spec"] = dataclasses.asdict(self)
+        case.cfl_ac = 0.4      # small or weakly tensioned cases are bound by the sound term
         return case
 
 

@@ -1,0 +1,175 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bars (see the readings and tolerances documented with the library):
+  * cell keys, canonical order and neighbour counts: bit-exact;
+  * FP64 fields after one advection step (tens of acoustic substeps):
+    max |gpu - oracle| <= 1e-12 * max |oracle| per field;
+  * FP32 fields after one acoustic substep: <= 1e-5 * max |oracle|;
+    after a whole advection step: <= 2e-4 (rounding of FP32 amplified
+    through the substeps, see the derivation in the design notes).
+Fields compared: displacement x - x0, velocity, density deviation rho - rho0,
+colour gradient and viscous acceleration, fluid particles only.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import sphcases
+
+pytestmark = pytest.mark.gpu
+
+S = pytest.importorskip("paper_2503_16082_gb300")
+
+
+def gpu_case(case, precision, **kw):
+    return S.case_from_spec(case, precision=precision, **kw)
+
+
+def run_both(case, precision, n_adv, ora_kw=None, **kw):
+    h = gpu_case(case, precision, **kw)
+    try:
+        info = S.step(h, n_adv)
+        g = {
+            "pos": S.read_fields(h, S.FIELD_POS, case.dim),
+            "vel": S.read_fields(h, S.FIELD_VEL, case.dim),
+            "rho": S.read_fields(h, S.FIELD_RHO, case.dim),
+            "gradC": S.read_fields(h, S.FIELD_GRADC, case.dim),
+            "acc_visc": S.read_fields(h, S.FIELD_ACC_VISC, case.dim),
+        }
+    finally:
+        S.destroy(h)
+    pos, vel, rho, kind = case.flat()
+    P = oracle.params_for_case(case, **(ora_kw or {}))
+    p1, v1, r1, oinfo, gC, av = oracle.run(P, pos, vel, rho, kind, n_adv)
+    d = case.dim
+    o = {"pos": p1[:, :d], "vel": v1[:, :d], "rho": r1, "gradC": gC[:, :d], "acc_visc": av[:, :d]}
+    return g, o, info, oinfo, pos[:, :d], kind
+
+
+def rel_err(g, o, pos0, kind, key, case):
+    fl = kind < 2
+    a, b = g[key][fl], o[key][fl]
+    if key == "pos":
+        a, b = a - pos0[fl], b - pos0[fl]
+    if key == "rho":
+        rho0 = np.asarray(case.fluid_props()[0])[kind[fl]]
+        a, b = a - rho0, b - rho0
+    scale = np.abs(b).max()
+    return np.abs(a - b).max() / scale if scale > 0 else np.abs(a - b).max()
+
+
+def small(dim, **kw):
+    args = dict(n_side=24 if dim == 2 else 10, R_frac=0.3, seed=11, jitter=0.15, vel_amp=0.05)
+    args.update(kw)
+    return sphcases.small_droplet(dim, **args)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("precision", [32, 64])
+def test_keys_order_and_counts_bit_exact(dim, precision):
+    case = small(dim)
+    h = gpu_case(case, precision)
+    try:
+        S.step(h, 1)
+        origin, cs, ncell = S.debug_grid(h)
+        keys, ids = S.debug_keys(h)
+        counts = S.debug_neighbor_counts(h)
+    finally:
+        S.destroy(h)
+    pos, vel, rho, kind = case.flat()
+    P = oracle.params_for_case(case)
+    o_origin, o_cs, o_ncell = oracle.grid(P, pos, pad=2)
+    assert cs == o_cs
+    assert np.array_equal(origin, o_origin) and np.array_equal(ncell, o_ncell)
+    okeys, cells, order, outside = oracle.cell_keys(P, pos, o_origin, o_cs, o_ncell)
+    assert outside == 0
+    assert np.array_equal(ids, order)                 # canonical order
+    assert np.array_equal(keys, okeys[order])         # Morton key of every slot
+    ocounts, _ = oracle.neighbors(P, pos)
+    assert np.array_equal(counts, ocounts)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fp64_one_advection_step(dim):
+    case = small(dim)
+    g, o, info, oinfo, pos0, kind = run_both(case, 64, 1)
+    assert info["n_sub"] == oinfo["n_sub"] > 5
+    for key in ("pos", "vel", "rho", "gradC", "acc_visc"):
+        assert rel_err(g, o, pos0, kind, key, case) <= 1e-12, key
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fp64_three_advection_steps_and_keys_after_motion(dim):
+    case = small(dim)
+    g, o, info, oinfo, pos0, kind = run_both(case, 64, 3)
+    assert info["n_sub"] == oinfo["n_sub"]
+    assert info["t"] == pytest.approx(oinfo["t"], rel=1e-14)
+    for key in ("pos", "vel", "rho", "gradC", "acc_visc"):
+        assert rel_err(g, o, pos0, kind, key, case) <= 1e-11, key
+
+
+def one_substep_case(dim):
+    # viscous enough that the advection step is shorter than the acoustic
+    # step, so one advection step is exactly one acoustic substep (Eq. 16-18)
+    return small(dim, mu_l=50.0, mu_g=0.5)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fp32_one_substep(dim):
+    case = one_substep_case(dim)
+    g, o, info, oinfo, pos0, kind = run_both(case, 32, 1)
+    assert info["n_sub"] == oinfo["n_sub"] == 1
+    for key in ("pos", "vel", "rho", "gradC", "acc_visc"):
+        assert rel_err(g, o, pos0, kind, key, case) <= 1e-5, key
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fp32_one_advection_step(dim):
+    case = small(dim)
+    g, o, info, oinfo, pos0, kind = run_both(case, 32, 1)
+    assert info["n_sub"] == oinfo["n_sub"]
+    for key in ("pos", "vel", "rho", "gradC", "acc_visc"):
+        assert rel_err(g, o, pos0, kind, key, case) <= 2e-4, key
+
+
+@pytest.mark.parametrize("opts,ora", [
+    (dict(limiter=1), dict(limiter=1)),
+    (dict(limiter=2), dict(limiter=2)),
+    (dict(grad_mode=1), dict(grad_mode=1)),
+    (dict(penalty_form=1), dict(penalty_form=1)),
+    (dict(tvf_alpha=0.0), dict(tvf_alpha=0.0)),
+    (dict(xi=0.0), dict(xi=0.0)),
+])
+def test_fp64_readings_flags(opts, ora):
+    case = small(2)
+    g, o, info, oinfo, pos0, kind = run_both(case, 64, 1, ora_kw=ora, **opts)
+    assert info["n_sub"] == oinfo["n_sub"]
+    for key in ("pos", "vel", "rho", "gradC"):
+        assert rel_err(g, o, pos0, kind, key, case) <= 1e-12, key
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_graph_and_host_loop_identical(precision):
+    case = small(3)
+    out = []
+    for mode in (S.LOOP_GRAPH, S.LOOP_HOST):
+        h = gpu_case(case, precision, loop_mode=mode)
+        S.step(h, 2)
+        out.append((S.read_fields(h, S.FIELD_POS, 3), S.read_fields(h, S.FIELD_VEL, 3),
+                    S.read_fields(h, S.FIELD_RHO, 3), S.case_info(h)))
+        S.destroy(h)
+    for a, b in zip(out[0][:3], out[1][:3]):
+        assert np.array_equal(a, b)
+    assert out[0][3]["n_sub"] == out[1][3]["n_sub"]
+
+
+def test_profile_step_matches_graph_step():
+    case = small(2)
+    h1, h2 = gpu_case(case, 32), gpu_case(case, 32)
+    S.step(h1, 1)
+    prof = S.profile_step(h2)
+    assert prof["sweep_B"][1] == S.case_info(h1)["n_sub"]
+    assert all(ms >= 0 for ms, _ in prof.values())
+    assert np.array_equal(S.read_fields(h1, S.FIELD_VEL, 2), S.read_fields(h2, S.FIELD_VEL, 2))
+    S.destroy(h1)
+    S.destroy(h2)
