@@ -163,7 +163,8 @@ def run_ours(args, dist: Dist):
     spec = workload(args.workload)
     n_fluid = spec.n_fluid
 
-    h = S.case_from_spec(spec, precision=args.precision)
+    nbr_mode = S.NBR_CELLS if args.nbr == "cells" else S.NBR_LIST
+    h = S.case_from_spec(spec, precision=args.precision, nbr_mode=nbr_mode)
     S.set_stream(h, stream.cuda_stream)
     S.step(h, args.warmup)                       # engine set-up, graph capture, warm-up
     info0 = S.case_info(h)
@@ -184,9 +185,10 @@ def run_ours(args, dist: Dist):
     n_sub = info1["n_sub"] - info0["n_sub"]
     units = float(n_fluid) * n_sub
     value, tmax, total_units = aggregate(dist, units, ms / 1e3)
-    # kernels launched in the timed region: per advection step 13 set-up
-    # kernels + 1 closing kernel, per substep 4
-    launches = args.steps * 14 + 4 * n_sub
+    # kernels launched in the timed region: per advection step 14 set-up
+    # kernels (speed reduction 3, rebuild 8, list 1, correction matrix,
+    # viscous + shift) + 1 closing kernel, per substep 4
+    launches = args.steps * 15 + 4 * n_sub
 
     # live per-kernel timing of one more advection step (events around each
     # launch on the same stream) for the roofline of the dominant kernel
@@ -218,7 +220,7 @@ def run_ours(args, dist: Dist):
         dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h2 = S.case_from_spec(spec, precision=args.precision)
+        h2 = S.case_from_spec(spec, precision=args.precision, nbr_mode=nbr_mode)
         S.set_stream(h2, stream.cuda_stream)
         d2h = 0
         e_sub0 = 0
@@ -290,6 +292,8 @@ def main():
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nbr", default="list", choices=["list", "cells"],
+                    help="neighbour source of the sweeps (list built per advection step, or cell walk)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -298,7 +302,7 @@ def main():
     config = {"workload": args.workload, "particles": None, "fluid_particles": None,
               "step": "one advection step (rebuild + all acoustic substeps)",
               "l2": "inputs larger than L2 (~170 MB FP32 working set vs 129 MB L2)",
-              "parallelism": f"replicas x{max(ws, 1)}"}
+              "parallelism": f"replicas x{max(ws, 1)}", "neighbours": args.nbr}
     dtype = "f32" if args.precision == 32 else "f64"
 
     if args.impl == "reference":

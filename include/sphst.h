@@ -48,6 +48,7 @@ extern "C" {
 #define SPHST_ERR_COINCIDENT (-10)   /* two particles at the same position        */
 #define SPHST_ERR_STALLED    (-11)   /* advection step exceeded max_substeps      */
 #define SPHST_ERR_CAPACITY   (-12)   /* destination buffer too small              */
+#define SPHST_ERR_NEIGHBORS  (-13)   /* a particle has more neighbours than max_neighbors */
 
 /* --------------------------------------------------------- particle kinds */
 #define SPHST_FLUID 0
@@ -73,6 +74,12 @@ extern "C" {
  * every substep */
 #define SPHST_LOOP_GRAPH 0
 #define SPHST_LOOP_HOST  1
+/* how the sweeps find neighbours: LIST builds a neighbour list of the frozen
+ * configuration once per advection step (Section 3.3) and every substep's
+ * sweeps read it; CELLS walks the 3^d cells around each particle every time.
+ * Both visit neighbours in the same order and give identical results. */
+#define SPHST_NBR_LIST  0
+#define SPHST_NBR_CELLS 1
 
 /* ------------------------------------------------------------- fields     */
 #define SPHST_FIELD_POS      0   /* n x dim positions                            */
@@ -108,6 +115,8 @@ typedef struct {
     double  cfl_ac;         /* factor of the acoustic criterion, Eq. 17 (0.6);
                                a density-ratio-1000 interface bound by the
                                sound term needs <= 0.5 (2D) / 0.4 (3D)        */
+    int32_t nbr_mode;       /* SPHST_NBR_*                                     */
+    int32_t max_neighbors;  /* list capacity per particle; 0: 128 (3D), 48 (2D) */
 } sphst_case_params;
 
 typedef struct {
@@ -130,8 +139,8 @@ typedef struct {
 
 /* Fill *p with the defaults: dim 2, precision 32, h_factor 1.3, c0 10,
  * gamma 1, xi -1 (derived), tvf_alpha 0.2, readings 0, graph loop,
- * grid_pad 2, block 128, max_substeps 1000000, cfl_ad 0.1, cfl_ac 0.6;
- * dx must still be set. */
+ * grid_pad 2, block 128, max_substeps 1000000, cfl_ad 0.1, cfl_ac 0.6,
+ * neighbour lists with the default capacity; dx must still be set. */
 void sphst_default_params(sphst_case_params *p);
 
 /* Create an empty case from the problem statement of Sections 2-3.
@@ -161,7 +170,8 @@ int sphst_add_phase_particles(sphst_case c, const sphst_phase_props *props, int6
  * (optional) receives the case totals.  A case whose device status turns
  * non-zero stops where it failed and keeps returning that error; its fields
  * stay readable.  Errors: STATE (case is a batch member), NONFINITE, DOMAIN,
- * COINCIDENT, STALLED, OOM, CUDA, UNSUPPORTED (cell grid too large). */
+ * COINCIDENT, STALLED, NEIGHBORS, OOM, CUDA, UNSUPPORTED (cell grid too
+ * large, or more than 2^26 particles in one engine with neighbour lists). */
 int sphst_step(sphst_case c, int64_t n_adv, sphst_step_info *info);
 
 /* Copy one field, in insertion order and FP64 whatever the internal

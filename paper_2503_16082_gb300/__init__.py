@@ -21,7 +21,8 @@ from . import build as _build
 OK = 0
 ERR_INVALID_ARG, ERR_STATE, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA = -1, -2, -3, -4, -5
 ERR_NONFINITE, ERR_TIMEOUT, ERR_OVER_BUDGET, ERR_DOMAIN = -6, -7, -8, -9
-ERR_COINCIDENT, ERR_STALLED, ERR_CAPACITY = -10, -11, -12
+ERR_COINCIDENT, ERR_STALLED, ERR_CAPACITY, ERR_NEIGHBORS = -10, -11, -12, -13
+NBR_LIST, NBR_CELLS = 0, 1
 FLUID, WALL = 0, 1
 LIMITER_DENSITY, LIMITER_NONE, LIMITER_ZERO = 0, 1, 2
 GRAD_COMMON, GRAD_PRINTED = 0, 1
@@ -37,7 +38,8 @@ class CaseParams(C.Structure):
                 ("xi", C.c_double), ("tvf_alpha", C.c_double), ("limiter", C.c_int32),
                 ("grad_mode", C.c_int32), ("penalty_form", C.c_int32), ("loop_mode", C.c_int32),
                 ("grid_pad", C.c_int32), ("block", C.c_int32), ("max_substeps", C.c_int64),
-                ("cfl_ad", C.c_double), ("cfl_ac", C.c_double)]
+                ("cfl_ad", C.c_double), ("cfl_ac", C.c_double),
+                ("nbr_mode", C.c_int32), ("max_neighbors", C.c_int32)]
 
 
 class PhaseProps(C.Structure):

@@ -39,6 +39,7 @@ int map_status(int32_t s) {
     case DEV_ERR_DOMAIN: return SPHST_ERR_DOMAIN;
     case DEV_ERR_COINCIDENT: return SPHST_ERR_COINCIDENT;
     case DEV_ERR_STALLED: return SPHST_ERR_STALLED;
+    case DEV_ERR_NBR_OVERFLOW: return SPHST_ERR_NEIGHBORS;
     }
     return SPHST_ERR_CUDA;
 }
@@ -49,6 +50,7 @@ static const char *status_text(int s) {
     case SPHST_ERR_DOMAIN: return "a particle left the cell grid";
     case SPHST_ERR_COINCIDENT: return "two particles at the same position";
     case SPHST_ERR_STALLED: return "advection step exceeded max_substeps";
+    case SPHST_ERR_NEIGHBORS: return "a particle has more neighbours than max_neighbors";
     }
     return "error";
 }
@@ -156,6 +158,8 @@ CaseDesc make_desc(const CaseRec *c) {
     d.max_substeps = c->P.max_substeps > 0 ? c->P.max_substeps : 1000000;
     d.cfl_ad = c->P.cfl_ad;
     d.cfl_ac = c->P.cfl_ac;
+    d.nbr_mode = c->P.nbr_mode;
+    d.nbr_k = c->P.max_neighbors > 0 ? c->P.max_neighbors : (c->P.dim == 3 ? 128 : 48);
     d.pf = phys_of<float>(c);
     d.pd = phys_of<double>(c);
     return d;
@@ -163,7 +167,9 @@ CaseDesc make_desc(const CaseRec *c) {
 
 int64_t footprint(const sphst_case_params *P, int64_t n) {
     const int64_t tsz = P->precision == 64 ? 8 : 4;
-    const int64_t per = 8 * 4 * tsz + 2 * tsz + 4 * 4;        // V4 arrays (8 incl. 2 for B), scalars, ints
+    const int64_t kmax = P->nbr_mode == SPHST_NBR_LIST
+                             ? (P->max_neighbors > 0 ? P->max_neighbors : (P->dim == 3 ? 128 : 48)) : 0;
+    const int64_t per = 8 * 4 * tsz + 2 * tsz + 4 * 4 + 4 * kmax + 4;  // V4 arrays, scalars, ints, list
     // cell table: cells ~ n / 2.6^d per axis padded to a power of two
     const double side = std::pow((double)std::max<int64_t>(n, 1), 1.0 / P->dim) / 2.6 + 2.0 * P->grid_pad + 2.0;
     int bits = 0;
@@ -240,6 +246,8 @@ void sphst_default_params(sphst_case_params *p) {
     p->max_substeps = 1000000;
     p->cfl_ad = 0.1;
     p->cfl_ac = 0.6;
+    p->nbr_mode = SPHST_NBR_LIST;
+    p->max_neighbors = 0;
 }
 
 const char *sphst_last_error(void) { return g_error.c_str(); }
@@ -257,6 +265,10 @@ int sphst_create_case(const sphst_case_params *params, sphst_case *out) {
     if (P.limiter < 0 || P.limiter > 2 || P.grad_mode < 0 || P.grad_mode > 1 ||
         P.penalty_form < 0 || P.penalty_form > 1 || P.loop_mode < 0 || P.loop_mode > 1) {
         set_error("unknown reading or loop flag");
+        return SPHST_ERR_INVALID_ARG;
+    }
+    if (P.nbr_mode < 0 || P.nbr_mode > 1 || P.max_neighbors < 0 || P.max_neighbors > 1024) {
+        set_error("nbr_mode must be 0 or 1 and max_neighbors 0..1024");
         return SPHST_ERR_INVALID_ARG;
     }
     if (P.grid_pad < 1 || P.grid_pad > 64 || P.block < 32 || P.block > 256 || P.block % 32) {

@@ -27,6 +27,9 @@ template <typename T> struct EngineT : Engine {
     uint32_t *id = nullptr, *key = nullptr, *rank = nullptr, *perm = nullptr;
     // cell table + scan scratch
     uint32_t *starts = nullptr, *block_sums = nullptr;
+    uint32_t *nbr = nullptr, *nbr_cnt = nullptr;   // neighbour lists (ELL per case) and counts
+    int64_t nbr_total = 0;
+    bool any_list = false;
     // cases
     CaseDesc *d_desc = nullptr;
     CaseState *d_state = nullptr;
@@ -101,7 +104,17 @@ template <typename T> struct EngineT : Engine {
             n_tiles += (r->n + block - 1) / block;
             max_case_n = std::max(max_case_n, r->n);
             any_tvf = any_tvf || d.tvf_on;
+            if (d.nbr_mode == 0) {
+                d.nbr_base = nbr_total;
+                nbr_total += (int64_t)d.nbr_k * r->n;
+                any_list = true;
+                h_desc[c] = d;
+            }
             if (r->P.loop_mode == SPHST_LOOP_HOST) loop_mode = SPHST_LOOP_HOST;
+        }
+        if (any_list && n >= ((int64_t)1 << (32 - NBR_SHIFT))) {
+            set_error("more than 2^26 particles in one engine: use the cell-walk neighbour mode");
+            return SPHST_ERR_UNSUPPORTED;
         }
         if (n >= (int64_t)0xffffffffll || table_total + 1 >= (int64_t)0xffffffffll) {
             set_error("engine too large for 32-bit particle or cell indices");
@@ -123,6 +136,7 @@ template <typename T> struct EngineT : Engine {
         size_t o_tiles = take(sizeof(Tile) * (size_t)std::max<int64_t>(n_tiles, 1));
         size_t o_flag = take(64);
         size_t o_read = take((size_t)std::max<int64_t>(max_case_n, 1) * 3 * sizeof(double));
+        size_t o_nbr = take((size_t)std::max<int64_t>(nbr_total, 1) * 4), o_ncnt = take(nn * 4);
         cudaError_t e = cudaMalloc(&arena, off);
         if (e != cudaSuccess) {
             arena = nullptr;
@@ -141,6 +155,8 @@ template <typename T> struct EngineT : Engine {
         d_desc = (CaseDesc *)(b + o_desc); d_state = (CaseState *)(b + o_state);
         d_tiles = (Tile *)(b + o_tiles); d_loop_flag = (int *)(b + o_flag);
         d_read = (double *)(b + o_read);
+        nbr = (uint32_t *)(b + o_nbr);
+        nbr_cnt = (uint32_t *)(b + o_ncnt);
         SPH_CK(cudaMemsetAsync(arena, 0, off, stream));
         // tiles
         std::vector<Tile> tiles;
@@ -215,7 +231,7 @@ template <typename T> struct EngineT : Engine {
         const int nthr = 256;
         const int cgrid = (ncases + 127) / 128;
         const int pgrid = (int)((n + nthr - 1) / nthr);
-        SweepArgs a{d_tiles, d_desc, d_state, starts};
+        SweepArgs a{d_tiles, d_desc, d_state, starts, nbr, nbr_cnt};
         SPH_CK(cudaMemsetAsync(starts, 0, (size_t)(table_total + 1) * 4, stream));
         k_reset_vmax<<<cgrid, 128, 0, stream>>>(ncases, d_state);
         k_vmax<T><<<(unsigned)n_tiles, block, 0, stream>>>(d_tiles, d_desc, d_state, pos, vel);
@@ -230,6 +246,7 @@ template <typename T> struct EngineT : Engine {
         k_cell_sort<<<(unsigned)((table_total + nthr - 1) / nthr), nthr, 0, stream>>>(table_total, starts, id, perm);
         k_gather<T><<<pgrid, nthr, 0, stream>>>(n, perm, pos, vel, drho, id, snap, vel_new, drho_old, rank);
         k_copy_back<T><<<pgrid, nthr, 0, stream>>>(n, snap, vel_new, drho_old, rank, pos, vel, drho, id);
+        if (any_list) k_build_list<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, nbr, nbr_cnt);
         if (any_tvf) k_sweep_M<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, bmat);
         k_sweep_V<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, vel, bmat, acc_visc, pos);
         SPH_CK(cudaGetLastError());
@@ -237,7 +254,7 @@ template <typename T> struct EngineT : Engine {
     }
 
     int launch_body(cudaGraphConditionalHandle h, int use_handle) {
-        SweepArgs a{d_tiles, d_desc, d_state, starts};
+        SweepArgs a{d_tiles, d_desc, d_state, starts, nbr, nbr_cnt};
         k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, h, use_handle);
         k_sweep_A<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, gradC);
         k_sweep_B<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, vel, gradC, acc_visc, vel_new, drho_old);
@@ -341,7 +358,7 @@ template <typename T> struct EngineT : Engine {
         const int pgrid = (int)((n + nthr - 1) / nthr);
         const int64_t ns = table_total + 1;
         const unsigned nb = (unsigned)((ns + SCAN_ITEMS - 1) / SCAN_ITEMS);
-        SweepArgs a{d_tiles, d_desc, d_state, starts};
+        SweepArgs a{d_tiles, d_desc, d_state, starts, nbr, nbr_cnt};
         timed(1, 3, [&] {
             k_reset_vmax<<<cgrid, 128, 0, stream>>>(ncases, d_state);
             k_vmax<T><<<(unsigned)n_tiles, block, 0, stream>>>(d_tiles, d_desc, d_state, pos, vel);
@@ -357,6 +374,9 @@ template <typename T> struct EngineT : Engine {
             k_cell_sort<<<(unsigned)((table_total + nthr - 1) / nthr), nthr, 0, stream>>>(table_total, starts, id, perm);
             k_gather<T><<<pgrid, nthr, 0, stream>>>(n, perm, pos, vel, drho, id, snap, vel_new, drho_old, rank);
             k_copy_back<T><<<pgrid, nthr, 0, stream>>>(n, snap, vel_new, drho_old, rank, pos, vel, drho, id);
+        });
+        timed(0, any_list ? 1 : 0, [&] {
+            if (any_list) k_build_list<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, nbr, nbr_cnt);
         });
         timed(1, any_tvf ? 2 : 1, [&] {
             if (any_tvf) k_sweep_M<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, bmat);

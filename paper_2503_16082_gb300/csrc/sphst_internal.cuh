@@ -99,6 +99,9 @@ struct CaseDesc {
     double rho0[2], eta[2];
     int64_t max_substeps;
     double cfl_ad, cfl_ac;
+    int32_t nbr_mode;          // 0: neighbour list built per advection step; 1: cell walk
+    int32_t nbr_k;             // list capacity per particle
+    int64_t nbr_base;          // first list word of this case
     CasePhys<float> pf;
     CasePhys<double> pd;
 };
@@ -125,7 +128,7 @@ struct CaseState {
 };
 
 enum : int32_t { DEV_OK = 0, DEV_ERR_NONFINITE = 1, DEV_ERR_DOMAIN = 2, DEV_ERR_COINCIDENT = 3,
-                 DEV_ERR_STALLED = 4 };
+                 DEV_ERR_STALLED = 4, DEV_ERR_NBR_OVERFLOW = 5 };
 
 struct Tile { int32_t c; int32_t n; int64_t begin; };   // one block: n particles of case c
 

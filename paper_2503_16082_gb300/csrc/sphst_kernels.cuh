@@ -32,6 +32,18 @@ template <> __device__ __forceinline__ V4<float> ld4<float>(const V4<float> *p) 
 
 __device__ __forceinline__ double bits_to_d(unsigned long long b) { return __longlong_as_double((long long)b); }
 
+// explicitly rounded operations for the pair geometry, so that the cell walk
+// and the neighbour list produce bitwise-identical r_ij and r^2
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <typename T, int D> __device__ __forceinline__ T norm2(T x, T y, T z) {
+    return D == 3 ? fma_rn(x, x, fma_rn(y, y, mul_rn(z, z))) : fma_rn(x, x, mul_rn(y, y));
+}
+
 // |v|^2 in FP64 with a fixed operation order and no contraction
 template <typename T> __device__ __forceinline__ double speed2(const V4<T> &v, int dim) {
     double x = (double)v.x, y = (double)v.y, z = (double)v.z;
@@ -74,22 +86,22 @@ __device__ __forceinline__ bool walk(const CaseDesc &d, const CasePhys<T> &cp,
     for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz) {
         const int nz = cz + oz;
         if (D == 3 && (nz < 0 || nz >= d.ncell[2])) continue;
-        const T sz = D == 3 ? si.z - T(oz) * cs : T(0);
+        const T sz = D == 3 ? sub_rn(si.z, mul_rn(T(oz), cs)) : T(0);
         for (int oy = -1; oy <= 1; ++oy) {
             const int ny = cy + oy;
             if (ny < 0 || ny >= d.ncell[1]) continue;
-            const T sy = si.y - T(oy) * cs;
+            const T sy = sub_rn(si.y, mul_rn(T(oy), cs));
             for (int ox = -1; ox <= 1; ++ox) {
                 const int nx = cx + ox;
                 if (nx < 0 || nx >= d.ncell[0]) continue;
-                const T sx = si.x - T(ox) * cs;
+                const T sx = sub_rn(si.x, mul_rn(T(ox), cs));
                 const uint32_t m = toff + morton<D>(nx, ny, nz);
                 const uint32_t b = __ldg(starts + m), e = __ldg(starts + m + 1);
                 for (uint32_t j = b; j < e; ++j) {
                     const V4<T> sj = ld4(snap + j);
-                    const T rx = sx - sj.x, ry = sy - sj.y;
-                    const T rz = D == 3 ? sz - sj.z : T(0);
-                    const T r2 = D == 3 ? rx * rx + ry * ry + rz * rz : rx * rx + ry * ry;
+                    const T rx = sub_rn(sx, sj.x), ry = sub_rn(sy, sj.y);
+                    const T rz = D == 3 ? sub_rn(sz, sj.z) : T(0);
+                    const T r2 = norm2<T, D>(rx, ry, rz);
                     if (r2 < R2 && j != (uint32_t)i) {
                         if (r2 > T(0)) f(j, sj, rx, ry, rz, r2);
                         else coincident = true;
@@ -99,6 +111,55 @@ __device__ __forceinline__ bool walk(const CaseDesc &d, const CasePhys<T> &cp,
         }
     }
     return coincident;
+}
+
+// Neighbour list of the frozen configuration (ELL layout per case: entry k of
+// particle i at nbr[nbr_base + k * n_case + (i - p_begin)], so a warp's 32
+// lanes read 32 consecutive words).  An entry is j << 6 | cell code, the code
+// holding (o + 1) per axis in 2 bits, o the neighbour cell's offset.  The
+// list keeps the cell-walk order, so both visit neighbours identically.
+constexpr uint32_t NBR_SHIFT = 6;
+template <int D>
+__device__ __forceinline__ uint32_t cell_code(int ox, int oy, int oz) {
+    return (uint32_t)(ox + 1) | ((uint32_t)(oy + 1) << 2) | (D == 3 ? ((uint32_t)(oz + 1) << 4) : 0u);
+}
+
+template <typename T, int D, typename F>
+__device__ __forceinline__ void walk_list(const CaseDesc &d, const CasePhys<T> &cp,
+                                          const uint32_t *__restrict__ nbr,
+                                          const uint32_t *__restrict__ cnt,
+                                          const V4<T> *__restrict__ snap, int64_t i,
+                                          const V4<T> &si, F &&f) {
+    const int64_t stride = d.p_end - d.p_begin;
+    const uint32_t *base = nbr + d.nbr_base + (i - d.p_begin);
+    const uint32_t c = cnt[i];
+    const T cs = cp.cs;
+    for (uint32_t k = 0; k < c; ++k) {
+        const uint32_t e = __ldg(base + (int64_t)k * stride);
+        const uint32_t j = e >> NBR_SHIFT;
+        const T ox = T((int)(e & 3u) - 1), oy = T((int)((e >> 2) & 3u) - 1);
+        const V4<T> sj = ld4(snap + j);
+        const T rx = sub_rn(sub_rn(si.x, mul_rn(ox, cs)), sj.x);
+        const T ry = sub_rn(sub_rn(si.y, mul_rn(oy, cs)), sj.y);
+        T rz = T(0);
+        if (D == 3) rz = sub_rn(sub_rn(si.z, mul_rn(T((int)((e >> 4) & 3u) - 1), cs)), sj.z);
+        const T r2 = norm2<T, D>(rx, ry, rz);
+        f(j, sj, rx, ry, rz, r2);
+    }
+}
+
+// neighbours of i from the list (LIST) or from the cell walk
+template <bool LIST, typename T, int D, typename F>
+__device__ __forceinline__ bool neighbors(const CaseDesc &d, const CasePhys<T> &cp,
+                                          const uint32_t *starts, const uint32_t *nbr,
+                                          const uint32_t *cnt, const V4<T> *snap, int64_t i,
+                                          const V4<T> &si, uint32_t pki, F &&f) {
+    if constexpr (LIST) {
+        walk_list<T, D>(d, cp, nbr, cnt, snap, i, si, f);
+        return false;
+    } else {
+        return walk<T, D>(d, cp, starts, snap, i, si, pki, f);
+    }
 }
 
 // kernel radial derivative and unit vector of one pair
@@ -454,15 +515,15 @@ static __global__ void k_adv_end(int ncases, CaseState *st) {
 
 // ================================================================= sweeps
 // ---- M: correction matrix of Eq. 15, B_i = -(sum_j r_ij (x) grad_i W_ij V_j)^-1
-template <typename T, int D>
+template <bool LIST, typename T, int D>
 __device__ __forceinline__ void sweep_M(const CaseDesc &d, const CasePhys<T> &cp, int64_t i,
-                                        const uint32_t *starts, const V4<T> *snap, const T *drho,
+                                        const uint32_t *starts, const uint32_t *nbr, const uint32_t *cnt, const V4<T> *snap, const T *drho,
                                         V4<T> *bmat, int32_t *status) {
     const V4<T> si = ld4(snap + i);
     const uint32_t pki = w_bits(si.w);
     if (phase_of(pki) == PH_WALL) return;
     T m00 = 0, m01 = 0, m02 = 0, m11 = 0, m12 = 0, m22 = 0;
-    const bool coinc = walk<T, D>(d, cp, starts, snap, i, si, pki,
+    const bool coinc = neighbors<LIST, T, D>(d, cp, starts, nbr, cnt, snap, i, si, pki,
         [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
             const PairGeo<T> g = geo(cp, r2);
             const uint32_t kj = phase_of(w_bits(sj.w));
@@ -496,9 +557,9 @@ __device__ __forceinline__ void sweep_M(const CaseDesc &d, const CasePhys<T> &cp
 }
 
 // ---- V: viscous acceleration (Eq. 13) and transport shift (Eq. 14)
-template <typename T, int D>
+template <bool LIST, typename T, int D>
 __device__ __forceinline__ void sweep_V(const CaseDesc &d, const CasePhys<T> &cp, int64_t i,
-                                        const uint32_t *starts, const V4<T> *snap, const T *drho,
+                                        const uint32_t *starts, const uint32_t *nbr, const uint32_t *cnt, const V4<T> *snap, const T *drho,
                                         const V4<T> *vel, const V4<T> *bmat, V4<T> *acc_visc,
                                         V4<T> *pos, int32_t *status) {
     const V4<T> si = ld4(snap + i);
@@ -512,7 +573,7 @@ __device__ __forceinline__ void sweep_V(const CaseDesc &d, const CasePhys<T> &cp
     V4<T> Bi0 = {0, 0, 0, 0}, Bi1 = {0, 0, 0, 0};
     if (tvf) { Bi0 = bmat[2 * i]; Bi1 = bmat[2 * i + 1]; }
     T ax = 0, ay = 0, az = 0, sx = 0, sy = 0, sz = 0;
-    const bool coinc = walk<T, D>(d, cp, starts, snap, i, si, pki,
+    const bool coinc = neighbors<LIST, T, D>(d, cp, starts, nbr, cnt, snap, i, si, pki,
         [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
             const PairGeo<T> g = geo(cp, r2);
             const uint32_t kj = phase_of(w_bits(sj.w));
@@ -556,9 +617,9 @@ __device__ __forceinline__ void sweep_V(const CaseDesc &d, const CasePhys<T> &cp
 }
 
 // ---- A: colour gradient, Eq. 22 (only pairs of different fluids contribute)
-template <typename T, int D>
+template <bool LIST, typename T, int D>
 __device__ __forceinline__ void sweep_A(const CaseDesc &d, const CasePhys<T> &cp, int64_t i,
-                                        const uint32_t *starts, const V4<T> *snap, const T *drho,
+                                        const uint32_t *starts, const uint32_t *nbr, const uint32_t *cnt, const V4<T> *snap, const T *drho,
                                         V4<T> *gradC) {
     const V4<T> si = ld4(snap + i);
     const uint32_t pki = w_bits(si.w);
@@ -568,7 +629,7 @@ __device__ __forceinline__ void sweep_A(const CaseDesc &d, const CasePhys<T> &cp
         const uint32_t other = ki ^ 1u;
         const T two_phi = cp.two_phi[ki];
         const T m_o = cp.mass[other], rho0_o = cp.rho0[other];
-        walk<T, D>(d, cp, starts, snap, i, si, pki,
+        neighbors<LIST, T, D>(d, cp, starts, nbr, cnt, snap, i, si, pki,
             [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
                 if (phase_of(w_bits(sj.w)) != other) return;
                 const PairGeo<T> gg = geo(cp, r2);
@@ -584,9 +645,9 @@ __device__ __forceinline__ void sweep_A(const CaseDesc &d, const CasePhys<T> &cp
 }
 
 // ---- B: pressure + surface tension + kick
-template <typename T, int D>
+template <bool LIST, typename T, int D>
 __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &cp, T dt,
-                                          int64_t i, const uint32_t *starts, const V4<T> *snap,
+                                          int64_t i, const uint32_t *starts, const uint32_t *nbr, const uint32_t *cnt, const V4<T> *snap,
                                           const T *drho, const V4<T> *vel, const V4<T> *gradC,
                                           const V4<T> *acc_visc, V4<T> *vel_new, T *drho_old,
                                           uint32_t *phase_out) {
@@ -609,7 +670,7 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
     const T c0 = cp.c0, inv_c0 = cp.inv_c0;
     const T xg = cp.xi * cp.gamma;
     T apx = 0, apy = 0, apz = 0, asx = 0, asy = 0, asz = 0;
-    walk<T, D>(d, cp, starts, snap, i, si, pki,
+    neighbors<LIST, T, D>(d, cp, starts, nbr, cnt, snap, i, si, pki,
         [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
             const PairGeo<T> g = geo(cp, r2);
             const T ex = rx * g.inv_r, ey = ry * g.inv_r, ez = D == 3 ? rz * g.inv_r : T(0);
@@ -697,9 +758,9 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
 }
 
 // ---- C: continuity (Eq. 6) with v* (normal component -U*) + drift
-template <typename T, int D>
+template <bool LIST, typename T, int D>
 __device__ __forceinline__ void sweep_C(const CaseDesc &d, const CasePhys<T> &cp, T dt, int64_t i,
-                                        const uint32_t *starts, const V4<T> *snap,
+                                        const uint32_t *starts, const uint32_t *nbr, const uint32_t *cnt, const V4<T> *snap,
                                         const T *drho_old, const V4<T> *vel_new, T *drho,
                                         V4<T> *vel, V4<T> *pos) {
     const V4<T> si = ld4(snap + i);
@@ -712,7 +773,7 @@ __device__ __forceinline__ void sweep_C(const CaseDesc &d, const CasePhys<T> &cp
     const V4<T> vi = vel_new[i];
     const T c0 = cp.c0;
     T s = 0;
-    walk<T, D>(d, cp, starts, snap, i, si, pki,
+    neighbors<LIST, T, D>(d, cp, starts, nbr, cnt, snap, i, si, pki,
         [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
             const PairGeo<T> g = geo(cp, r2);
             const uint32_t kj = phase_of(w_bits(sj.w));
@@ -747,7 +808,61 @@ struct SweepArgs {
     const CaseDesc *desc;
     CaseState *st;
     const uint32_t *starts;
+    const uint32_t *nbr;
+    const uint32_t *cnt;
 };
+
+// calls body.template operator()<LIST, D>() for the case's dimension and
+// neighbour source (block-uniform branch)
+#define SPH_DISPATCH(d, CALL)                                      \
+    do {                                                           \
+        if ((d).dim == 3) {                                        \
+            if ((d).nbr_mode == 0) { constexpr bool LIST = true; constexpr int D = 3; CALL; } \
+            else { constexpr bool LIST = false; constexpr int D = 3; CALL; }                   \
+        } else {                                                   \
+            if ((d).nbr_mode == 0) { constexpr bool LIST = true; constexpr int D = 2; CALL; } \
+            else { constexpr bool LIST = false; constexpr int D = 2; CALL; }                   \
+        }                                                          \
+    } while (0)
+
+// ---- L: neighbour list of the frozen configuration (fluid particles only)
+template <typename T, int D>
+__device__ __forceinline__ void build_list(const CaseDesc &d, const CasePhys<T> &cp, int64_t i,
+                                           const uint32_t *starts, const V4<T> *snap,
+                                           uint32_t *nbr, uint32_t *cnt, int32_t *status) {
+    const V4<T> si = ld4(snap + i);
+    const uint32_t pki = w_bits(si.w);
+    if (phase_of(pki) == PH_WALL) { cnt[i] = 0; return; }
+    const int cx = cell_x<D>(pki), cy = cell_y<D>(pki), cz = cell_z<D>(pki);
+    const int64_t stride = d.p_end - d.p_begin;
+    uint32_t *base = nbr + d.nbr_base + (i - d.p_begin);
+    const uint32_t kmax = (uint32_t)d.nbr_k;
+    uint32_t c = 0;
+    bool overflow = false;
+    const bool coinc = walk<T, D>(d, cp, starts, snap, i, si, pki,
+        [&](uint32_t j, const V4<T> &sj, T, T, T, T) {
+            if (c >= kmax) { overflow = true; return; }
+            const uint32_t pkj = w_bits(sj.w);
+            const uint32_t code = cell_code<D>(cell_x<D>(pkj) - cx, cell_y<D>(pkj) - cy,
+                                               cell_z<D>(pkj) - cz);
+            base[(int64_t)c * stride] = (j << NBR_SHIFT) | code;
+            ++c;
+        });
+    cnt[i] = c;
+    if (coinc) atomicCAS(status, 0, DEV_ERR_COINCIDENT);
+    if (overflow) atomicCAS(status, 0, DEV_ERR_NBR_OVERFLOW);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_build_list(SweepArgs a, const V4<T> *snap, uint32_t *nbr, uint32_t *cnt) {
+    const Tile t = a.tiles[blockIdx.x];
+    if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
+    const CaseDesc &d = a.desc[t.c];
+    if (d.nbr_mode != 0) return;
+    const int64_t i = t.begin + threadIdx.x;
+    if (d.dim == 3) build_list<T, 3>(d, phys<T>(d), i, a.starts, snap, nbr, cnt, &a.st[t.c].status);
+    else build_list<T, 2>(d, phys<T>(d), i, a.starts, snap, nbr, cnt, &a.st[t.c].status);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_sweep_M(SweepArgs a, const V4<T> *snap, const T *drho, V4<T> *bmat) {
@@ -756,8 +871,8 @@ __global__ void __launch_bounds__(256) k_sweep_M(SweepArgs a, const V4<T> *snap,
     const CaseDesc &d = a.desc[t.c];
     if (!d.tvf_on) return;
     const int64_t i = t.begin + threadIdx.x;
-    if (d.dim == 3) sweep_M<T, 3>(d, phys<T>(d), i, a.starts, snap, drho, bmat, &a.st[t.c].status);
-    else sweep_M<T, 2>(d, phys<T>(d), i, a.starts, snap, drho, bmat, &a.st[t.c].status);
+    SPH_DISPATCH(d, (sweep_M<LIST, T, D>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, bmat,
+                                          &a.st[t.c].status)));
 }
 
 template <typename T>
@@ -767,8 +882,8 @@ __global__ void __launch_bounds__(256) k_sweep_V(SweepArgs a, const V4<T> *snap,
     if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
     const CaseDesc &d = a.desc[t.c];
     const int64_t i = t.begin + threadIdx.x;
-    if (d.dim == 3) sweep_V<T, 3>(d, phys<T>(d), i, a.starts, snap, drho, vel, bmat, acc_visc, pos, &a.st[t.c].status);
-    else sweep_V<T, 2>(d, phys<T>(d), i, a.starts, snap, drho, vel, bmat, acc_visc, pos, &a.st[t.c].status);
+    SPH_DISPATCH(d, (sweep_V<LIST, T, D>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, vel, bmat,
+                                          acc_visc, pos, &a.st[t.c].status)));
 }
 
 template <typename T>
@@ -777,8 +892,7 @@ __global__ void __launch_bounds__(256) k_sweep_A(SweepArgs a, const V4<T> *snap,
     if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
     const CaseDesc &d = a.desc[t.c];
     const int64_t i = t.begin + threadIdx.x;
-    if (d.dim == 3) sweep_A<T, 3>(d, phys<T>(d), i, a.starts, snap, drho, gradC);
-    else sweep_A<T, 2>(d, phys<T>(d), i, a.starts, snap, drho, gradC);
+    SPH_DISPATCH(d, (sweep_A<LIST, T, D>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, gradC)));
 }
 
 template <typename T>
@@ -793,8 +907,8 @@ __global__ void __launch_bounds__(256) k_sweep_B(SweepArgs a, const V4<T> *snap,
     if ((int)threadIdx.x < t.n) {
         const int64_t i = t.begin + threadIdx.x;
         const T dt = (T)a.st[t.c].dt;
-        if (d.dim == 3) v2 = sweep_B<T, 3>(d, phys<T>(d), dt, i, a.starts, snap, drho, vel, gradC, acc_visc, vel_new, drho_old, &ph);
-        else v2 = sweep_B<T, 2>(d, phys<T>(d), dt, i, a.starts, snap, drho, vel, gradC, acc_visc, vel_new, drho_old, &ph);
+        SPH_DISPATCH(d, (v2 = sweep_B<LIST, T, D>(d, phys<T>(d), dt, i, a.starts, a.nbr, a.cnt, snap, drho,
+                                                   vel, gradC, acc_visc, vel_new, drho_old, &ph)));
     }
     unsigned long long m0 = ph == 0 ? (unsigned long long)__double_as_longlong(v2) : 0ull;
     unsigned long long m1 = ph == 1 ? (unsigned long long)__double_as_longlong(v2) : 0ull;
@@ -814,8 +928,8 @@ __global__ void __launch_bounds__(256) k_sweep_C(SweepArgs a, const V4<T> *snap,
     const CaseDesc &d = a.desc[t.c];
     const int64_t i = t.begin + threadIdx.x;
     const T dt = (T)a.st[t.c].dt;
-    if (d.dim == 3) sweep_C<T, 3>(d, phys<T>(d), dt, i, a.starts, snap, drho_old, vel_new, drho, vel, pos);
-    else sweep_C<T, 2>(d, phys<T>(d), dt, i, a.starts, snap, drho_old, vel_new, drho, vel, pos);
+    SPH_DISPATCH(d, (sweep_C<LIST, T, D>(d, phys<T>(d), dt, i, a.starts, a.nbr, a.cnt, snap, drho_old,
+                                          vel_new, drho, vel, pos)));
 }
 
 // ------------------------------------------------------------ read-back

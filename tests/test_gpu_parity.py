@@ -90,9 +90,10 @@ def test_keys_order_and_counts_bit_exact(dim, precision):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
-def test_fp64_one_advection_step(dim):
+@pytest.mark.parametrize("nbr", ["list", "cells"])
+def test_fp64_one_advection_step(dim, nbr):
     case = small(dim)
-    g, o, info, oinfo, pos0, kind = run_both(case, 64, 1)
+    g, o, info, oinfo, pos0, kind = run_both(case, 64, 1, nbr_mode=S.NBR_LIST if nbr == "list" else S.NBR_CELLS)
     assert info["n_sub"] == oinfo["n_sub"] > 5
     for key in ("pos", "vel", "rho", "gradC", "acc_visc"):
         assert rel_err(g, o, pos0, kind, key, case) <= 1e-12, key
@@ -173,3 +174,38 @@ def test_profile_step_matches_graph_step():
     assert np.array_equal(S.read_fields(h1, S.FIELD_VEL, 2), S.read_fields(h2, S.FIELD_VEL, 2))
     S.destroy(h1)
     S.destroy(h2)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("precision", [32, 64])
+def test_list_and_cell_walk_agree(dim, precision):
+    # the neighbour list keeps the cell-walk order and the pair geometry is
+    # computed with explicitly rounded operations, so the two sources agree to
+    # rounding (the compiler may still contract the pair sums differently in
+    # the two call sites)
+    case = small(dim)
+    out = []
+    for mode in (S.NBR_LIST, S.NBR_CELLS):
+        h = gpu_case(case, precision, nbr_mode=mode)
+        info = S.step(h, 2)
+        out.append(([S.read_fields(h, f, dim) for f in (S.FIELD_POS, S.FIELD_VEL, S.FIELD_RHO, S.FIELD_GRADC)],
+                    info["n_sub"]))
+        S.destroy(h)
+    assert out[0][1] == out[1][1]
+    pos0 = case.flat()[0][:, :dim]
+    tol = 1e-12 if precision == 64 else 1e-4
+    for k, (a, b) in enumerate(zip(out[0][0], out[1][0])):
+        if k == 0:
+            a, b = a - pos0, b - pos0
+        if k == 2:
+            a, b = a - np.round(a), b - np.round(a)
+        scale = np.abs(b).max()
+        assert np.abs(a - b).max() <= tol * scale, k
+
+
+def test_neighbor_overflow_is_reported():
+    case = small(3)
+    h = gpu_case(case, 32, max_neighbors=8)
+    info = S.step(h, 1, check=False)
+    assert info["rc"] == S.ERR_NEIGHBORS
+    S.destroy(h)
