@@ -224,6 +224,29 @@ int sphst_set_stream(sphst_case c, void *cuda_stream);
 #define SPHST_PROFILE_GROUPS 6
 int sphst_profile_step(sphst_case c, double *kernel_ms, int64_t *launches);
 
+/* Cell order without allocating (the paper has no counterpart: this serves
+ * callers that may not allocate device memory -- a framework whose memory
+ * pool owns every allocation, or a real-time caller that must not allocate
+ * after start-up).  It computes what one rebuild computes for the particle
+ * order: for n particles at pos_dev (DEVICE pointer, n x 3 doubles, the
+ * unused coordinate of 2D ignored) on the grid (origin3, cell_size, ncell3
+ * as returned by sphst_debug_grid), keys_dev[k] receives the Morton code of
+ * the k-th particle in canonical order and order_dev[k] its index in pos_dev
+ * (the order sorts by (Morton code, index)).  keys_dev and order_dev are
+ * DEVICE buffers of n entries owned by the caller; cuda_stream (a
+ * cudaStream_t as void*, NULL for the default stream) runs the kernels and
+ * is synchronised before return.  All intermediate data live in a fixed
+ * device array of the library (about 8 MB per GPU, kept until exit): at most
+ * 524,288 particles and 2^20 Morton cells (2^(dim*bits) with 2^bits >= the
+ * largest ncell); larger inputs return INVALID_ARG.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress), so
+ * make the first call on each device before any stream capture.  Calls that
+ * overlap on the GPU share the array and race.  Errors: INVALID_ARG, DOMAIN
+ * (a particle outside the grid; it is clamped to the nearest cell), CUDA. */
+int sphst_cell_order_noalloc(int32_t dim, int64_t n, const double *pos_dev,
+                             const double *origin3, double cell_size, const int32_t *ncell3,
+                             uint64_t *keys_dev, int64_t *order_dev, void *cuda_stream);
+
 /* ------------------------------------------------------------- batches   */
 /* A batch advances many independent cases together: their particles share
  * one set of device arrays, one segmented cell list (the case index selects

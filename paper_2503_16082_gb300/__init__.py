@@ -79,6 +79,8 @@ EXPORTS = {
     "sphst_debug_neighbor_counts": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "sphst_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sphst_profile_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sphst_cell_order_noalloc": (C.c_int, [C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_double,
+                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sphst_batch_create": (C.c_int, [C.c_int32, C.POINTER(C.c_void_p)]),
     "sphst_batch_add": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sphst_batch_remove": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -224,6 +226,20 @@ def profile_step(case) -> dict:
     nl = np.zeros(len(PROFILE_GROUPS), dtype=np.int64)
     _check(load().sphst_profile_step(case, ms.ctypes.data, nl.ctypes.data), "profile_step")
     return {g: (float(ms[k]), int(nl[k])) for k, g in enumerate(PROFILE_GROUPS)}
+
+
+def cell_order_noalloc(dim: int, n: int, pos_dev_ptr: int, origin, cell_size: float, ncell,
+                       keys_dev_ptr: int, order_dev_ptr: int, cuda_stream: int = 0) -> None:
+    """Canonical cell order of n particles already on the device, computed
+    without any device allocation (all buffers are the caller's; the
+    library's fixed scratch array holds the intermediates).  Arguments are
+    raw device pointers, e.g. ``tensor.data_ptr()``."""
+    origin = np.ascontiguousarray(origin, dtype=np.float64)
+    ncell = np.ascontiguousarray(ncell, dtype=np.int32)
+    _check(load().sphst_cell_order_noalloc(dim, n, C.c_void_p(pos_dev_ptr), origin.ctypes.data,
+                                           cell_size, ncell.ctypes.data, C.c_void_p(keys_dev_ptr),
+                                           C.c_void_p(order_dev_ptr), C.c_void_p(cuda_stream)),
+           "cell_order_noalloc")
 
 
 def batch_create(precision: int = 32):

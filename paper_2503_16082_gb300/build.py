@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsphst.so")
-SOURCES = ["sphst_api.cu", "sphst_f32.cu", "sphst_f64.cu"]
+SOURCES = ["sphst_api.cu", "sphst_f32.cu", "sphst_f64.cu", "sphst_noalloc.cu"]
 HEADERS = ["sphst_internal.cuh", "sphst_kernels.cuh", "sphst_engine.cuh", "sphst_engine_impl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
@@ -33,7 +33,10 @@ def _stale(target: str, deps) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile and link; SPHST_NVCC_DEFINES (e.g. "-DSPHST_SWEEP_MINB=4")
+    adds tuning defines (pass force=True when it changes)."""
     os.makedirs(BUILD, exist_ok=True)
+    extra = os.environ.get("SPHST_NVCC_DEFINES", "").split()
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(HERE, "..", "include", "sphst.h")]
     objs = []
     jobs = []
@@ -42,7 +45,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         obj = os.path.join(BUILD, s.replace(".cu", ".o"))
         objs.append(obj)
         if force or _stale(obj, [src] + hdrs):
-            jobs.append([nvcc(), *FLAGS, *ARCH, "-c", src, "-o", obj])
+            jobs.append([nvcc(), *FLAGS, *extra, *ARCH, "-c", src, "-o", obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
