@@ -282,6 +282,105 @@ def run_reference(args, dist: Dist):
                       f"set-up + {SAMPLE_SUBSTEPS} acoustic substeps of the FP64 oracle"}
 
 
+# ------------------------------------------------------ batched and served
+def run_batch(args):
+    """Config 4: independent 2D/3D droplet cases advanced together in one
+    engine (one graph per advection step), against the same cases stepped
+    one at a time through the single-case path."""
+    import torch
+
+    import paper_2503_16082_gb300 as S
+
+    torch.cuda.set_device(0)
+    specs = sphcases.batch_cases(args.cases)
+    cases = [sp.build() for sp in specs]
+    # coarse 3D drops with strong tension cluster beyond the default list
+    # capacity of 128 neighbours; the batch uses 192
+    hs = [S.case_from_spec(c, precision=args.precision, max_neighbors=192 if c.dim == 3 else 0)
+          for c in cases]
+    b = S.batch_create(args.precision)
+    for h in hs:
+        S.batch_add(b, h)
+    S.batch_step(b, args.warmup)
+    sub0 = [S.case_info(h)["n_sub"] for h in hs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S.batch_step(b, args.steps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    units = sum(c.n_fluid * (S.case_info(h)["n_sub"] - s0) for c, h, s0 in zip(cases, hs, sub0))
+    statuses = [S.case_info(h)["status"] for h in hs]
+    for h in hs:
+        S.batch_remove(b, h)
+        S.destroy(h)
+    S.batch_destroy(b)
+    # the single-case path on a sample of the same cases
+    k = min(args.plain_sample, len(cases))
+    punits, psecs = 0, 0.0
+    for c in cases[:k]:
+        h = S.case_from_spec(c, precision=args.precision, max_neighbors=192 if c.dim == 3 else 0)
+        S.step(h, args.warmup)
+        s0 = S.case_info(h)["n_sub"]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.step(h, args.steps)
+        torch.cuda.synchronize()
+        psecs += time.perf_counter() - t0
+        punits += c.n_fluid * (S.case_info(h)["n_sub"] - s0)
+        S.destroy(h)
+    line = {"metric": METRIC, "mode": "batch", "value": round(units / dt, 1), "unit": METRIC,
+            "cases": len(cases), "particles": int(sum(c.n for c in cases)),
+            "fluid_particles": int(sum(c.n_fluid for c in cases)), "steps": args.steps,
+            "warmup": args.warmup, "seconds": round(dt, 3), "failed_cases": int(sum(1 for x in statuses if x)),
+            "failed_status": {str(x): int(sum(1 for y in statuses if y == x)) for x in set(statuses) if x},
+            "failed_specs": [dict(dim=sp.dim, n=c.n, sigma=round(sp.sigma, 3), shape=sp.shape)
+                             for sp, c, x in zip(specs, cases, statuses) if x][:8],
+            "plain_single_case": {"value": round(punits / psecs, 1), "cases_sampled": k},
+            "speedup_vs_plain": round((units / dt) / (punits / psecs), 2),
+            "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
+            "config": {"workload": "batch_cases seed 20250320", "step": "one advection step of every case"}}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Config 5: Poisson arrivals of droplet cases into the continuous-batching
+    server; p50/p99 time from submission to result."""
+    import torch
+
+    import paper_2503_16082_gb300 as S
+    from paper_2503_16082_gb300 import serve
+
+    torch.cuda.set_device(0)
+    specs = sphcases.served_stream(args.requests, rate=args.rate, n_hi=args.serve_n_hi)
+    cases = [sp.build() for sp in specs]
+    srv = serve.Server(precision=args.precision, budget_bytes=args.budget_gb * 1e9)
+    srv.start()
+    t0 = time.perf_counter()
+    futs = []
+    for sp, c in zip(specs, cases):
+        delay = t0 + sp.arrival - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        futs.append(srv.submit(c, n_adv=args.serve_adv))
+    res = [f.result(timeout=3600) for f in futs]
+    wall = time.perf_counter() - t0
+    srv.stop()
+    st = srv.stats()
+    srv.close()
+    lat = np.array([r.latency for r in res])
+    line = {"metric": METRIC, "mode": "serve", "value": round(st["particle_substeps"] / wall, 1),
+            "unit": METRIC, "requests": len(res), "arrival_rate_per_s": args.rate,
+            "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
+            "p99_latency_s": round(float(np.percentile(lat, 99)), 4),
+            "gpu_busy_fraction": round(st["busy_s"] / wall, 3), "rounds": st["rounds"],
+            "failed": int(sum(1 for r in res if r.info["status"])),
+            "advection_steps_per_request": args.serve_adv, "budget_gb": args.budget_gb,
+            "particles_per_request_range": [5e3, args.serve_n_hi],
+            "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
+            "config": {"workload": "served_stream seed 20250321", "wall_s": round(wall, 2)}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -294,9 +393,22 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--nbr", default="list", choices=["list", "cells"],
                     help="neighbour source of the sweeps (list built per advection step, or cell walk)")
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"],
+                    help="single: the headline line; batch / serve: the batched and served workloads")
+    ap.add_argument("--cases", type=int, default=512)
+    ap.add_argument("--plain-sample", type=int, default=32)
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--serve-adv", type=int, default=1)
+    ap.add_argument("--serve-n-hi", type=float, default=2e6)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.mode == "batch":
+        return run_batch(args)
+    if args.mode == "serve":
+        return run_serve(args)
 
     ws, rank, local = dist_env()
     config = {"workload": args.workload, "particles": None, "fluid_particles": None,

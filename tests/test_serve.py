@@ -1,0 +1,75 @@
+"""Serving loop: admission by device-memory budget (host logic, CPU) and
+continuous batching on the GPU, where requests that arrive while others run
+join the shared batch and every result equals the same case solved alone."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import sphcases
+
+S = pytest.importorskip("paper_2503_16082_gb300")
+from paper_2503_16082_gb300 import serve  # noqa: E402
+
+
+def test_oversized_request_rejected_on_host():
+    srv = serve.Server(budget_bytes=1e6)
+    fut = srv.submit(sphcases.small_droplet(3, 16), n_adv=1)
+    with pytest.raises(S.SphstError):
+        fut.result(timeout=1)
+    assert srv.idle()
+    S.batch_destroy(srv.batch)
+
+
+def test_footprint_orders_requests():
+    srv = serve.Server(budget_bytes=1e12)
+    small = srv.footprint(sphcases.small_droplet(2, 12))
+    big = srv.footprint(sphcases.small_droplet(3, 20))
+    assert 0 < small < big
+    S.batch_destroy(srv.batch)
+
+
+@pytest.mark.gpu
+def test_results_equal_alone_and_in_the_mix():
+    specs = [sphcases.small_droplet(2, 20, R_frac=0.3, seed=1, jitter=0.1, vel_amp=0.02),
+             sphcases.small_droplet(3, 10, R_frac=0.3, seed=2, jitter=0.1, vel_amp=0.02),
+             sphcases.small_droplet(2, 26, R_frac=0.25, shape="square", sigma=0.5),
+             sphcases.small_droplet(3, 12, R_frac=0.3, shape="mode2", amp=0.15)]
+    steps = [3, 2, 4, 2]
+    srv = serve.Server(budget_bytes=1e11)
+    srv.start()
+    futs = []
+    for s, n in zip(specs, steps):          # staggered arrivals while others run
+        futs.append(srv.submit(s, n_adv=n))
+        time.sleep(0.01)
+    results = [f.result(timeout=120) for f in futs]
+    srv.stop()
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == 4 and st["p99_s"] >= st["p50_s"] > 0
+    for s, n, r in zip(specs, steps, results):
+        h = S.case_from_spec(s)
+        S.step(h, n)
+        for f in (S.FIELD_POS, S.FIELD_VEL, S.FIELD_RHO):
+            assert np.array_equal(r.fields[f], S.read_fields(h, f, s.dim))
+        assert r.info["n_adv"] == n
+        S.destroy(h)
+
+
+@pytest.mark.gpu
+def test_admission_waits_for_memory():
+    a = sphcases.small_droplet(2, 20)
+    srv = serve.Server(budget_bytes=1e12)
+    one = srv.footprint(a)
+    srv.budget = 1.5 * one                   # room for one resident case
+    f1 = srv.submit(a, n_adv=2)
+    f2 = srv.submit(a, n_adv=2)
+    srv.step()
+    assert len(srv.members) == 1 and len(srv.queue) == 1
+    srv.run_until_idle(timeout=60)
+    r1, r2 = f1.result(), f2.result()
+    assert r2.admitted >= r1.finished
+    for f in (S.FIELD_POS, S.FIELD_VEL):
+        assert np.array_equal(r1.fields[f], r2.fields[f])
+    srv.close()
