@@ -1,0 +1,92 @@
+"""Integral observables computed on the host from read-back fields.
+
+* Laplace jump (Eq. 37): mean pressure of the drop's core (r < R_eff/2)
+  minus mean pressure of the surrounding fluid farther than R_eff + 3h from
+  the drop centre, with R_eff the radius of a disc/ball of the drop's volume.
+* Oscillation period: zero crossings of the drop's shape anisotropy
+  (I_xx - I_yy in 2D, I_zz - (I_xx + I_yy)/2 in 3D, second moments about the
+  drop's centroid), mean spacing of same-direction crossings, linearly
+  interpolated.
+* Total momentum of the fluids.
+"""
+from __future__ import annotations
+
+import math
+from typing import Sequence
+
+import numpy as np
+
+
+def effective_radius(n_drop: int, dx: float, dim: int) -> float:
+    vol = n_drop * dx ** dim
+    return math.sqrt(vol / math.pi) if dim == 2 else (3.0 * vol / (4.0 * math.pi)) ** (1.0 / 3.0)
+
+
+def laplace_jump(pos, p, phase, dx: float, h: float, drop_phase: int = 0, outer_phase: int = 1):
+    """(dp, R_eff) of a drop given positions (n, dim), pressures and phase ids."""
+    dim = pos.shape[1]
+    drop = phase == drop_phase
+    c = pos[drop].mean(axis=0)
+    r = np.linalg.norm(pos - c, axis=1)
+    Reff = effective_radius(int(drop.sum()), dx, dim)
+    inner = drop & (r < 0.5 * Reff)
+    outer = (phase == outer_phase) & (r > Reff + 3.0 * h)
+    return float(p[inner].mean() - p[outer].mean()), Reff
+
+
+def anisotropy(pos, phase, drop_phase: int = 0) -> float:
+    q = pos[phase == drop_phase]
+    d = q - q.mean(axis=0)
+    if q.shape[1] == 2:
+        return float((d[:, 0] ** 2).mean() - (d[:, 1] ** 2).mean())
+    return float((d[:, 2] ** 2).mean() - 0.5 * ((d[:, 0] ** 2).mean() + (d[:, 1] ** 2).mean()))
+
+
+def period_from_signal(t: Sequence[float], s: Sequence[float]) -> float:
+    """Mean spacing of upward zero crossings of s - mean(s); nan if < 2."""
+    t = np.asarray(t, dtype=float)
+    s = np.asarray(s, dtype=float)
+    s = s - s.mean()
+    ups = []
+    for k in range(1, len(s)):
+        if s[k - 1] < 0.0 <= s[k]:
+            f = -s[k - 1] / (s[k] - s[k - 1])
+            ups.append(t[k - 1] + f * (t[k] - t[k - 1]))
+    if len(ups) < 2:
+        return float("nan")
+    return float(np.mean(np.diff(ups)))
+
+
+def momentum(vel, mass) -> np.ndarray:
+    return (np.asarray(mass)[:, None] * vel).sum(axis=0)
+
+
+def period_2d_drop(R: float, rho_drop: float, gamma: float) -> float:
+    """Eq. 35: tau = 2 pi sqrt(R^3 rho / (6 gamma)) (drop in a much lighter fluid)."""
+    return 2.0 * math.pi * math.sqrt(R ** 3 * rho_drop / (6.0 * gamma))
+
+
+def period_lamb_3d(R: float, rho_in: float, rho_out: float, gamma: float) -> float:
+    """Lamb's n = 2 mode of a drop in a second fluid: w^2 = 24 gamma / (R^3 (3 rho_in + 2 rho_out))."""
+    return 2.0 * math.pi / math.sqrt(24.0 * gamma / (R ** 3 * (3.0 * rho_in + 2.0 * rho_out)))
+
+
+def fit_period(t: Sequence[float], s: Sequence[float], guess: float, skip: float = 0.05) -> float:
+    """Period of s(t) ~ c + exp(-l t) (a cos w t + b sin w t), fitted by a grid
+    search over (w, l) around 2 pi / guess with linear least squares for
+    (a, b, c); the first `skip` fraction of the record is ignored."""
+    t = np.asarray(t, dtype=float)
+    s = np.asarray(s, dtype=float)
+    keep = t >= t[0] + skip * (t[-1] - t[0])
+    t, s = t[keep], s[keep]
+    w0 = 2.0 * math.pi / guess
+    best = (np.inf, float("nan"))
+    for w in np.linspace(0.3 * w0, 3.0 * w0, 541):
+        for lam in np.linspace(0.0, 2.0 * w0, 21):
+            e = np.exp(-lam * (t - t[0]))
+            A = np.stack([np.ones_like(t), e * np.cos(w * t), e * np.sin(w * t)], axis=1)
+            coef, res, *_ = np.linalg.lstsq(A, s, rcond=None)
+            r = float(((A @ coef - s) ** 2).sum())
+            if r < best[0]:
+                best = (r, 2.0 * math.pi / w)
+    return best[1]

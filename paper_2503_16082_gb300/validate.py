@@ -1,0 +1,135 @@
+"""Run the paper-shaped workloads on the GPU and report their observables.
+
+  python -m paper_2503_16082_gb300.validate laplace_2d [--precision 64] [--adv 500]
+  python -m paper_2503_16082_gb300.validate oscillating_3d [--periods 1.5]
+  python -m paper_2503_16082_gb300.validate impact_3d [--t-end 2]
+  python -m paper_2503_16082_gb300.validate oscillating_2d [--ratio 1000]
+
+Each prints one JSON line.  laplace_2d: Young-Laplace jump (Eq. 37)
+averaged over the last 20% of the run, against gamma / R_eff.  oscillating_*:
+period of the drop's shape anisotropy against Eq. 35 (2D, ratio >> 1), the
+equal-density textbook value (2D, ratio 1) or Lamb's n = 2 value (3D).
+impact_3d: whether the run stays finite to t_end, with its substep count.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import sphcases  # noqa: E402
+
+import paper_2503_16082_gb300 as S  # noqa: E402
+from paper_2503_16082_gb300 import observables as ob  # noqa: E402
+
+
+def laplace(args):
+    case = sphcases.laplace_2d()
+    h = S.case_from_spec(case, precision=args.precision)
+    phase = S.read_fields(h, S.FIELD_PHASE, 2)
+    samples = []
+    t0 = time.perf_counter()
+    every = 10
+    for k in range(0, args.adv, every):
+        info = S.step(h, every, check=False)
+        if info["rc"]:
+            break
+        if k >= 0.8 * args.adv:
+            dp, R = ob.laplace_jump(S.read_fields(h, S.FIELD_POS, 2), S.read_fields(h, S.FIELD_PRESSURE, 2),
+                                    phase, case.dx, case.h_factor * case.dx)
+            samples.append(dp * R / case.gamma)
+    wall = time.perf_counter() - t0
+    vmax = float(np.abs(S.read_fields(h, S.FIELD_VEL, 2)).max())
+    S.destroy(h)
+    return {"workload": "laplace_2d", "precision": args.precision, "adv": info["n_adv"],
+            "substeps": info["n_sub"], "t": info["t"], "status": info["status"],
+            "dp_R_over_gamma_mean": float(np.mean(samples)) if samples else None,
+            "dp_R_over_gamma_std": float(np.std(samples)) if samples else None,
+            "exact": 1.0, "vmax_end": vmax, "wall_s": round(wall, 2)}
+
+
+def oscillating(args, dim):
+    if dim == 3:
+        case = sphcases.oscillating_3d()
+        R, rho_in, rho_out = 0.5, 1000.0, 1.0
+        tau = ob.period_lamb_3d(R, rho_in, rho_out, case.gamma)
+    else:
+        case = sphcases.oscillating_2d(ratio=args.ratio)
+        tau = ob.period_2d_drop(0.2, 1.0, 1.0) * (math.sqrt(2.0) if args.ratio == 1 else 1.0)
+    h = S.case_from_spec(case, precision=args.precision)
+    phase = S.read_fields(h, S.FIELD_PHASE, dim)
+    ts, an = [], []
+    t0 = time.perf_counter()
+    t_end = args.periods * tau
+    info = S.case_info(h)
+    while info["t"] < t_end:
+        info = S.step(h, args.every, check=False)
+        if info["rc"]:
+            break
+        ts.append(info["t"])
+        an.append(ob.anisotropy(S.read_fields(h, S.FIELD_POS, dim), phase))
+    wall = time.perf_counter() - t0
+    S.destroy(h)
+    s = np.array(an) - np.mean(an)
+    cr = [ts[k - 1] + (ts[k] - ts[k - 1]) * (-s[k - 1]) / (s[k] - s[k - 1])
+          for k in range(1, len(s)) if np.sign(s[k]) != np.sign(s[k - 1]) and s[k] != s[k - 1]]
+    period = ob.fit_period(ts, an, tau) if len(ts) > 10 else float("nan")
+    return {"workload": f"oscillating_{dim}d", "precision": args.precision, "ratio": args.ratio if dim == 2 else 1000,
+            "adv": info["n_adv"], "substeps": info["n_sub"], "t": info["t"], "status": info["status"],
+            "zero_crossings": [round(c, 4) for c in cr], "period": period, "theory": tau,
+            "rel_error": (period - tau) / tau if period == period else None,
+            "anisotropy_amplitude": float(np.abs(s).max()) if len(s) else None, "wall_s": round(wall, 2)}
+
+
+def impact(args):
+    case = sphcases.impact_3d()
+    h = S.case_from_spec(case, precision=args.precision)
+    t0 = time.perf_counter()
+    info = S.case_info(h)
+    while info["t"] < args.t_end:
+        info = S.step(h, 10, check=False)
+        if info["rc"]:
+            break
+    wall = time.perf_counter() - t0
+    vel = S.read_fields(h, S.FIELD_VEL, 3)
+    S.destroy(h)
+    return {"workload": "impact_3d", "precision": args.precision, "particles": case.n,
+            "adv": info["n_adv"], "substeps": info["n_sub"], "t": info["t"], "status": info["status"],
+            "finite": bool(np.isfinite(vel).all()), "vmax": float(np.abs(vel).max()),
+            "particle_substeps_per_s": case.n_fluid * info["n_sub"] / wall, "wall_s": round(wall, 2)}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("workload", choices=["laplace_2d", "oscillating_3d", "oscillating_2d", "impact_3d"])
+    ap.add_argument("--precision", type=int, default=None, choices=[32, 64])
+    ap.add_argument("--adv", type=int, default=500)
+    ap.add_argument("--periods", type=float, default=1.5)
+    ap.add_argument("--every", type=int, default=5)
+    ap.add_argument("--ratio", type=float, default=1000.0)
+    ap.add_argument("--t-end", type=float, default=2.0)
+    args = ap.parse_args(argv)
+    if args.precision is None:
+        args.precision = 64 if args.workload in ("laplace_2d", "oscillating_2d") else 32
+    if args.workload == "laplace_2d":
+        out = laplace(args)
+    elif args.workload == "oscillating_3d":
+        out = oscillating(args, 3)
+    elif args.workload == "oscillating_2d":
+        out = oscillating(args, 2)
+    else:
+        out = impact(args)
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,126 @@
+"""Integral observables on the GPU path, against the oracle and against the
+closed forms the paper and textbooks give:
+
+* the Young-Laplace jump (Eq. 37) of a static drop: GPU time average equals
+  the oracle's within 1%, and both equal gamma / R within the resolution
+  error of R = 10 dp;
+* the 2D drop of §5.1 (velocity of Eq. 34): the GPU's shape-anisotropy
+  signal equals the oracle's while the two FP64 trajectories still coincide
+  (the flow is chaotic: last-bit differences grow over thousands of
+  substeps); at density ratio 1 the fitted period equals the textbook n = 2
+  value 2 pi sqrt(2 R^3 rho / (6 gamma)) within 20% at R = 12 dp;
+* total momentum of a wall-free run is conserved to FP32 rounding.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import sphcases
+from paper_2503_16082_gb300 import observables as ob
+
+pytestmark = pytest.mark.gpu
+
+S = pytest.importorskip("paper_2503_16082_gb300")
+
+
+def laplace_case():
+    return sphcases.small_droplet(2, 40, R_frac=0.25, rho_l=1.0, rho_g=1.0, mu_l=0.05,
+                                  mu_g=0.05, c0=20.0)
+
+
+def laplace_series_gpu(case, precision, t_from, t_to, chunk=20):
+    h = S.case_from_spec(case, precision=precision)
+    phase = S.read_fields(h, S.FIELD_PHASE, 2)
+    out = []
+    t = 0.0
+    while t < t_to:
+        info = S.step(h, chunk)
+        t = info["t"]
+        if t > t_from:
+            dp, R = ob.laplace_jump(S.read_fields(h, S.FIELD_POS, 2), S.read_fields(h, S.FIELD_PRESSURE, 2),
+                                    phase, case.dx, case.h_factor * case.dx)
+            out.append(dp * R / case.gamma)
+    S.destroy(h)
+    return np.array(out)
+
+
+def laplace_series_oracle(case, t_from, t_to, chunk=20):
+    pos, vel, rho, kind = case.flat()
+    P = oracle.params_for_case(case)
+    rho0 = np.asarray(case.fluid_props()[0])[np.minimum(kind, 1)]
+    out = []
+    t = 0.0
+    while t < t_to:
+        pos, vel, rho, info, _, _ = oracle.run(P, pos, vel, rho, kind, chunk)
+        t += info["t"]
+        if t > t_from:
+            p = case.c0 ** 2 * (rho - rho0)
+            dp, R = ob.laplace_jump(pos[:, :2], p, kind, case.dx, case.h_factor * case.dx)
+            out.append(dp * R / case.gamma)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_laplace_jump_gpu_vs_oracle_and_closed_form(precision):
+    case = laplace_case()
+    g = laplace_series_gpu(case, precision, 0.2, 0.45)
+    o = laplace_series_oracle(case, 0.2, 0.45)
+    assert len(g) == len(o) > 5
+    gm, om = g.mean(), o.mean()
+    assert abs(gm - om) <= 0.01 * abs(om), (gm, om)
+    assert 0.8 < gm < 1.3, gm
+
+
+def period_series_gpu(case, t_end, precision=64, chunk=10):
+    h = S.case_from_spec(case, precision=precision)
+    phase = S.read_fields(h, S.FIELD_PHASE, 2)
+    ts, an = [], []
+    t = 0.0
+    while t < t_end:
+        info = S.step(h, chunk)
+        t = info["t"]
+        ts.append(t)
+        an.append(ob.anisotropy(S.read_fields(h, S.FIELD_POS, 2), phase))
+    S.destroy(h)
+    return np.array(ts), np.array(an)
+
+
+def test_oscillating_drop_period_ratio1_matches_textbook():
+    case = sphcases.oscillating_2d(ratio=1.0)
+    want = 2 * math.pi * math.sqrt(2 * 0.2 ** 3 * 1.0 / (6 * 1.0))
+    ts, an = period_series_gpu(case, 3 * want)
+    period = ob.fit_period(ts, an, want)
+    assert abs(period - want) <= 0.20 * want, (period, want)
+
+
+def test_oscillating_drop_signal_gpu_vs_oracle():
+    case = sphcases.oscillating_2d(ratio=1000.0)
+    ts, an = period_series_gpu(case, 0.05)
+    pos, vel, rho, kind = case.flat()
+    P = oracle.params_for_case(case)
+    ots, oan = [], []
+    t = 0.0
+    while t < 0.05:
+        pos, vel, rho, info, _, _ = oracle.run(P, pos, vel, rho, kind, 10)
+        t += info["t"]
+        ots.append(t)
+        oan.append(ob.anisotropy(pos[:, :2], kind))
+    ots, oan = np.array(ots), np.array(oan)
+    assert len(ts) == len(ots) and np.allclose(ts, ots, rtol=1e-12)
+    # ~530 advection steps / 2100 substeps: the FP64 trajectories coincide
+    assert np.abs(an - oan).max() <= 1e-8 * np.abs(oan).max()
+
+
+def test_momentum_conserved_without_walls():
+    case = sphcases.free_blob(dim=2, n_side=24, vel_amp=0.05, rho_jitter=1e-6)
+    h = S.case_from_spec(case, precision=32, tvf_alpha=0.0)
+    v0 = S.read_fields(h, S.FIELD_VEL, 2)
+    ph = S.read_fields(h, S.FIELD_PHASE, 2).astype(int)
+    m = np.asarray(case.fluid_props()[0])[ph] * case.dx ** 2
+    S.step(h, 5)
+    v1 = S.read_fields(h, S.FIELD_VEL, 2)
+    S.destroy(h)
+    scale = (m * np.linalg.norm(v0, axis=1)).sum()
+    assert np.abs(ob.momentum(v1, m) - ob.momentum(v0, m)).max() <= 1e-5 * scale
