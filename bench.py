@@ -39,8 +39,9 @@ import sphcases  # noqa: E402
 METRIC = "particle-substeps/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 # algorithmic FP32 flops per neighbour pair of sweep B (derivation in the design doc):
-FLOPS_PAIR_B = 59            # geometry + Riemann pressure, every pair
-FLOPS_PAIR_B_SURF = 110      # surface stress + penalty, pairs touching the interface
+FP64_PEAK_TFLOPS = 1.25      # nominal FP64 (non-tensor) rate of a GB300
+FLOPS_PAIR_B = 59            # geometry + Riemann pressure, every pair (sweep B)
+FLOPS_PAIR_B_SURF = 110      # surface stress + penalty, pairs touching the interface (sweep S)
 
 
 def workload(name: str):
@@ -164,7 +165,8 @@ def run_ours(args, dist: Dist):
     n_fluid = spec.n_fluid
 
     nbr_mode = S.NBR_CELLS if args.nbr == "cells" else S.NBR_LIST
-    h = S.case_from_spec(spec, precision=args.precision, nbr_mode=nbr_mode)
+    extra = {"block": args.block} if args.block else {}
+    h = S.case_from_spec(spec, precision=args.precision, nbr_mode=nbr_mode, **extra)
     S.set_stream(h, stream.cuda_stream)
     S.step(h, args.warmup)                       # engine set-up, graph capture, warm-up
     info0 = S.case_info(h)
@@ -185,14 +187,16 @@ def run_ours(args, dist: Dist):
     n_sub = info1["n_sub"] - info0["n_sub"]
     units = float(n_fluid) * n_sub
     value, tmax, total_units = aggregate(dist, units, ms / 1e3)
-    # kernels launched in the timed region: per advection step 14 set-up
-    # kernels (speed reduction 3, rebuild 8, list 1, correction matrix,
-    # viscous + shift) + 1 closing kernel, per substep 4
-    launches = args.steps * 15 + 4 * n_sub
-
     # live per-kernel timing of one more advection step (events around each
     # launch on the same stream) for the roofline of the dominant kernel
     prof = S.profile_step(h)
+    # kernels launched in the timed region, from the launch counts of that
+    # step: set-up kernels + 1 closing kernel per advection step, the
+    # per-substep kernels (criterion, A, S, B, C) per substep
+    prof_sub = max(prof["criterion"][1], 1)
+    per_step = prof["rebuild"][1] + prof["setup"][1] + 1
+    per_sub = sum(prof[g][1] for g in ("criterion", "sweep_A", "sweep_S", "sweep_B", "sweep_C")) / prof_sub
+    launches = int(round(args.steps * per_step + n_sub * per_sub))
     counts = S.debug_neighbor_counts(h)
     phase = S.read_fields(h, S.FIELD_PHASE, spec.dim)
     gradc = S.read_fields(h, S.FIELD_GRADC, spec.dim)
@@ -203,14 +207,26 @@ def run_ours(args, dist: Dist):
     pairs_surf = int(min(2 * counts[iface].sum(), pairs))
     b_ms, b_launches = prof["sweep_B"]
     b_avg = b_ms / max(b_launches, 1) / 1e3
-    flops = FLOPS_PAIR_B * pairs + FLOPS_PAIR_B_SURF * pairs_surf
+    # sweep B carries the pressure pairs; with the neighbour list the surface
+    # pairs run in sweep S, with the cell walk in B itself
+    surf_in_b = args.nbr == "cells"
+    flops = FLOPS_PAIR_B * pairs + (FLOPS_PAIR_B_SURF * pairs_surf if surf_in_b else 0)
     achieved = flops / b_avg / 1e12
-    roofline = {"bound": "alu", "kernel": "k_sweep_B<float>", "achieved": round(achieved, 3),
-                "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
-                "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+    f32 = args.precision == 32
+    peak = FP32_PEAK_TFLOPS if f32 else FP64_PEAK_TFLOPS
+    roofline = {"bound": "alu",
+                "kernel": f"k_sweep_B<{'float' if f32 else 'double'}, {spec.dim}, {'false' if surf_in_b else 'true'}>",
+                "achieved": round(achieved, 3),
+                "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if f32
+                                else "nominal FP64 rate of a GB300"),
                 "flops_per_launch": flops, "pairs": pairs, "pairs_surface": pairs_surf,
                 "avg_launch_ms": round(b_avg * 1e3, 4)}
+    if not surf_in_b and prof["sweep_S"][1]:
+        s_avg = prof["sweep_S"][0] / prof["sweep_S"][1] / 1e3
+        roofline["sweep_S"] = {"avg_launch_ms": round(s_avg * 1e3, 4),
+                               "achieved": round(FLOPS_PAIR_B_SURF * pairs_surf / s_avg / 1e12, 3)}
     kernel_ms = {g: {"ms": round(m, 3), "launches": l} for g, (m, l) in prof.items()}
     S.destroy(h)
 
@@ -220,7 +236,7 @@ def run_ours(args, dist: Dist):
         dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h2 = S.case_from_spec(spec, precision=args.precision, nbr_mode=nbr_mode)
+        h2 = S.case_from_spec(spec, precision=args.precision, nbr_mode=nbr_mode, **extra)
         S.set_stream(h2, stream.cuda_stream)
         d2h = 0
         e_sub0 = 0
@@ -393,6 +409,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--nbr", default="list", choices=["list", "cells"],
                     help="neighbour source of the sweeps (list built per advection step, or cell walk)")
+    ap.add_argument("--block", type=int, default=0, help="particles per tile / threads per block (0: library default)")
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"],
                     help="single: the headline line; batch / serve: the batched and served workloads")
     ap.add_argument("--cases", type=int, default=512)

@@ -217,11 +217,14 @@ int sphst_set_stream(sphst_case c, void *cuda_stream);
 /* Advance one advection step with every kernel launched on its own (no
  * graph) and bracketed by CUDA events on the case's stream.  kernel_ms[k]
  * receives the summed device time of kernel group k and launches[k] its
- * launch count, for k = 0 rebuild (keys, scan, sort, gather), 1 set-up
- * (speed reduction, criteria, correction matrix, viscous + shift),
- * 2 criterion per substep, 3 sweep A, 4 sweep B, 5 sweep C.  Both arrays
- * hold SPHST_PROFILE_GROUPS entries.  The step is a normal step of the case. */
-#define SPHST_PROFILE_GROUPS 6
+ * launch count, for k = 0 rebuild (keys, scan, sort, gather, neighbour
+ * list, interface band), 1 set-up (speed reduction, criteria, correction
+ * matrix, viscous + shift), 2 criterion per substep, 3 sweep A (colour
+ * gradient), 4 sweep B (pressure + kick), 5 sweep C (continuity + drift),
+ * 6 sweep S (surface sum of the interface band; neighbour-list cases only).
+ * Both arrays hold SPHST_PROFILE_GROUPS entries.  The step is a normal step
+ * of the case. */
+#define SPHST_PROFILE_GROUPS 7
 int sphst_profile_step(sphst_case c, double *kernel_ms, int64_t *launches);
 
 /* Cell order without allocating (the paper has no counterpart: this serves

@@ -212,7 +212,7 @@ def debug_neighbor_counts(case):
     return cnt[:n]
 
 
-PROFILE_GROUPS = ("rebuild", "setup", "criterion", "sweep_A", "sweep_B", "sweep_C")
+PROFILE_GROUPS = ("rebuild", "setup", "criterion", "sweep_A", "sweep_B", "sweep_C", "sweep_S")
 
 
 def set_stream(case, cuda_stream: int) -> None:

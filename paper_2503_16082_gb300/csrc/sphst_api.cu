@@ -169,7 +169,7 @@ int64_t footprint(const sphst_case_params *P, int64_t n) {
     const int64_t tsz = P->precision == 64 ? 8 : 4;
     const int64_t kmax = P->nbr_mode == SPHST_NBR_LIST
                              ? (P->max_neighbors > 0 ? P->max_neighbors : (P->dim == 3 ? 128 : 48)) : 0;
-    const int64_t per = 8 * 4 * tsz + 2 * tsz + 4 * 4 + 4 * kmax + 4;  // V4 arrays, scalars, ints, list
+    const int64_t per = 9 * 4 * tsz + 2 * tsz + 4 * 4 + 4 * kmax + 4 + 1;  // V4 arrays, scalars, ints, list, band
     // cell table: cells ~ n / 2.6^d per axis padded to a power of two
     const double side = std::pow((double)std::max<int64_t>(n, 1), 1.0 / P->dim) / 2.6 + 2.0 * P->grid_pad + 2.0;
     int bits = 0;

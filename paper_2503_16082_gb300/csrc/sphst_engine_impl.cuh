@@ -19,15 +19,32 @@ namespace sphst {
 
 enum ArrayId { A_POS = 0, A_VEL, A_DRHO, A_ID, A_GRADC, A_ACCV };
 
+// Tile classes: 0 = 3D list, 1 = 2D list, 2 = 3D cell walk, 3 = 2D cell walk.
+// SPH_CLASSES(NCLS, KERN, args...) launches KERN<T, D, LIST> over the tiles of
+// each non-empty class among the first NCLS (2: list classes only).
+#define SPH_CLASSES(NCLS, KERN, ...)                                                   \
+    for (int k_ = 0; k_ < (NCLS); ++k_) {                                              \
+        if (!cls_n[k_]) continue;                                                      \
+        const SweepArgs a_ = sweep_args(k_);                                           \
+        const unsigned g_ = (unsigned)cls_n[k_];                                       \
+        switch (k_) {                                                                  \
+        case 0: KERN<T, 3, true><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;    \
+        case 1: KERN<T, 2, true><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;    \
+        case 2: KERN<T, 3, false><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;   \
+        default: KERN<T, 2, false><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;  \
+        }                                                                              \
+    }
+
 template <typename T> struct EngineT : Engine {
     // particle arrays
     V4<T> *pos = nullptr, *snap = nullptr, *vel = nullptr, *vel_new = nullptr;
-    V4<T> *gradC = nullptr, *acc_visc = nullptr, *bmat = nullptr;
+    V4<T> *gradC = nullptr, *acc_visc = nullptr, *acc_surf = nullptr, *bmat = nullptr;
     T *drho = nullptr, *drho_old = nullptr;
     uint32_t *id = nullptr, *key = nullptr, *rank = nullptr, *perm = nullptr;
     // cell table + scan scratch
     uint32_t *starts = nullptr, *block_sums = nullptr;
     uint32_t *nbr = nullptr, *nbr_cnt = nullptr;   // neighbour lists (ELL per case) and counts
+    uint8_t *band = nullptr;                        // interface band of the frozen configuration
     int64_t nbr_total = 0;
     bool any_list = false;
     // cases
@@ -38,6 +55,7 @@ template <typename T> struct EngineT : Engine {
     double *d_read = nullptr;              // read-back buffer
     void *arena = nullptr;
     int64_t n = 0, table_total = 0, n_tiles = 0, max_case_n = 0;
+    int64_t cls_b[4] = {0, 0, 0, 0}, cls_n[4] = {0, 0, 0, 0};   // tile range of each class
     int ncases = 0, block = 128;
     bool any_tvf = false;
     int loop_mode = SPHST_LOOP_GRAPH;
@@ -128,6 +146,7 @@ template <typename T> struct EngineT : Engine {
         size_t o_pos = take(nn * sizeof(V4<T>)), o_snap = take(nn * sizeof(V4<T>));
         size_t o_vel = take(nn * sizeof(V4<T>)), o_veln = take(nn * sizeof(V4<T>));
         size_t o_gc = take(nn * sizeof(V4<T>)), o_av = take(nn * sizeof(V4<T>));
+        size_t o_as = take(nn * sizeof(V4<T>));
         size_t o_bm = take(2 * nn * sizeof(V4<T>));
         size_t o_dr = take(nn * sizeof(T)), o_dro = take(nn * sizeof(T));
         size_t o_id = take(nn * 4), o_key = take(nn * 4), o_rank = take(nn * 4), o_perm = take(nn * 4);
@@ -137,6 +156,7 @@ template <typename T> struct EngineT : Engine {
         size_t o_flag = take(64);
         size_t o_read = take((size_t)std::max<int64_t>(max_case_n, 1) * 3 * sizeof(double));
         size_t o_nbr = take((size_t)std::max<int64_t>(nbr_total, 1) * 4), o_ncnt = take(nn * 4);
+        size_t o_band = take(nn);
         cudaError_t e = cudaMalloc(&arena, off);
         if (e != cudaSuccess) {
             arena = nullptr;
@@ -147,7 +167,8 @@ template <typename T> struct EngineT : Engine {
         char *b = (char *)arena;
         pos = (V4<T> *)(b + o_pos); snap = (V4<T> *)(b + o_snap);
         vel = (V4<T> *)(b + o_vel); vel_new = (V4<T> *)(b + o_veln);
-        gradC = (V4<T> *)(b + o_gc); acc_visc = (V4<T> *)(b + o_av); bmat = (V4<T> *)(b + o_bm);
+        gradC = (V4<T> *)(b + o_gc); acc_visc = (V4<T> *)(b + o_av);
+        acc_surf = (V4<T> *)(b + o_as); bmat = (V4<T> *)(b + o_bm);
         drho = (T *)(b + o_dr); drho_old = (T *)(b + o_dro);
         id = (uint32_t *)(b + o_id); key = (uint32_t *)(b + o_key);
         rank = (uint32_t *)(b + o_rank); perm = (uint32_t *)(b + o_perm);
@@ -157,13 +178,20 @@ template <typename T> struct EngineT : Engine {
         d_read = (double *)(b + o_read);
         nbr = (uint32_t *)(b + o_nbr);
         nbr_cnt = (uint32_t *)(b + o_ncnt);
+        band = (uint8_t *)(b + o_band);
         SPH_CK(cudaMemsetAsync(arena, 0, off, stream));
-        // tiles
+        // tiles, grouped by class
         std::vector<Tile> tiles;
         tiles.reserve(n_tiles);
-        for (int c = 0; c < ncases; ++c)
-            for (int64_t s = h_desc[c].p_begin; s < h_desc[c].p_end; s += block)
-                tiles.push_back(Tile{c, (int32_t)std::min<int64_t>(block, h_desc[c].p_end - s), s});
+        for (int k = 0; k < 4; ++k) {
+            cls_b[k] = (int64_t)tiles.size();
+            for (int c = 0; c < ncases; ++c) {
+                if (tile_class(h_desc[c]) != k) continue;
+                for (int64_t s = h_desc[c].p_begin; s < h_desc[c].p_end; s += block)
+                    tiles.push_back(Tile{c, (int32_t)std::min<int64_t>(block, h_desc[c].p_end - s), s});
+            }
+            cls_n[k] = (int64_t)tiles.size() - cls_b[k];
+        }
         SPH_CK(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, stream));
         SPH_CK(cudaMemcpyAsync(d_desc, h_desc.data(), sizeof(CaseDesc) * ncases, cudaMemcpyHostToDevice, stream));
         // fill each case
@@ -226,12 +254,19 @@ template <typename T> struct EngineT : Engine {
         return SPHST_OK;
     }
 
+    static int tile_class(const CaseDesc &d) { return (d.nbr_mode == 0 ? 0 : 2) + (d.dim == 3 ? 0 : 1); }
+    SweepArgs sweep_args(int k) const { return SweepArgs{d_tiles, d_desc, d_state, starts, nbr, nbr_cnt, cls_b[k]}; }
+    int n_classes(int upto) const {
+        int m = 0;
+        for (int k = 0; k < upto; ++k) m += cls_n[k] > 0;
+        return m;
+    }
+
     // ---------------------------------------------------------- launches
     int launch_pre() {
         const int nthr = 256;
         const int cgrid = (ncases + 127) / 128;
         const int pgrid = (int)((n + nthr - 1) / nthr);
-        SweepArgs a{d_tiles, d_desc, d_state, starts, nbr, nbr_cnt};
         SPH_CK(cudaMemsetAsync(starts, 0, (size_t)(table_total + 1) * 4, stream));
         k_reset_vmax<<<cgrid, 128, 0, stream>>>(ncases, d_state);
         k_vmax<T><<<(unsigned)n_tiles, block, 0, stream>>>(d_tiles, d_desc, d_state, pos, vel);
@@ -246,19 +281,20 @@ template <typename T> struct EngineT : Engine {
         k_cell_sort<<<(unsigned)((table_total + nthr - 1) / nthr), nthr, 0, stream>>>(table_total, starts, id, perm);
         k_gather<T><<<pgrid, nthr, 0, stream>>>(n, perm, pos, vel, drho, id, snap, vel_new, drho_old, rank);
         k_copy_back<T><<<pgrid, nthr, 0, stream>>>(n, snap, vel_new, drho_old, rank, pos, vel, drho, id);
-        if (any_list) k_build_list<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, nbr, nbr_cnt);
-        if (any_tvf) k_sweep_M<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, bmat);
-        k_sweep_V<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, vel, bmat, acc_visc, pos);
+        SPH_CLASSES(2, k_build_list, snap, nbr, nbr_cnt);
+        SPH_CLASSES(2, k_band, snap, band);
+        if (any_tvf) SPH_CLASSES(4, k_sweep_M, snap, drho, bmat);
+        SPH_CLASSES(4, k_sweep_V, snap, drho, vel, bmat, acc_visc, pos);
         SPH_CK(cudaGetLastError());
         return SPHST_OK;
     }
 
     int launch_body(cudaGraphConditionalHandle h, int use_handle) {
-        SweepArgs a{d_tiles, d_desc, d_state, starts, nbr, nbr_cnt};
         k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, h, use_handle);
-        k_sweep_A<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, gradC);
-        k_sweep_B<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, vel, gradC, acc_visc, vel_new, drho_old);
-        k_sweep_C<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho_old, vel_new, drho, vel, pos);
+        SPH_CLASSES(4, k_sweep_A, snap, drho, gradC);
+        SPH_CLASSES(2, k_sweep_S, band, snap, vel, gradC, acc_surf);
+        SPH_CLASSES(4, k_sweep_B, band, snap, vel, gradC, acc_visc, acc_surf, vel_new);
+        SPH_CLASSES(4, k_sweep_C, snap, vel_new, drho, vel, pos);
         SPH_CK(cudaGetLastError());
         return SPHST_OK;
     }
@@ -358,7 +394,7 @@ template <typename T> struct EngineT : Engine {
         const int pgrid = (int)((n + nthr - 1) / nthr);
         const int64_t ns = table_total + 1;
         const unsigned nb = (unsigned)((ns + SCAN_ITEMS - 1) / SCAN_ITEMS);
-        SweepArgs a{d_tiles, d_desc, d_state, starts, nbr, nbr_cnt};
+        const int ncls = n_classes(4), nlist = n_classes(2);
         timed(1, 3, [&] {
             k_reset_vmax<<<cgrid, 128, 0, stream>>>(ncases, d_state);
             k_vmax<T><<<(unsigned)n_tiles, block, 0, stream>>>(d_tiles, d_desc, d_state, pos, vel);
@@ -375,18 +411,20 @@ template <typename T> struct EngineT : Engine {
             k_gather<T><<<pgrid, nthr, 0, stream>>>(n, perm, pos, vel, drho, id, snap, vel_new, drho_old, rank);
             k_copy_back<T><<<pgrid, nthr, 0, stream>>>(n, snap, vel_new, drho_old, rank, pos, vel, drho, id);
         });
-        timed(0, any_list ? 1 : 0, [&] {
-            if (any_list) k_build_list<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, nbr, nbr_cnt);
+        timed(0, 2 * nlist, [&] {
+            SPH_CLASSES(2, k_build_list, snap, nbr, nbr_cnt);
+            SPH_CLASSES(2, k_band, snap, band);
         });
-        timed(1, any_tvf ? 2 : 1, [&] {
-            if (any_tvf) k_sweep_M<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, bmat);
-            k_sweep_V<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, vel, bmat, acc_visc, pos);
+        timed(1, any_tvf ? 2 * ncls : ncls, [&] {
+            if (any_tvf) SPH_CLASSES(4, k_sweep_M, snap, drho, bmat);
+            SPH_CLASSES(4, k_sweep_V, snap, drho, vel, bmat, acc_visc, pos);
         });
         for (;;) {
             timed(2, 1, [&] { k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, 0, 0); });
-            timed(3, 1, [&] { k_sweep_A<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, gradC); });
-            timed(4, 1, [&] { k_sweep_B<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho, vel, gradC, acc_visc, vel_new, drho_old); });
-            timed(5, 1, [&] { k_sweep_C<T><<<(unsigned)n_tiles, block, 0, stream>>>(a, snap, drho_old, vel_new, drho, vel, pos); });
+            timed(3, ncls, [&] { SPH_CLASSES(4, k_sweep_A, snap, drho, gradC); });
+            timed(6, nlist, [&] { SPH_CLASSES(2, k_sweep_S, band, snap, vel, gradC, acc_surf); });
+            timed(4, ncls, [&] { SPH_CLASSES(4, k_sweep_B, band, snap, vel, gradC, acc_visc, acc_surf, vel_new); });
+            timed(5, ncls, [&] { SPH_CLASSES(4, k_sweep_C, snap, vel_new, drho, vel, pos); });
             if (rc) break;
             int flag = 0;
             cudaError_t e = cudaMemcpy(&flag, d_loop_flag, sizeof(int), cudaMemcpyDeviceToHost);

@@ -25,6 +25,19 @@
 //                      sweeps (caps registers per thread)
 //   SPHST_SWEEPB_MINB  the same for sweep B alone (default 4: 64 registers)
 //   SPHST_LIST_UNROLL  unroll factor of the neighbour-list loop
+//   SPHST_LIST_PREFETCH 1: load list entry k+1 while pair k is evaluated
+//   SPHST_FAST_DIV     1: FP32 pair divisions through the SFU reciprocal
+//   SPHST_PIPE         1: sweeps B and C load the next neighbour's position and
+//                      state while the current pair is evaluated
+#ifndef SPHST_LIST_PREFETCH
+#define SPHST_LIST_PREFETCH 1
+#endif
+#ifndef SPHST_FAST_DIV
+#define SPHST_FAST_DIV 1
+#endif
+#ifndef SPHST_PIPE
+#define SPHST_PIPE 0
+#endif
 #ifndef SPHST_LIST_LDCS
 #define SPHST_LIST_LDCS 1
 #endif
@@ -63,6 +76,47 @@ template <typename T> __device__ __forceinline__ V4<T> ld4(const V4<T> *p) { ret
 template <> __device__ __forceinline__ V4<float> ld4<float>(const V4<float> *p) {
     float4 v = __ldg(reinterpret_cast<const float4 *>(p));
     return V4<float>{v.x, v.y, v.z, v.w};
+}
+
+// Divisions inside the FP32 pair loops: __fdividef (error <= 2 ulp for
+// divisors below 2^126, which densities and |grad C| are) instead of the
+// IEEE sequence; FP64 keeps IEEE division.  1/sqrt likewise.
+__device__ __forceinline__ float div_fast(float a, float b) {
+#if SPHST_FAST_DIV
+    return __fdividef(a, b);
+#else
+    return a / b;
+#endif
+}
+__device__ __forceinline__ double div_fast(double a, double b) { return a / b; }
+__device__ __forceinline__ float rsqrt_fast(float x) {
+#if SPHST_FAST_DIV
+    return rsqrtf(x);
+#else
+    return 1.0f / sqrtf(x);
+#endif
+}
+__device__ __forceinline__ double rsqrt_fast(double x) { return 1.0 / sqrt(x); }
+
+// b - 1 as a floating-point value for a 2-bit field b (0..2), without an
+// integer conversion: the bit pattern 2^23 + b (2^52 + b) is exact and the
+// subtraction of 2^23 + 1 (2^52 + 1) is exact too
+__device__ __forceinline__ float code_off(uint32_t b, float) {
+    return __fsub_rn(__uint_as_float(0x4B000000u | b), 8388609.0f);
+}
+__device__ __forceinline__ double code_off(uint32_t b, double) {
+    return __dsub_rn(__longlong_as_double(0x4330000000000000ll | (long long)b), 4503599627370497.0);
+}
+
+// a ? x1 : x0 for the two fluid phases' constants (no indexed loads)
+template <typename T> __device__ __forceinline__ T sel(uint32_t k, T x0, T x1) { return k ? x1 : x0; }
+
+__device__ __forceinline__ uint32_t ld_list(const uint32_t *p) {
+#if SPHST_LIST_LDCS
+    return __ldcs(p);
+#else
+    return __ldg(p);
+#endif
 }
 
 __device__ __forceinline__ double bits_to_d(unsigned long long b) { return __longlong_as_double((long long)b); }
@@ -151,51 +205,141 @@ __device__ __forceinline__ bool walk(const CaseDesc &d, const CasePhys<T> &cp,
 // Neighbour list of the frozen configuration (ELL layout per case: entry k of
 // particle i at nbr[nbr_base + k * n_case + (i - p_begin)], so a warp's 32
 // lanes read 32 consecutive words).  An entry is j << 6 | cell code, the code
-// holding (o + 1) per axis in 2 bits, o the neighbour cell's offset.  The
-// list keeps the cell-walk order, so both visit neighbours identically.
+// holding (o + 1) per axis in 2 bits, o the neighbour cell's offset.  Each
+// list holds the neighbours of the other fluid phase first, then the rest,
+// each part in cell-walk order; cnt[i] = count | (other-phase count << 16),
+// so the colour-gradient sweep reads only the first part.
 constexpr uint32_t NBR_SHIFT = 6;
+constexpr uint32_t CNT_MASK = 0xffffu;
+enum NbrPart { PART_ALL = 0, PART_OTHER = 1 };
 template <int D>
 __device__ __forceinline__ uint32_t cell_code(int ox, int oy, int oz) {
     return (uint32_t)(ox + 1) | ((uint32_t)(oy + 1) << 2) | (D == 3 ? ((uint32_t)(oz + 1) << 4) : 0u);
 }
 
-template <typename T, int D, typename F>
+template <int PART, typename T, int D, typename F>
 __device__ __forceinline__ void walk_list(const CaseDesc &d, const CasePhys<T> &cp,
                                           const uint32_t *__restrict__ nbr,
                                           const uint32_t *__restrict__ cnt,
                                           const V4<T> *__restrict__ snap, int64_t i,
                                           const V4<T> &si, F &&f) {
     const int64_t stride = d.p_end - d.p_begin;
-    const uint32_t *base = nbr + d.nbr_base + (i - d.p_begin);
-    const uint32_t c = cnt[i];
+    const uint32_t *p = nbr + d.nbr_base + (i - d.p_begin);
+    const uint32_t c = PART == PART_OTHER ? cnt[i] >> 16 : cnt[i] & CNT_MASK;
     const T cs = cp.cs;
+#if SPHST_LIST_PREFETCH
+    uint32_t next = c ? ld_list(p) : 0u;
+#endif
 #pragma unroll kListUnroll
     for (uint32_t k = 0; k < c; ++k) {
-#if SPHST_LIST_LDCS
-        const uint32_t e = __ldcs(base + (int64_t)k * stride);
+#if SPHST_LIST_PREFETCH
+        const uint32_t e = next;
+        p += stride;
+        if (k + 1 < c) next = ld_list(p);
 #else
-        const uint32_t e = __ldg(base + (int64_t)k * stride);
+        const uint32_t e = ld_list(p);
+        p += stride;
 #endif
         const uint32_t j = e >> NBR_SHIFT;
-        const T ox = T((int)(e & 3u) - 1), oy = T((int)((e >> 2) & 3u) - 1);
         const V4<T> sj = ld4(snap + j);
-        const T rx = sub_rn(sub_rn(si.x, mul_rn(ox, cs)), sj.x);
-        const T ry = sub_rn(sub_rn(si.y, mul_rn(oy, cs)), sj.y);
+        // s_i - o cs with o in {-1, 0, 1}: o cs is exact, so the FMA rounds
+        // once, exactly like the cell walk's subtraction
+        const T rx = sub_rn(fma_rn(-code_off(e & 3u, T()), cs, si.x), sj.x);
+        const T ry = sub_rn(fma_rn(-code_off((e >> 2) & 3u, T()), cs, si.y), sj.y);
         T rz = T(0);
-        if (D == 3) rz = sub_rn(sub_rn(si.z, mul_rn(T((int)((e >> 4) & 3u) - 1), cs)), sj.z);
+        if (D == 3) rz = sub_rn(fma_rn(-code_off((e >> 4) & 3u, T()), cs, si.z), sj.z);
         const T r2 = norm2<T, D>(rx, ry, rz);
         f(j, sj, rx, ry, rz, r2);
     }
 }
 
-// neighbours of i from the list (LIST) or from the cell walk
+// The list walk with one more per-neighbour array: f(j, s_j, aux_j, r_ij, r^2).
+// With SPHST_PIPE the entry two ahead and the position and aux word of the
+// next neighbour are in flight while the current pair is evaluated.
+template <typename T, int D, typename F>
+__device__ __forceinline__ void walk_list_aux(const CaseDesc &d, const CasePhys<T> &cp,
+                                              const uint32_t *__restrict__ nbr,
+                                              const uint32_t *__restrict__ cnt,
+                                              const V4<T> *__restrict__ snap,
+                                              const V4<T> *__restrict__ aux, int64_t i,
+                                              const V4<T> &si, F &&f) {
+    const int64_t stride = d.p_end - d.p_begin;
+    const uint32_t *p = nbr + d.nbr_base + (i - d.p_begin);
+    const uint32_t c = cnt[i] & CNT_MASK;
+    const T cs = cp.cs;
+    const auto pair = [&](uint32_t e, const V4<T> &sj, const V4<T> &aj) {
+        const T rx = sub_rn(fma_rn(-code_off(e & 3u, T()), cs, si.x), sj.x);
+        const T ry = sub_rn(fma_rn(-code_off((e >> 2) & 3u, T()), cs, si.y), sj.y);
+        T rz = T(0);
+        if (D == 3) rz = sub_rn(fma_rn(-code_off((e >> 4) & 3u, T()), cs, si.z), sj.z);
+        f(e >> NBR_SHIFT, sj, aj, rx, ry, rz, norm2<T, D>(rx, ry, rz));
+    };
+#if SPHST_PIPE
+    if (c == 0) return;
+    uint32_t e = ld_list(p);
+    p += stride;
+    uint32_t e_next = c > 1 ? ld_list(p) : 0u;
+    p += stride;
+    V4<T> sj = ld4(snap + (e >> NBR_SHIFT)), aj = ld4(aux + (e >> NBR_SHIFT));
+#pragma unroll 1
+    for (uint32_t k = 0; k < c; ++k) {
+        const uint32_t ec = e;
+        const V4<T> sc = sj, ac = aj;
+        if (k + 1 < c) {
+            e = e_next;
+            sj = ld4(snap + (e >> NBR_SHIFT));
+            aj = ld4(aux + (e >> NBR_SHIFT));
+            if (k + 2 < c) e_next = ld_list(p);
+            p += stride;
+        }
+        pair(ec, sc, ac);
+    }
+#else
+#if SPHST_LIST_PREFETCH
+    uint32_t next = c ? ld_list(p) : 0u;
+#endif
+#pragma unroll kListUnroll
+    for (uint32_t k = 0; k < c; ++k) {
+#if SPHST_LIST_PREFETCH
+        const uint32_t e = next;
+        p += stride;
+        if (k + 1 < c) next = ld_list(p);
+#else
+        const uint32_t e = ld_list(p);
+        p += stride;
+#endif
+        const uint32_t j = e >> NBR_SHIFT;
+        pair(e, ld4(snap + j), ld4(aux + j));
+    }
+#endif
+}
+
+// neighbours of i with aux[j] loaded for f(j, s_j, aux_j, r_ij, r^2), from the
+// list or the cell walk
 template <bool LIST, typename T, int D, typename F>
+__device__ __forceinline__ bool neighbors_aux(const CaseDesc &d, const CasePhys<T> &cp,
+                                              const uint32_t *starts, const uint32_t *nbr,
+                                              const uint32_t *cnt, const V4<T> *snap, const V4<T> *aux,
+                                              int64_t i, const V4<T> &si, uint32_t pki, F &&f) {
+    if constexpr (LIST) {
+        walk_list_aux<T, D>(d, cp, nbr, cnt, snap, aux, i, si, f);
+        return false;
+    } else {
+        return walk<T, D>(d, cp, starts, snap, i, si, pki,
+            [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) { f(j, sj, ld4(aux + j), rx, ry, rz, r2); });
+    }
+}
+
+// neighbours of i from the list (LIST) or from the cell walk; PART_OTHER
+// restricts the list to the other fluid phase (the cell walk visits all and
+// the caller filters)
+template <bool LIST, typename T, int D, int PART = PART_ALL, typename F>
 __device__ __forceinline__ bool neighbors(const CaseDesc &d, const CasePhys<T> &cp,
                                           const uint32_t *starts, const uint32_t *nbr,
                                           const uint32_t *cnt, const V4<T> *snap, int64_t i,
                                           const V4<T> &si, uint32_t pki, F &&f) {
     if constexpr (LIST) {
-        walk_list<T, D>(d, cp, nbr, cnt, snap, i, si, f);
+        walk_list<PART, T, D>(d, cp, nbr, cnt, snap, i, si, f);
         return false;
     } else {
         return walk<T, D>(d, cp, starts, snap, i, si, pki, f);
@@ -246,8 +390,9 @@ __device__ __forceinline__ void init_one(const CaseDesc &d, int c, int64_t k, co
     pos[i] = p;
     V4<T> v;
     v.x = (T)avel[3 * k]; v.y = (T)avel[3 * k + 1]; v.z = (T)avel[3 * k + 2]; v.w = T(0);
-    vel[i] = v;
     drho[i] = ph < 2 ? (T)(arho[k] - d.rho0[ph]) : T(0);
+    v.w = drho[i];                    // vel.w mirrors drho (read with the velocity)
+    vel[i] = v;
     id[i] = (uint32_t)k;
 }
 
@@ -575,7 +720,7 @@ __device__ __forceinline__ void sweep_M(const CaseDesc &d, const CasePhys<T> &cp
         [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
             const PairGeo<T> g = geo(cp, r2);
             const uint32_t kj = phase_of(w_bits(sj.w));
-            const T Vj = kj == PH_WALL ? cp.vol_wall : cp.mass[kj] / (cp.rho0[kj] + drho[j]);
+            const T Vj = kj == PH_WALL ? cp.vol_wall : div_fast(cp.mass[kj], cp.rho0[kj] + drho[j]);
             // r (x) dW e V = (dW V / r) r_vec (x) r_vec
             const T s = g.dW * Vj * g.inv_r;
             m00 += s * rx * rx; m01 += s * rx * ry; m11 += s * ry * ry;
@@ -634,7 +779,7 @@ __device__ __forceinline__ void sweep_V(const CaseDesc &d, const CasePhys<T> &cp
             } else {
                 const T eta_j = cp.eta[kj];
                 eta_bar = T(2) * eta_i * eta_j / (eta_i + eta_j);
-                Vj = cp.mass[kj] / (cp.rho0[kj] + drho[j]);
+                Vj = div_fast(cp.mass[kj], cp.rho0[kj] + vj.w);
                 if (tvf) { Bj0 = bmat[2 * j]; Bj1 = bmat[2 * j + 1]; }
             }
             const T f = eta_bar * g.dW * Vj * g.inv_r;     // eta (v_ij / r) dW V
@@ -677,11 +822,11 @@ __device__ __forceinline__ void sweep_A(const CaseDesc &d, const CasePhys<T> &cp
         const uint32_t other = ki ^ 1u;
         const T two_phi = cp.two_phi[ki];
         const T m_o = cp.mass[other], rho0_o = cp.rho0[other];
-        neighbors<LIST, T, D>(d, cp, starts, nbr, cnt, snap, i, si, pki,
+        neighbors<LIST, T, D, PART_OTHER>(d, cp, starts, nbr, cnt, snap, i, si, pki,
             [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
-                if (phase_of(w_bits(sj.w)) != other) return;
+                if (!LIST && phase_of(w_bits(sj.w)) != other) return;
                 const PairGeo<T> gg = geo(cp, r2);
-                const T Vj = m_o / (rho0_o + drho[j]);
+                const T Vj = div_fast(m_o, rho0_o + drho[j]);
                 const T s = two_phi * gg.dW * Vj * gg.inv_r;
                 g.x += s * rx;
                 g.y += s * ry;
@@ -693,115 +838,153 @@ __device__ __forceinline__ void sweep_A(const CaseDesc &d, const CasePhys<T> &cp
 }
 
 // ---- B: pressure + surface tension + kick
-template <bool LIST, typename T, int D>
+// With the neighbour list the surface sum (Eqs. 24, 26, 30, 33) is a kernel of
+// its own (S, below), launched before B and taken only by particles of the
+// interface band (band[i]: i or one of its neighbours has neighbours of the
+// other fluid; elsewhere grad C = 0 for i and all its neighbours and every
+// surface term is zero).  B then runs the pressure sum over all neighbours and
+// adds the stored surface sum.  Both sums keep their order, so the result
+// equals the single pass of the cell walk term by term.
+//
+// PASS: 0 = pressure + surface in one walk (cell walk), 1 = pressure and the
+// stored surface sum (list), 2 = surface sum only (list, band particles).
+template <bool LIST, int PASS, typename T, int D>
 __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &cp, T dt,
-                                          int64_t i, const uint32_t *starts, const uint32_t *nbr, const uint32_t *cnt, const V4<T> *snap,
-                                          const T *drho, const V4<T> *vel, const V4<T> *gradC,
-                                          const V4<T> *acc_visc, V4<T> *vel_new, T *drho_old,
+                                          int64_t i, const uint32_t *starts, const uint32_t *nbr, const uint32_t *cnt,
+                                          const uint8_t *band, const V4<T> *snap,
+                                          const V4<T> *vel, const V4<T> *gradC,
+                                          const V4<T> *acc_visc, V4<T> *acc_surf, V4<T> *vel_new,
                                           uint32_t *phase_out) {
     const V4<T> si = ld4(snap + i);
     const uint32_t pki = w_bits(si.w);
     const uint32_t ki = phase_of(pki);
     *phase_out = ki;
     if (ki == PH_WALL) return 0.0;
-    const T dri = drho[i];
-    const T rho_i = cp.rho0[ki] + dri;
-    const T p_i = cp.c0sq * dri;
+    if (PASS == 2 && !band[i]) return 0.0;
     const V4<T> vi = vel[i];
-    const V4<T> gi = gradC[i];
-    const bool if_i = gi.w * cp.h > cp.nhat_eps;
-    const T inv_gi = if_i ? T(1) / gi.w : T(0);
-    const T nix = gi.x * inv_gi, niy = gi.y * inv_gi, niz = gi.z * inv_gi;
-    const T gam_gi = if_i ? cp.gamma * gi.w : T(0);
+    const T dri = vi.w;
+    const T rho_i = sel(ki, cp.rho0[0], cp.rho0[1]) + dri;
+    const T p_i = cp.c0sq * dri;
     const int lim = d.limiter;
-    const bool surface_on = d.n_fluid_phases == 2;
-    const T c0 = cp.c0, inv_c0 = cp.inv_c0;
-    const T xg = cp.xi * cp.gamma;
     T apx = 0, apy = 0, apz = 0, asx = 0, asy = 0, asz = 0;
-    neighbors<LIST, T, D>(d, cp, starts, nbr, cnt, snap, i, si, pki,
-        [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
-            const PairGeo<T> g = geo(cp, r2);
-            const T ex = rx * g.inv_r, ey = ry * g.inv_r, ez = D == 3 ? rz * g.inv_r : T(0);
-            const uint32_t kj = phase_of(w_bits(sj.w));
-            const V4<T> vj = vel[j];
-            const T UL = -(vi.x * ex + vi.y * ey + (D == 3 ? vi.z * ez : T(0)));
-            const T UR = -(vj.x * ex + vj.y * ey + (D == 3 ? vj.z * ez : T(0)));
-            if (kj == PH_WALL) {
-                // mirror state behind a wall moving with v_w: rho_i, p_i, 2 U_w - U_L
-                const T dU = T(2) * (UL - UR);
-                const T beta = limiter_beta(lim, dU, inv_c0);
-                const T Ps = p_i + beta * rho_i * c0 * dU * T(0.5);
-                const T f = Ps * g.dW * cp.vol_wall;
-                apx += f * ex; apy += f * ey; if (D == 3) apz += f * ez;
-                return;
-            }
-            const T drj = drho[j];
-            const T rho_j = cp.rho0[kj] + drj;
-            const T p_j = cp.c0sq * drj;
-            const T Vj = cp.mass[kj] / rho_j;
-            const T inv_rs = T(1) / (rho_i + rho_j);
-            const T pbar = (rho_i * p_j + rho_j * p_i) * inv_rs;     // Eq. 12
-            const T dU = UL - UR;
-            const T beta = limiter_beta(lim, dU, inv_c0);           // Eq. 11
-            const T Ps = pbar + beta * c0 * rho_i * rho_j * dU * inv_rs;   // Eq. 8
-            const T f = Ps * g.dW * Vj;
+
+    // pressure (Eqs. 7-12); walls by their mirror state
+    const auto pressure = [&](uint32_t, const V4<T> &sj, const V4<T> &vj, T rx, T ry, T rz, T r2) {
+        const PairGeo<T> g = geo(cp, r2);
+        const T ex = rx * g.inv_r, ey = ry * g.inv_r, ez = D == 3 ? rz * g.inv_r : T(0);
+        const uint32_t kj = phase_of(w_bits(sj.w));
+        const T UL = -(vi.x * ex + vi.y * ey + (D == 3 ? vi.z * ez : T(0)));
+        const T UR = -(vj.x * ex + vj.y * ey + (D == 3 ? vj.z * ez : T(0)));
+        if (kj == PH_WALL) {
+            // mirror state behind a wall moving with v_w: rho_i, p_i, 2 U_w - U_L
+            const T dU = T(2) * (UL - UR);
+            const T beta = limiter_beta(lim, dU, cp.inv_c0);
+            const T Ps = p_i + beta * rho_i * cp.c0 * dU * T(0.5);
+            const T f = Ps * g.dW * cp.vol_wall;
             apx += f * ex; apy += f * ey; if (D == 3) apz += f * ez;
-            if (!surface_on) return;
-            const V4<T> gj = gradC[j];
-            if (gi.w == T(0) && gj.w == T(0)) return;                // every surface term vanishes
-            const bool if_j = gj.w * cp.h > cp.nhat_eps;
-            const T inv_gj = if_j ? T(1) / gj.w : T(0);
-            const T njx = gj.x * inv_gj, njy = gj.y * inv_gj, njz = gj.z * inv_gj;
-            const T gam_gj = if_j ? cp.gamma * gj.w : T(0);
-            const T nie = nix * ex + niy * ey + niz * ez;
-            const T nje = njx * ex + njy * ey + njz * ez;
-            // Pi e = gamma |gradC| (e - n (n.e))   (Eq. 24)
-            const T pix = gam_gi * (ex - nix * nie), piy = gam_gi * (ey - niy * nie), piz = gam_gi * (ez - niz * nie);
-            const T pjx = gam_gj * (ex - njx * nje), pjy = gam_gj * (ey - njy * nje), pjz = gam_gj * (ez - njz * nje);
-            const bool same = kj == ki;
-            const T sg = (same || d.grad_mode == 1) ? T(1) : T(-1);
-            const T bx = T(0.5) * (gi.x + sg * gj.x), by = T(0.5) * (gi.y + sg * gj.y),
-                    bz = T(0.5) * (gi.z + sg * gj.z);
-            const T bn = sqrt(bx * bx + by * by + bz * bz);
-            const T Cij = same ? T(0) : T(1);
-            // C-hat e (Eq. 30 with the selected contraction)
-            T cx, cy, cz;
-            if (d.penalty_form == 0) {
-                const T fac = bn > T(0) ? g.r * (bx * ex + by * ey + bz * ez) / bn : T(0);
-                cx = Cij * ex - fac * bx; cy = Cij * ey - fac * by; cz = Cij * ez - fac * bz;
-            } else {
-                const T s = Cij - bn * g.r;
-                cx = s * ex; cy = s * ey; cz = s * ez;
-            }
-            // N-bar C-hat e = (n_i (n_i.c) + n_j (n_j.c)) / 2
-            const T nic = nix * cx + niy * cy + niz * cz;
-            const T njc = njx * cx + njy * cy + njz * cz;
-            const T qx = T(0.5) * (nix * nic + njx * njc), qy = T(0.5) * (niy * nic + njy * njc),
-                    qz = T(0.5) * (niz * nic + njz * njc);
-            const T pen = xg * g.inv_r;
-            T sx, sy, sz;
-            if (same) {   // Eq. 33, first line; T-bar c = c - N-bar c
-                sx = pix + pjx + pen * (cx - qx);
-                sy = piy + pjy + pen * (cy - qy);
-                sz = piz + pjz + pen * (cz - qz);
-            } else {      // Eq. 33, second line
-                const T a = cp.two_phi[kj], b = cp.two_phi[ki], c = cp.four_phi_phi * pen;
-                sx = a * pix + b * pjx - c * qx;
-                sy = a * piy + b * pjy - c * qy;
-                sz = a * piz + b * pjz - c * qz;
-            }
-            const T w = g.dW * Vj;
-            asx += sx * w; asy += sy * w; if (D == 3) asz += sz * w;
-        });
+            return;
+        }
+        const T drj = vj.w;
+        const T rho_j = sel(kj, cp.rho0[0], cp.rho0[1]) + drj;
+        const T p_j = cp.c0sq * drj;
+        const T Vj = div_fast(sel(kj, cp.mass[0], cp.mass[1]), rho_j);
+        const T inv_rs = div_fast(T(1), rho_i + rho_j);
+        const T pbar = (rho_i * p_j + rho_j * p_i) * inv_rs;     // Eq. 12
+        const T dU = UL - UR;
+        const T beta = limiter_beta(lim, dU, cp.inv_c0);        // Eq. 11
+        const T Ps = pbar + beta * cp.c0 * rho_i * rho_j * dU * inv_rs;   // Eq. 8
+        const T f = Ps * g.dW * Vj;
+        apx += f * ex; apy += f * ey; if (D == 3) apz += f * ez;
+    };
+
+    // surface stress and penalty (Eqs. 24, 26, 30, 33); walls take no part
+    const V4<T> gi = d.n_fluid_phases == 2 ? gradC[i] : V4<T>{0, 0, 0, 0};
+    const auto surface = [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
+        const uint32_t kj = phase_of(w_bits(sj.w));
+        if (kj == PH_WALL) return;
+        const V4<T> gj = gradC[j];
+        if (gi.w == T(0) && gj.w == T(0)) return;                // every surface term vanishes
+        const PairGeo<T> g = geo(cp, r2);
+        const T ex = rx * g.inv_r, ey = ry * g.inv_r, ez = D == 3 ? rz * g.inv_r : T(0);
+        const T rho_j = sel(kj, cp.rho0[0], cp.rho0[1]) + vel[j].w;
+        const T Vj = div_fast(sel(kj, cp.mass[0], cp.mass[1]), rho_j);
+        const bool if_i = gi.w * cp.h > cp.nhat_eps;
+        const T inv_gi = if_i ? div_fast(T(1), gi.w) : T(0);
+        const T nix = gi.x * inv_gi, niy = gi.y * inv_gi, niz = gi.z * inv_gi;
+        const T gam_gi = if_i ? cp.gamma * gi.w : T(0);
+        const bool if_j = gj.w * cp.h > cp.nhat_eps;
+        const T inv_gj = if_j ? div_fast(T(1), gj.w) : T(0);
+        const T njx = gj.x * inv_gj, njy = gj.y * inv_gj, njz = gj.z * inv_gj;
+        const T gam_gj = if_j ? cp.gamma * gj.w : T(0);
+        const T nie = nix * ex + niy * ey + niz * ez;
+        const T nje = njx * ex + njy * ey + njz * ez;
+        // Pi e = gamma |gradC| (e - n (n.e))   (Eq. 24)
+        const T pix = gam_gi * (ex - nix * nie), piy = gam_gi * (ey - niy * nie), piz = gam_gi * (ez - niz * nie);
+        const T pjx = gam_gj * (ex - njx * nje), pjy = gam_gj * (ey - njy * nje), pjz = gam_gj * (ez - njz * nje);
+        const bool same = kj == ki;
+        const T sg = (same || d.grad_mode == 1) ? T(1) : T(-1);
+        const T bx = T(0.5) * (gi.x + sg * gj.x), by = T(0.5) * (gi.y + sg * gj.y),
+                bz = T(0.5) * (gi.z + sg * gj.z);
+        const T b2 = bx * bx + by * by + bz * bz;
+        const T inv_bn = b2 > T(0) ? rsqrt_fast(b2) : T(0);
+        const T Cij = same ? T(0) : T(1);
+        // C-hat e (Eq. 30 with the selected contraction)
+        T cx, cy, cz;
+        if (d.penalty_form == 0) {
+            const T fac = g.r * (bx * ex + by * ey + bz * ez) * inv_bn;
+            cx = Cij * ex - fac * bx; cy = Cij * ey - fac * by; cz = Cij * ez - fac * bz;
+        } else {
+            const T s = Cij - b2 * inv_bn * g.r;
+            cx = s * ex; cy = s * ey; cz = s * ez;
+        }
+        // N-bar C-hat e = (n_i (n_i.c) + n_j (n_j.c)) / 2
+        const T nic = nix * cx + niy * cy + niz * cz;
+        const T njc = njx * cx + njy * cy + njz * cz;
+        const T qx = T(0.5) * (nix * nic + njx * njc), qy = T(0.5) * (niy * nic + njy * njc),
+                qz = T(0.5) * (niz * nic + njz * njc);
+        const T pen = cp.xi * cp.gamma * g.inv_r;
+        T sx, sy, sz;
+        if (same) {   // Eq. 33, first line; T-bar c = c - N-bar c
+            sx = pix + pjx + pen * (cx - qx);
+            sy = piy + pjy + pen * (cy - qy);
+            sz = piz + pjz + pen * (cz - qz);
+        } else {      // Eq. 33, second line
+            const T a = sel(kj, cp.two_phi[0], cp.two_phi[1]), b = sel(ki, cp.two_phi[0], cp.two_phi[1]),
+                    c = cp.four_phi_phi * pen;
+            sx = a * pix + b * pjx - c * qx;
+            sy = a * piy + b * pjy - c * qy;
+            sz = a * piz + b * pjz - c * qz;
+        }
+        const T w = g.dW * Vj;
+        asx += sx * w; asy += sy * w; if (D == 3) asz += sz * w;
+    };
+
+    const bool surface_on = d.n_fluid_phases == 2;
+    if constexpr (PASS == 2) {
+        if (surface_on) neighbors<LIST, T, D>(d, cp, starts, nbr, cnt, snap, i, si, pki, surface);
+        acc_surf[i] = V4<T>{asx, asy, asz, T(0)};
+        return 0.0;
+    } else if constexpr (PASS == 1) {
+        neighbors_aux<LIST, T, D>(d, cp, starts, nbr, cnt, snap, vel, i, si, pki, pressure);
+        if (surface_on && band[i]) {
+            const V4<T> as = acc_surf[i];
+            asx = as.x; asy = as.y; asz = as.z;
+        }
+    } else {
+        neighbors<LIST, T, D>(d, cp, starts, nbr, cnt, snap, i, si, pki,
+            [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
+                pressure(j, sj, vel[j], rx, ry, rz, r2);
+                if (surface_on) surface(j, sj, rx, ry, rz, r2);
+            });
+    }
     const T inv_rho = T(1) / rho_i;
     const V4<T> av = acc_visc[i];
     V4<T> vn;
     vn.x = vi.x + dt * (T(-2) * inv_rho * apx + inv_rho * asx + av.x);
     vn.y = vi.y + dt * (T(-2) * inv_rho * apy + inv_rho * asy + av.y);
     vn.z = D == 3 ? vi.z + dt * (T(-2) * inv_rho * apz + inv_rho * asz + av.z) : T(0);
-    vn.w = T(0);
+    vn.w = dri;                       // density deviation for sweep C
     vel_new[i] = vn;
-    drho_old[i] = dri;
     return speed2(vn, D);
 }
 
@@ -809,48 +992,53 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
 template <bool LIST, typename T, int D>
 __device__ __forceinline__ void sweep_C(const CaseDesc &d, const CasePhys<T> &cp, T dt, int64_t i,
                                         const uint32_t *starts, const uint32_t *nbr, const uint32_t *cnt, const V4<T> *snap,
-                                        const T *drho_old, const V4<T> *vel_new, T *drho,
+                                        const V4<T> *vel_new, T *drho,
                                         V4<T> *vel, V4<T> *pos) {
     const V4<T> si = ld4(snap + i);
     const uint32_t pki = w_bits(si.w);
     const uint32_t ki = phase_of(pki);
     if (ki == PH_WALL) return;
-    const T dri = drho_old[i];
-    const T rho_i = cp.rho0[ki] + dri;
-    const T p_i = cp.c0sq * dri;
-    const V4<T> vi = vel_new[i];
-    const T c0 = cp.c0;
+    V4<T> vi = vel_new[i];
+    const T dri = vi.w;
+    const T rho0_0 = cp.rho0[0], rho0_1 = cp.rho0[1], m_0 = cp.mass[0], m_1 = cp.mass[1];
+    const T c0 = cp.c0, c0sq = cp.c0sq, vol_wall = cp.vol_wall;
+    const T rho_i = sel(ki, rho0_0, rho0_1) + dri;
+    const T p_i = c0sq * dri;
     T s = 0;
-    neighbors<LIST, T, D>(d, cp, starts, nbr, cnt, snap, i, si, pki,
-        [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
+    neighbors_aux<LIST, T, D>(d, cp, starts, nbr, cnt, snap, vel_new, i, si, pki,
+        [&](uint32_t, const V4<T> &sj, const V4<T> &vj, T rx, T ry, T rz, T r2) {
             const PairGeo<T> g = geo(cp, r2);
             const uint32_t kj = phase_of(w_bits(sj.w));
-            const V4<T> vj = vel_new[j];
             const T dvx = vi.x - vj.x, dvy = vi.y - vj.y, dvz = D == 3 ? vi.z - vj.z : T(0);
             // (v_i - v_j).e = U_R - U_L
             const T dve = (dvx * rx + dvy * ry + dvz * rz) * g.inv_r;
             if (kj == PH_WALL) {          // v* = v_w
-                s += dve * g.dW * cp.vol_wall;
+                s += dve * g.dW * vol_wall;
                 return;
             }
-            const T drj = drho_old[j];
-            const T rho_j = cp.rho0[kj] + drj;
-            const T p_j = cp.c0sq * drj;
-            const T Vj = cp.mass[kj] / rho_j;
+            const T drj = vj.w;
+            const T rho_j = sel(kj, rho0_0, rho0_1) + drj;
+            const T p_j = c0sq * drj;
+            const T Vj = div_fast(sel(kj, m_0, m_1), rho_j);
             // (v_i - v*).e = U* - U_L = (Z_R (U_R - U_L) + p_i - p_j) / (Z_L + Z_R)
-            const T du = (rho_j * c0 * dve + (p_i - p_j)) / (c0 * (rho_i + rho_j));
+            const T du = div_fast(rho_j * c0 * dve + (p_i - p_j), c0 * (rho_i + rho_j));
             s += du * g.dW * Vj;
         });
-    drho[i] = dri + dt * (T(2) * rho_i * s);
+    const T dr_new = dri + dt * (T(2) * rho_i * s);
+    drho[i] = dr_new;
     V4<T> p = pos[i];
     p.x += dt * vi.x;
     p.y += dt * vi.y;
     if (D == 3) p.z += dt * vi.z;
     pos[i] = p;
+    vi.w = dr_new;
     vel[i] = vi;
 }
 
 // ---------------------------------------------------------- sweep kernels
+// Tiles are grouped by class (dimension, neighbour source) and each class is
+// launched with its own instantiation, so every kernel is compiled (and its
+// registers allocated) for one dimension and one neighbour source only.
 struct SweepArgs {
     const Tile *tiles;
     const CaseDesc *desc;
@@ -858,20 +1046,8 @@ struct SweepArgs {
     const uint32_t *starts;
     const uint32_t *nbr;
     const uint32_t *cnt;
+    int64_t tile0;                 // first tile of the launched class
 };
-
-// calls body.template operator()<LIST, D>() for the case's dimension and
-// neighbour source (block-uniform branch)
-#define SPH_DISPATCH(d, CALL)                                      \
-    do {                                                           \
-        if ((d).dim == 3) {                                        \
-            if ((d).nbr_mode == 0) { constexpr bool LIST = true; constexpr int D = 3; CALL; } \
-            else { constexpr bool LIST = false; constexpr int D = 3; CALL; }                   \
-        } else {                                                   \
-            if ((d).nbr_mode == 0) { constexpr bool LIST = true; constexpr int D = 2; CALL; } \
-            else { constexpr bool LIST = false; constexpr int D = 2; CALL; }                   \
-        }                                                          \
-    } while (0)
 
 // ---- L: neighbour list of the frozen configuration (fluid particles only)
 template <typename T, int D>
@@ -885,69 +1061,104 @@ __device__ __forceinline__ void build_list(const CaseDesc &d, const CasePhys<T> 
     const int64_t stride = d.p_end - d.p_begin;
     uint32_t *base = nbr + d.nbr_base + (i - d.p_begin);
     const uint32_t kmax = (uint32_t)d.nbr_k;
-    uint32_t c = 0;
-    bool overflow = false;
-    const bool coinc = walk<T, D>(d, cp, starts, snap, i, si, pki,
-        [&](uint32_t j, const V4<T> &sj, T, T, T, T) {
-            if (c >= kmax) { overflow = true; return; }
-            const uint32_t pkj = w_bits(sj.w);
-            const uint32_t code = cell_code<D>(cell_x<D>(pkj) - cx, cell_y<D>(pkj) - cy,
-                                               cell_z<D>(pkj) - cz);
-            base[(int64_t)c * stride] = (j << NBR_SHIFT) | code;
-            ++c;
-        });
-    cnt[i] = c;
+    const uint32_t other = phase_of(pki) ^ 1u;
+    uint32_t c = 0, c_other = 0;
+    bool overflow = false, coinc = false;
+    // two walks: neighbours of the other fluid phase, then all the rest
+    for (int part = 0; part < 2; ++part) {
+        coinc |= walk<T, D>(d, cp, starts, snap, i, si, pki,
+            [&](uint32_t j, const V4<T> &sj, T, T, T, T) {
+                const uint32_t pkj = w_bits(sj.w);
+                if ((phase_of(pkj) == other) != (part == 0)) return;
+                if (c >= kmax) { overflow = true; return; }
+                const uint32_t code = cell_code<D>(cell_x<D>(pkj) - cx, cell_y<D>(pkj) - cy,
+                                                   cell_z<D>(pkj) - cz);
+                base[(int64_t)c * stride] = (j << NBR_SHIFT) | code;
+                ++c;
+            });
+        if (part == 0) c_other = c;
+    }
+    cnt[i] = c | (c_other << 16);
     if (coinc) atomicCAS(status, 0, DEV_ERR_COINCIDENT);
     if (overflow) atomicCAS(status, 0, DEV_ERR_NBR_OVERFLOW);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_build_list(SweepArgs a, const V4<T> *snap, uint32_t *nbr, uint32_t *cnt) {
-    const Tile t = a.tiles[blockIdx.x];
+// ---- interface band of the frozen configuration: i, or one of its
+// neighbours, has neighbours of the other fluid phase
+template <typename T, int D, bool LIST>
+__global__ void __launch_bounds__(256) k_band(SweepArgs a, const V4<T> *snap, uint8_t *band) {
+    const Tile t = a.tiles[a.tile0 + blockIdx.x];
     if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
     const CaseDesc &d = a.desc[t.c];
-    if (d.nbr_mode != 0) return;
     const int64_t i = t.begin + threadIdx.x;
-    if (d.dim == 3) build_list<T, 3>(d, phys<T>(d), i, a.starts, snap, nbr, cnt, &a.st[t.c].status);
-    else build_list<T, 2>(d, phys<T>(d), i, a.starts, snap, nbr, cnt, &a.st[t.c].status);
+    const uint32_t ci = a.cnt[i];
+    bool b = (ci >> 16) != 0;
+    if (!b && d.n_fluid_phases == 2) {
+        const int64_t stride = d.p_end - d.p_begin;
+        const uint32_t *p = a.nbr + d.nbr_base + (i - d.p_begin);
+        const uint32_t c = ci & CNT_MASK;
+        for (uint32_t k = 0; k < c && !b; ++k, p += stride) b = (a.cnt[ld_list(p) >> NBR_SHIFT] >> 16) != 0;
+    }
+    band[i] = b ? 1 : 0;
 }
 
-template <typename T>
+template <typename T, int D, bool LIST>
+__global__ void __launch_bounds__(256) k_build_list(SweepArgs a, const V4<T> *snap, uint32_t *nbr, uint32_t *cnt) {
+    const Tile t = a.tiles[a.tile0 + blockIdx.x];
+    if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
+    const CaseDesc &d = a.desc[t.c];
+    const int64_t i = t.begin + threadIdx.x;
+    build_list<T, D>(d, phys<T>(d), i, a.starts, snap, nbr, cnt, &a.st[t.c].status);
+}
+
+template <typename T, int D, bool LIST>
 __global__ void SPH_SWEEP_BOUNDS k_sweep_M(SweepArgs a, const V4<T> *snap, const T *drho, V4<T> *bmat) {
-    const Tile t = a.tiles[blockIdx.x];
+    const Tile t = a.tiles[a.tile0 + blockIdx.x];
     if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
     const CaseDesc &d = a.desc[t.c];
     if (!d.tvf_on) return;
     const int64_t i = t.begin + threadIdx.x;
-    SPH_DISPATCH(d, (sweep_M<LIST, T, D>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, bmat,
-                                          &a.st[t.c].status)));
+    sweep_M<LIST, T, D>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, bmat, &a.st[t.c].status);
 }
 
-template <typename T>
+template <typename T, int D, bool LIST>
 __global__ void SPH_SWEEP_BOUNDS k_sweep_V(SweepArgs a, const V4<T> *snap, const T *drho, const V4<T> *vel,
-                                                 const V4<T> *bmat, V4<T> *acc_visc, V4<T> *pos) {
-    const Tile t = a.tiles[blockIdx.x];
+                                           const V4<T> *bmat, V4<T> *acc_visc, V4<T> *pos) {
+    const Tile t = a.tiles[a.tile0 + blockIdx.x];
     if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
     const CaseDesc &d = a.desc[t.c];
     const int64_t i = t.begin + threadIdx.x;
-    SPH_DISPATCH(d, (sweep_V<LIST, T, D>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, vel, bmat,
-                                          acc_visc, pos, &a.st[t.c].status)));
+    sweep_V<LIST, T, D>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, vel, bmat, acc_visc, pos,
+                        &a.st[t.c].status);
 }
 
-template <typename T>
+template <typename T, int D, bool LIST>
 __global__ void SPH_SWEEP_BOUNDS k_sweep_A(SweepArgs a, const V4<T> *snap, const T *drho, V4<T> *gradC) {
-    const Tile t = a.tiles[blockIdx.x];
+    const Tile t = a.tiles[a.tile0 + blockIdx.x];
     if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
     const CaseDesc &d = a.desc[t.c];
     const int64_t i = t.begin + threadIdx.x;
-    SPH_DISPATCH(d, (sweep_A<LIST, T, D>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, gradC)));
+    sweep_A<LIST, T, D>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, gradC);
 }
 
-template <typename T>
-__global__ void SPH_SWEEPB_BOUNDS k_sweep_B(SweepArgs a, const V4<T> *snap, const T *drho, const V4<T> *vel,
-                                                 const V4<T> *gradC, const V4<T> *acc_visc,
-                                                 V4<T> *vel_new, T *drho_old) {
-    const Tile t = a.tiles[blockIdx.x];
+// surface sum of the band particles (list classes only), before B
+template <typename T, int D, bool LIST>
+__global__ void SPH_SWEEP_BOUNDS k_sweep_S(SweepArgs a, const uint8_t *band, const V4<T> *snap, const V4<T> *vel,
+                                           const V4<T> *gradC, V4<T> *acc_surf) {
+    const Tile t = a.tiles[a.tile0 + blockIdx.x];
+    if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
+    const CaseDesc &d = a.desc[t.c];
+    const int64_t i = t.begin + threadIdx.x;
+    uint32_t ph;
+    sweep_B<LIST, 2, T, D>(d, phys<T>(d), T(0), i, a.starts, a.nbr, a.cnt, band, snap, vel, gradC, nullptr,
+                           acc_surf, nullptr, &ph);
+}
+
+template <typename T, int D, bool LIST>
+__global__ void SPH_SWEEPB_BOUNDS k_sweep_B(SweepArgs a, const uint8_t *band, const V4<T> *snap, const V4<T> *vel,
+                                            const V4<T> *gradC, const V4<T> *acc_visc, V4<T> *acc_surf,
+                                            V4<T> *vel_new) {
+    const Tile t = a.tiles[a.tile0 + blockIdx.x];
     if (!a.st[t.c].active) return;                 // uniform per block
     const CaseDesc &d = a.desc[t.c];
     double v2 = 0.0;
@@ -955,8 +1166,8 @@ __global__ void SPH_SWEEPB_BOUNDS k_sweep_B(SweepArgs a, const V4<T> *snap, cons
     if ((int)threadIdx.x < t.n) {
         const int64_t i = t.begin + threadIdx.x;
         const T dt = (T)a.st[t.c].dt;
-        SPH_DISPATCH(d, (v2 = sweep_B<LIST, T, D>(d, phys<T>(d), dt, i, a.starts, a.nbr, a.cnt, snap, drho,
-                                                   vel, gradC, acc_visc, vel_new, drho_old, &ph)));
+        v2 = sweep_B<LIST, LIST ? 1 : 0, T, D>(d, phys<T>(d), dt, i, a.starts, a.nbr, a.cnt, band, snap, vel,
+                                               gradC, acc_visc, acc_surf, vel_new, &ph);
     }
     unsigned long long m0 = ph == 0 ? (unsigned long long)__double_as_longlong(v2) : 0ull;
     unsigned long long m1 = ph == 1 ? (unsigned long long)__double_as_longlong(v2) : 0ull;
@@ -968,16 +1179,15 @@ __global__ void SPH_SWEEPB_BOUNDS k_sweep_B(SweepArgs a, const V4<T> *snap, cons
     }
 }
 
-template <typename T>
-__global__ void SPH_SWEEP_BOUNDS k_sweep_C(SweepArgs a, const V4<T> *snap, const T *drho_old,
-                                                 const V4<T> *vel_new, T *drho, V4<T> *vel, V4<T> *pos) {
-    const Tile t = a.tiles[blockIdx.x];
+template <typename T, int D, bool LIST>
+__global__ void SPH_SWEEP_BOUNDS k_sweep_C(SweepArgs a, const V4<T> *snap, const V4<T> *vel_new, T *drho,
+                                           V4<T> *vel, V4<T> *pos) {
+    const Tile t = a.tiles[a.tile0 + blockIdx.x];
     if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
     const CaseDesc &d = a.desc[t.c];
     const int64_t i = t.begin + threadIdx.x;
     const T dt = (T)a.st[t.c].dt;
-    SPH_DISPATCH(d, (sweep_C<LIST, T, D>(d, phys<T>(d), dt, i, a.starts, a.nbr, a.cnt, snap, drho_old,
-                                          vel_new, drho, vel, pos)));
+    sweep_C<LIST, T, D>(d, phys<T>(d), dt, i, a.starts, a.nbr, a.cnt, snap, vel_new, drho, vel, pos);
 }
 
 // ------------------------------------------------------------ read-back

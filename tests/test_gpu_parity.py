@@ -179,10 +179,10 @@ def test_profile_step_matches_graph_step():
 @pytest.mark.parametrize("dim", [2, 3])
 @pytest.mark.parametrize("precision", [32, 64])
 def test_list_and_cell_walk_agree(dim, precision):
-    # the neighbour list keeps the cell-walk order and the pair geometry is
-    # computed with explicitly rounded operations, so the two sources agree to
-    # rounding (the compiler may still contract the pair sums differently in
-    # the two call sites)
+    # the list holds the same neighbours with the same pair geometry, but
+    # other-phase neighbours first, and the surface sum runs in its own
+    # kernel over the interface band: the two sources agree to the rounding
+    # of a reordered sum
     case = small(dim)
     out = []
     for mode in (S.NBR_LIST, S.NBR_CELLS):
@@ -201,6 +201,36 @@ def test_list_and_cell_walk_agree(dim, precision):
             a, b = a - np.round(a), b - np.round(a)
         scale = np.abs(b).max()
         assert np.abs(a - b).max() <= tol * scale, k
+
+
+def test_profiled_launch_counts():
+    # one advection step of a two-phase list case: every per-substep kernel
+    # (criterion, A, S, B, C) runs once per substep
+    case = small(3)
+    h = gpu_case(case, 32)
+    prof = S.profile_step(h)
+    n_sub = S.case_info(h)["n_sub"]
+    S.destroy(h)
+    for g in ("criterion", "sweep_A", "sweep_S", "sweep_B", "sweep_C"):
+        assert prof[g][1] == n_sub, g
+    assert prof["rebuild"][1] == 10          # keys, 3 scans, scatter, cell sort, gather, copy-back, list, band
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_surface_band_covers_every_surface_pair(dim):
+    # a drop whose interface band holds a small share of the particles: the
+    # band-restricted surface kernel must give the same velocities as the
+    # cell walk, which evaluates the surface terms of every pair
+    case = sphcases.small_droplet(dim, 24 if dim == 2 else 14, R_frac=0.25, shape="mode2", amp=0.15)
+    out = []
+    for mode in (S.NBR_LIST, S.NBR_CELLS):
+        h = gpu_case(case, 64, nbr_mode=mode, max_substeps=1)
+        S.step(h, 1, check=False)
+        out.append(S.read_fields(h, S.FIELD_VEL, dim))
+        S.destroy(h)
+    scale = np.abs(out[1]).max()
+    assert scale > 0
+    assert np.abs(out[0] - out[1]).max() <= 1e-12 * scale
 
 
 def test_neighbor_overflow_is_reported():
