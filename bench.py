@@ -369,6 +369,32 @@ def run_serve(args):
     torch.cuda.set_device(0)
     specs = sphcases.served_stream(args.requests, rate=args.rate, n_hi=args.serve_n_hi)
     cases = [sp.build() for sp in specs]
+    # capacity first: a batch of the stream's first cases, one advection step
+    # each after a warm-up step; the offered load (arrival rate x mean fluid
+    # particles x substeps per request) must stay below 0.9 of it, else the
+    # substep count per request is lowered
+    probe = cases[:min(len(cases), args.capacity_cases)]
+    b = S.batch_create(args.precision)
+    hs = [S.case_from_spec(c, precision=args.precision) for c in probe]
+    for h in hs:
+        S.batch_add(b, h)
+    S.batch_step(b, 1)
+    s0 = [S.case_info(h)["n_sub"] for h in hs]
+    torch.cuda.synchronize()
+    tc = time.perf_counter()
+    S.batch_step(b, 2)
+    torch.cuda.synchronize()
+    tc = time.perf_counter() - tc
+    capacity = sum(c.n_fluid * (S.case_info(h)["n_sub"] - s) for c, h, s in zip(probe, hs, s0)) / tc
+    for h in hs:
+        S.batch_remove(b, h)
+        S.destroy(h)
+    S.batch_destroy(b)
+    mean_fluid = float(np.mean([c.n_fluid for c in cases]))
+    n_sub = args.serve_substeps
+    while n_sub > 1 and args.rate * mean_fluid * n_sub > 0.9 * capacity:
+        n_sub -= 1
+    offered = args.rate * mean_fluid * n_sub
     srv = serve.Server(precision=args.precision, budget_bytes=args.budget_gb * 1e9)
     srv.start()
     t0 = time.perf_counter()
@@ -377,7 +403,7 @@ def run_serve(args):
         delay = t0 + sp.arrival - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        futs.append(srv.submit(c, n_adv=args.serve_adv))
+        futs.append(srv.submit(c, n_sub=n_sub))
     res = [f.result(timeout=3600) for f in futs]
     wall = time.perf_counter() - t0
     srv.stop()
@@ -390,7 +416,9 @@ def run_serve(args):
             "p99_latency_s": round(float(np.percentile(lat, 99)), 4),
             "gpu_busy_fraction": round(st["busy_s"] / wall, 3), "rounds": st["rounds"],
             "failed": int(sum(1 for r in res if r.info["status"])),
-            "advection_steps_per_request": args.serve_adv, "budget_gb": args.budget_gb,
+            "substeps_per_request": n_sub, "substeps_requested": args.serve_substeps,
+            "capacity": round(capacity, 1), "offered_load": round(offered, 1),
+            "offered_fraction": round(offered / capacity, 3), "budget_gb": args.budget_gb,
             "particles_per_request_range": [5e3, args.serve_n_hi],
             "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
             "config": {"workload": "served_stream seed 20250321", "wall_s": round(wall, 2)}}
@@ -416,7 +444,9 @@ def main():
     ap.add_argument("--plain-sample", type=int, default=32)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=50.0)
-    ap.add_argument("--serve-adv", type=int, default=1)
+    ap.add_argument("--serve-substeps", type=int, default=128,
+                    help="acoustic substeps per served request (lowered to keep the offered load below 0.9 of capacity)")
+    ap.add_argument("--capacity-cases", type=int, default=24)
     ap.add_argument("--serve-n-hi", type=float, default=2e6)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     args = ap.parse_args()

@@ -277,6 +277,35 @@ int sphst_batch_size(sphst_batch b, int64_t *n_cases);
 /* Release the batch (members stay valid and leave it). */
 int sphst_batch_destroy(sphst_batch b);
 
+/* ------------------------------------------------------------ diagnostics */
+/* FP64 reductions over a case's fluid particles on the device, in a fixed
+ * summation order (the same state gives the same bits).  Phase k has mass
+ * m_k = rho0_k dp^dim per particle; p = c0^2 (rho - rho0) (Eq. 2).
+ *   momentum      sum m v                          (conserved by Eqs. 8, 26, 33)
+ *   kinetic       sum m |v|^2 / 2
+ *   count[k]      particles of fluid phase k (k = 0: first fluid phase added)
+ *   first         sum x over phase 0               (centroid = first / count[0])
+ *   second        sum x_a x_b over phase 0: xx, yy, zz, xy, xz, yz
+ *   p_in, n_in    sum and count of p over phase-0 particles with |x - center| < r_in
+ *   p_out, n_out  sum and count of p over phase-1 particles with |x - center| > r_out
+ *   n_nonfinite   particles with a non-finite position, velocity or density
+ * These give the Laplace jump of Eq. 37 (p_in/n_in - p_out/n_out), the drop's
+ * shape moments for the oscillation period (Eq. 35) and the momentum drift.
+ * center: 3 doubles (unused axes ignored).  Before the first step the
+ * staged input is reduced on the host.  Errors: INVALID_ARG, CUDA. */
+typedef struct {
+    double  momentum[3];
+    double  kinetic;
+    int64_t count[2];
+    double  first[3];
+    double  second[6];
+    double  p_in, p_out;
+    int64_t n_in, n_out;
+    int64_t n_nonfinite;
+} sphst_diagnostics;
+int sphst_diagnose(sphst_case c, const double *center, double r_in, double r_out,
+                   sphst_diagnostics *out);
+
 /* Device bytes one case of n particles needs (particle arrays, cell table,
  * scratch), for admission control.  Errors: INVALID_ARG. */
 int sphst_footprint_bytes(const sphst_case_params *params, int64_t n_particles,

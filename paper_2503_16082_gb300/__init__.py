@@ -56,6 +56,20 @@ class StepInfo(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad_"}
 
 
+class Diagnostics(C.Structure):
+    _fields_ = [("momentum", C.c_double * 3), ("kinetic", C.c_double), ("count", C.c_int64 * 2),
+                ("first", C.c_double * 3), ("second", C.c_double * 6), ("p_in", C.c_double),
+                ("p_out", C.c_double), ("n_in", C.c_int64), ("n_out", C.c_int64),
+                ("n_nonfinite", C.c_int64)]
+
+    def as_dict(self):
+        out = {}
+        for f, _ in self._fields_:
+            v = getattr(self, f)
+            out[f] = list(v) if hasattr(v, "__len__") else v
+        return out
+
+
 class SphstError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"sphst error {code}: {msg}")
@@ -88,6 +102,7 @@ EXPORTS = {
     "sphst_batch_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "sphst_batch_destroy": (C.c_int, [C.c_void_p]),
     "sphst_footprint_bytes": (C.c_int, [C.POINTER(CaseParams), C.c_int64, C.POINTER(C.c_int64)]),
+    "sphst_diagnose": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.POINTER(Diagnostics)]),
 }
 
 _lib = None
@@ -210,6 +225,17 @@ def debug_neighbor_counts(case):
     cnt = np.zeros(max(n, 1), dtype=np.int32)
     _check(load().sphst_debug_neighbor_counts(case, cnt.ctypes.data, n), "debug_neighbor_counts")
     return cnt[:n]
+
+
+def diagnose(case, center=(0.0, 0.0, 0.0), r_in: float = 0.0, r_out: float = float("inf")) -> dict:
+    """FP64 device reductions of a case (sphst_diagnose): momentum, kinetic
+    energy, phase counts, phase-0 first and second moments, Laplace sampling
+    sums around `center`, non-finite count."""
+    c = np.zeros(3, dtype=np.float64)
+    c[:len(center)] = center
+    out = Diagnostics()
+    _check(load().sphst_diagnose(case, c.ctypes.data, float(r_in), float(r_out), C.byref(out)), "diagnose")
+    return out.as_dict()
 
 
 PROFILE_GROUPS = ("rebuild", "setup", "criterion", "sweep_A", "sweep_B", "sweep_C", "sweep_S")

@@ -124,6 +124,10 @@ template <typename T> static CasePhys<T> phys_of(const CaseRec *c) {
     p.c0sq = (T)(P.c0 * P.c0);
     p.inv_c0 = (T)(1.0 / P.c0);
     p.gamma = (T)P.gamma;
+    // limiter (Eq. 11): density reading min(max(3 dU / c0, 0), 1); beta = 1; beta = 0
+    p.beta_k = (T)(P.limiter == SPHST_LIMITER_DENSITY ? 3.0 / P.c0 : 0.0);
+    p.beta_lo = (T)(P.limiter == SPHST_LIMITER_NONE ? 1.0 : 0.0);
+    p.beta_hi = (T)(P.limiter == SPHST_LIMITER_ZERO ? 0.0 : 1.0);
     p.xi = (T)xi;
     for (int k = 0; k < 2; ++k) {
         p.rho0[k] = (T)c->rho0[k];
@@ -175,7 +179,7 @@ int64_t footprint(const sphst_case_params *P, int64_t n) {
     int bits = 0;
     while ((double)(1 << bits) < side) ++bits;
     const int64_t table = ((int64_t)1 << (P->dim * bits)) * 4 + 4;
-    return per * n + table + 4096;
+    return per * n + table + 4096 + (int64_t)(DIAG_BLOCKS + 1) * DIAG_Q * 8;
 }
 
 // Move `cases` into one new engine (copying resident state), release
@@ -391,6 +395,62 @@ int sphst_profile_step(sphst_case c, double *kernel_ms, int64_t *launches) {
 int sphst_case_info(sphst_case c, sphst_step_info *info) {
     if (!c || !info) { set_error("NULL argument"); return SPHST_ERR_INVALID_ARG; }
     *info = c->r.info;
+    return SPHST_OK;
+}
+
+// q[] layout: see k_diag_partial (DIAG_Q quantities)
+static void diag_from_q(const double *q, sphst_diagnostics *out) {
+    for (int a = 0; a < 3; ++a) out->momentum[a] = q[a];
+    out->kinetic = q[3];
+    out->count[0] = (int64_t)q[4];
+    out->count[1] = (int64_t)q[5];
+    for (int a = 0; a < 3; ++a) out->first[a] = q[6 + a];
+    for (int a = 0; a < 6; ++a) out->second[a] = q[9 + a];
+    out->p_in = q[15];
+    out->p_out = q[16];
+    out->n_in = (int64_t)q[17];
+    out->n_out = (int64_t)q[18];
+    out->n_nonfinite = (int64_t)q[19];
+}
+
+int sphst_diagnose(sphst_case c, const double *center, double r_in, double r_out, sphst_diagnostics *out) {
+    if (!c || !center || !out) { set_error("NULL argument"); return SPHST_ERR_INVALID_ARG; }
+    if (!(r_in >= 0.0) || !(r_out >= 0.0)) { set_error("r_in and r_out must be >= 0"); return SPHST_ERR_INVALID_ARG; }
+    const CaseRec &r = c->r;
+    double q[DIAG_Q] = {0};
+    if (r.engine) {
+        const int rc = r.engine->diagnose(r.slot, center, r_in, r_out, q);
+        if (rc) return rc;
+        diag_from_q(q, out);
+        return SPHST_OK;
+    }
+    // staged input, before the first step: the same sums on the host
+    const int dim = r.P.dim;
+    const double vol = dim == 2 ? r.P.dx * r.P.dx : r.P.dx * r.P.dx * r.P.dx;
+    for (int64_t i = 0; i < r.n; ++i) {
+        const int k = r.kind[i];
+        if (k > 1) continue;
+        const double *x = &r.pos[3 * i], *v = &r.vel[3 * i];
+        const double m = r.rho0[k] * vol;
+        bool finite = std::isfinite(r.rho[i]);
+        for (int a = 0; a < 3; ++a) finite = finite && std::isfinite(x[a]) && std::isfinite(v[a]);
+        if (!finite) { q[19] += 1.0; continue; }
+        for (int a = 0; a < 3; ++a) q[a] += m * v[a];
+        q[3] += 0.5 * m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        q[4 + k] += 1.0;
+        double r2 = 0.0;
+        for (int a = 0; a < dim; ++a) r2 += (x[a] - center[a]) * (x[a] - center[a]);
+        const double pr = r.P.c0 * r.P.c0 * (r.rho[i] - r.rho0[k]);
+        if (k == 0) {
+            for (int a = 0; a < 3; ++a) q[6 + a] += x[a];
+            q[9] += x[0] * x[0]; q[10] += x[1] * x[1]; q[11] += x[2] * x[2];
+            q[12] += x[0] * x[1]; q[13] += x[0] * x[2]; q[14] += x[1] * x[2];
+            if (r2 < r_in * r_in) { q[15] += pr; q[17] += 1.0; }
+        } else if (r2 > r_out * r_out) {
+            q[16] += pr; q[18] += 1.0;
+        }
+    }
+    diag_from_q(q, out);
     return SPHST_OK;
 }
 

@@ -63,6 +63,8 @@ struct Engine {
     virtual int read_field(int slot, int field, double *host) = 0;
     virtual int debug_keys(int slot, uint64_t *keys, int64_t *ids) = 0;
     virtual int debug_counts(int slot, int32_t *counts) = 0;
+    // FP64 reductions of one case (DIAG_Q doubles, layout of k_diag_final)
+    virtual int diagnose(int slot, const double *center, double r_in, double r_out, double *q) = 0;
     // device copies used when a case moves to another engine
     virtual void *dev_array(int which) = 0;
     virtual CaseState *dev_state() = 0;

@@ -53,6 +53,7 @@ template <typename T> struct EngineT : Engine {
     Tile *d_tiles = nullptr;
     int *d_loop_flag = nullptr;
     double *d_read = nullptr;              // read-back buffer
+    double *d_diag = nullptr;              // diagnostics partials + result
     void *arena = nullptr;
     int64_t n = 0, table_total = 0, n_tiles = 0, max_case_n = 0;
     int64_t cls_b[4] = {0, 0, 0, 0}, cls_n[4] = {0, 0, 0, 0};   // tile range of each class
@@ -157,6 +158,7 @@ template <typename T> struct EngineT : Engine {
         size_t o_read = take((size_t)std::max<int64_t>(max_case_n, 1) * 3 * sizeof(double));
         size_t o_nbr = take((size_t)std::max<int64_t>(nbr_total, 1) * 4), o_ncnt = take(nn * 4);
         size_t o_band = take(nn);
+        size_t o_diag = take((size_t)(DIAG_BLOCKS + 1) * DIAG_Q * sizeof(double));
         cudaError_t e = cudaMalloc(&arena, off);
         if (e != cudaSuccess) {
             arena = nullptr;
@@ -179,6 +181,7 @@ template <typename T> struct EngineT : Engine {
         nbr = (uint32_t *)(b + o_nbr);
         nbr_cnt = (uint32_t *)(b + o_ncnt);
         band = (uint8_t *)(b + o_band);
+        d_diag = (double *)(b + o_diag);
         SPH_CK(cudaMemsetAsync(arena, 0, off, stream));
         // tiles, grouped by class
         std::vector<Tile> tiles;
@@ -465,6 +468,22 @@ template <typename T> struct EngineT : Engine {
         SPH_CK(cudaGetLastError());
         const int w = (field == 0 || field == 1 || field == 5 || field == 6) ? d.dim : 1;
         SPH_CK(cudaMemcpyAsync(host, d_read, (size_t)m * w * sizeof(double), cudaMemcpyDeviceToHost, stream));
+        SPH_CK(cudaStreamSynchronize(stream));
+        return SPHST_OK;
+    }
+
+    int diagnose(int slot, const double *center, double r_in, double r_out, double *q) override {
+        const CaseDesc &d = h_desc[slot];
+        const int64_t m = d.p_end - d.p_begin;
+        const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, DIAG_BLOCKS));
+        double *res = d_diag + (size_t)DIAG_BLOCKS * DIAG_Q;
+        const double rin2 = r_in > 0.0 ? r_in * r_in : 0.0;
+        const double rout2 = r_out * r_out;
+        k_diag_partial<T><<<nb, 256, 0, stream>>>(d_desc, slot, pos, vel, drho, center[0], center[1], center[2],
+                                                  rin2, rout2, d_diag);
+        k_diag_final<<<1, 32, 0, stream>>>(d_diag, nb, res);
+        SPH_CK(cudaGetLastError());
+        SPH_CK(cudaMemcpyAsync(q, res, DIAG_Q * sizeof(double), cudaMemcpyDeviceToHost, stream));
         SPH_CK(cudaStreamSynchronize(stream));
         return SPHST_OK;
     }

@@ -81,6 +81,7 @@ template <typename T> struct CasePhys {
     T vol_wall;                // dp^dim
     T nhat_eps;                // |gradC| h threshold of an interface particle
     T tvf_coef;                // -alpha h^2 (Eq. 14, sign reading)
+    T beta_k, beta_lo, beta_hi; // Eq. 11 limiter as min(max(beta_k dU, lo), hi) per reading
 };
 
 struct CaseDesc {
@@ -131,5 +132,9 @@ enum : int32_t { DEV_OK = 0, DEV_ERR_NONFINITE = 1, DEV_ERR_DOMAIN = 2, DEV_ERR_
                  DEV_ERR_STALLED = 4, DEV_ERR_NBR_OVERFLOW = 5 };
 
 struct Tile { int32_t c; int32_t n; int64_t begin; };   // one block: n particles of case c
+
+// diagnostics: quantities per reduction and maximum partial blocks
+constexpr int DIAG_Q = 20;
+constexpr int DIAG_BLOCKS = 1024;
 
 }  // namespace sphst

@@ -27,6 +27,8 @@
 //   SPHST_LIST_UNROLL  unroll factor of the neighbour-list loop
 //   SPHST_LIST_PREFETCH 1: load list entry k+1 while pair k is evaluated
 //   SPHST_FAST_DIV     1: FP32 pair divisions through the SFU reciprocal
+//   SPHST_F32X2        1: x/y components of the FP32 pair geometry and sums in
+//                      packed two-lane instructions (sm_100 and later)
 //   SPHST_PIPE         1: sweeps B and C load the next neighbour's position and
 //                      state while the current pair is evaluated
 #ifndef SPHST_LIST_PREFETCH
@@ -37,6 +39,9 @@
 #endif
 #ifndef SPHST_PIPE
 #define SPHST_PIPE 0
+#endif
+#ifndef SPHST_F32X2
+#define SPHST_F32X2 1
 #endif
 #ifndef SPHST_LIST_LDCS
 #define SPHST_LIST_LDCS 1
@@ -108,6 +113,54 @@ __device__ __forceinline__ double code_off(uint32_t b, double) {
     return __dsub_rn(__longlong_as_double(0x4330000000000000ll | (long long)b), 4503599627370497.0);
 }
 
+// Two-lane (x, y) arithmetic, each lane rounded once: packed FP32
+// instructions for float, scalar operations for double.
+template <typename T> struct L2 { T x, y; };
+template <typename T> __device__ __forceinline__ L2<T> l2(T x, T y) { return L2<T>{x, y}; }
+__device__ __forceinline__ L2<float> fma2(L2<float> a, L2<float> b, L2<float> c) {
+#if SPHST_F32X2
+    const float2 r = __ffma2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y), make_float2(c.x, c.y));
+    return L2<float>{r.x, r.y};
+#else
+    return L2<float>{__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y)};
+#endif
+}
+__device__ __forceinline__ L2<float> add2(L2<float> a, L2<float> b) {
+#if SPHST_F32X2
+    const float2 r = __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+    return L2<float>{r.x, r.y};
+#else
+    return L2<float>{__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)};
+#endif
+}
+__device__ __forceinline__ L2<float> mul2(L2<float> a, L2<float> b) {
+#if SPHST_F32X2
+    const float2 r = __fmul2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+    return L2<float>{r.x, r.y};
+#else
+    return L2<float>{__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)};
+#endif
+}
+__device__ __forceinline__ L2<double> fma2(L2<double> a, L2<double> b, L2<double> c) {
+    return L2<double>{__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y)};
+}
+__device__ __forceinline__ L2<double> add2(L2<double> a, L2<double> b) {
+    return L2<double>{__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)};
+}
+__device__ __forceinline__ L2<double> mul2(L2<double> a, L2<double> b) {
+    return L2<double>{__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)};
+}
+// 1 - b for the 2-bit offset fields (bx, by), exactly: -(2^23 + b) + (2^23 + 1)
+__device__ __forceinline__ L2<float> neg_code_off2(uint32_t bx, uint32_t by, float) {
+    return add2(l2(__uint_as_float(0xCB000000u | bx), __uint_as_float(0xCB000000u | by)),
+                l2(8388609.0f, 8388609.0f));
+}
+__device__ __forceinline__ L2<double> neg_code_off2(uint32_t bx, uint32_t by, double) {
+    return add2(l2(__longlong_as_double((long long)(0xC330000000000000ull | bx)),
+                   __longlong_as_double((long long)(0xC330000000000000ull | by))),
+                l2(4503599627370497.0, 4503599627370497.0));
+}
+
 // a ? x1 : x0 for the two fluid phases' constants (no indexed loads)
 template <typename T> __device__ __forceinline__ T sel(uint32_t k, T x0, T x1) { return k ? x1 : x0; }
 
@@ -150,13 +203,16 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return v;
 }
 
-// Eq. 11 dissipation limiter (readings selected by the case)
-template <typename T> __device__ __forceinline__ T limiter_beta(int mode, T dU, T inv_c0) {
-    if (mode == 1) return T(1);
-    if (mode == 2) return T(0);
-    T b = T(3) * dU * inv_c0;
-    return b < T(0) ? T(0) : (b > T(1) ? T(1) : b);
-}
+// Eq. 11 dissipation limiter, branch-free: min(max(k dU, lo), hi) with the
+// case's (k, lo, hi) = (3 / c0, 0, 1) for the density reading, (0, 1, 1) for
+// beta = 1 and (0, 0, 0) for beta = 0
+__device__ __forceinline__ float clamp_lh(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
+__device__ __forceinline__ double clamp_lh(double x, double lo, double hi) { return fmin(fmax(x, lo), hi); }
+template <typename T> struct Limiter {
+    T k, lo, hi;
+    __device__ __forceinline__ explicit Limiter(const CasePhys<T> &cp) : k(cp.beta_k), lo(cp.beta_lo), hi(cp.beta_hi) {}
+    __device__ __forceinline__ T operator()(T dU) const { return clamp_lh(k * dU, lo, hi); }
+};
 
 // --------------------------------------------------------------- cell walk
 // Calls f(j, snap_j, r_ij vector, r^2) for every j != i with 0 < r_ij < 2h in
@@ -268,8 +324,10 @@ __device__ __forceinline__ void walk_list_aux(const CaseDesc &d, const CasePhys<
     const uint32_t c = cnt[i] & CNT_MASK;
     const T cs = cp.cs;
     const auto pair = [&](uint32_t e, const V4<T> &sj, const V4<T> &aj) {
-        const T rx = sub_rn(fma_rn(-code_off(e & 3u, T()), cs, si.x), sj.x);
-        const T ry = sub_rn(fma_rn(-code_off((e >> 2) & 3u, T()), cs, si.y), sj.y);
+        // (s_i - o cs) - s_j per axis, each step rounded once as in the cell walk
+        const L2<T> t = fma2(neg_code_off2(e & 3u, (e >> 2) & 3u, T()), l2(cs, cs), l2(si.x, si.y));
+        const L2<T> rxy = fma2(l2(sj.x, sj.y), l2(T(-1), T(-1)), t);
+        const T rx = rxy.x, ry = rxy.y;
         T rz = T(0);
         if (D == 3) rz = sub_rn(fma_rn(-code_off((e >> 4) & 3u, T()), cs, si.z), sj.z);
         f(e >> NBR_SHIFT, sj, aj, rx, ry, rz, norm2<T, D>(rx, ry, rz));
@@ -358,6 +416,20 @@ __device__ __forceinline__ PairGeo<T> geo(const CasePhys<T> &cp, T r2) {
     g.dW = cp.kcoef * q * u * u * u;
     return g;
 }
+// the same with the kernel constants held in registers by the caller
+template <typename T> struct KernelGeo {
+    T inv_h, kcoef;
+    __device__ __forceinline__ explicit KernelGeo(const CasePhys<T> &cp) : inv_h(cp.inv_h), kcoef(cp.kcoef) {}
+    __device__ __forceinline__ PairGeo<T> operator()(T r2) const {
+        PairGeo<T> g;
+        g.inv_r = rsq(r2);
+        g.r = r2 * g.inv_r;
+        const T q = g.r * inv_h;
+        const T u = T(1) - T(0.5) * q;
+        g.dW = kcoef * q * u * u * u;
+        return g;
+    }
+};
 
 // ================================================================ rebuild
 // First placement of a freshly uploaded case: absolute FP64 positions ->
@@ -865,36 +937,43 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
     const T dri = vi.w;
     const T rho_i = sel(ki, cp.rho0[0], cp.rho0[1]) + dri;
     const T p_i = cp.c0sq * dri;
-    const int lim = d.limiter;
     T apx = 0, apy = 0, apz = 0, asx = 0, asy = 0, asz = 0;
+    const Limiter<T> limiter_beta(cp);
+    const T c0 = cp.c0, c0sq = cp.c0sq, vol_wall = cp.vol_wall;
+    const T rho0_0 = cp.rho0[0], rho0_1 = cp.rho0[1], m_0 = cp.mass[0], m_1 = cp.mass[1];
+    const KernelGeo<T> kgeo(cp);
 
     // pressure (Eqs. 7-12); walls by their mirror state
     const auto pressure = [&](uint32_t, const V4<T> &sj, const V4<T> &vj, T rx, T ry, T rz, T r2) {
-        const PairGeo<T> g = geo(cp, r2);
-        const T ex = rx * g.inv_r, ey = ry * g.inv_r, ez = D == 3 ? rz * g.inv_r : T(0);
+        const PairGeo<T> g = kgeo(r2);
+        const L2<T> exy = mul2(l2(rx, ry), l2(g.inv_r, g.inv_r));
+        const T ex = exy.x, ey = exy.y, ez = D == 3 ? rz * g.inv_r : T(0);
         const uint32_t kj = phase_of(w_bits(sj.w));
-        const T UL = -(vi.x * ex + vi.y * ey + (D == 3 ? vi.z * ez : T(0)));
-        const T UR = -(vj.x * ex + vj.y * ey + (D == 3 ? vj.z * ez : T(0)));
+        // U_L - U_R = (v_j - v_i).e  (Eq. 10, U = -v.e)
+        const L2<T> dvxy = fma2(l2(vi.x, vi.y), l2(T(-1), T(-1)), l2(vj.x, vj.y));
+        const T dUe = dvxy.x * ex + dvxy.y * ey + (D == 3 ? (vj.z - vi.z) * ez : T(0));
         if (kj == PH_WALL) {
             // mirror state behind a wall moving with v_w: rho_i, p_i, 2 U_w - U_L
-            const T dU = T(2) * (UL - UR);
-            const T beta = limiter_beta(lim, dU, cp.inv_c0);
-            const T Ps = p_i + beta * rho_i * cp.c0 * dU * T(0.5);
-            const T f = Ps * g.dW * cp.vol_wall;
-            apx += f * ex; apy += f * ey; if (D == 3) apz += f * ez;
+            const T dU = T(2) * dUe;
+            const T beta = limiter_beta(dU);
+            const T Ps = p_i + beta * rho_i * c0 * dU * T(0.5);
+            const T f = Ps * g.dW * vol_wall;
+            const L2<T> a = fma2(l2(f, f), exy, l2(apx, apy));
+            apx = a.x; apy = a.y; if (D == 3) apz += f * ez;
             return;
         }
         const T drj = vj.w;
-        const T rho_j = sel(kj, cp.rho0[0], cp.rho0[1]) + drj;
-        const T p_j = cp.c0sq * drj;
-        const T Vj = div_fast(sel(kj, cp.mass[0], cp.mass[1]), rho_j);
+        const T rho_j = sel(kj, rho0_0, rho0_1) + drj;
+        const T p_j = c0sq * drj;
+        const T Vj = div_fast(sel(kj, m_0, m_1), rho_j);
         const T inv_rs = div_fast(T(1), rho_i + rho_j);
         const T pbar = (rho_i * p_j + rho_j * p_i) * inv_rs;     // Eq. 12
-        const T dU = UL - UR;
-        const T beta = limiter_beta(lim, dU, cp.inv_c0);        // Eq. 11
-        const T Ps = pbar + beta * cp.c0 * rho_i * rho_j * dU * inv_rs;   // Eq. 8
+        const T dU = dUe;
+        const T beta = limiter_beta(dU);                        // Eq. 11
+        const T Ps = pbar + beta * c0 * rho_i * rho_j * dU * inv_rs;   // Eq. 8
         const T f = Ps * g.dW * Vj;
-        apx += f * ex; apy += f * ey; if (D == 3) apz += f * ez;
+        const L2<T> a = fma2(l2(f, f), exy, l2(apx, apy));
+        apx = a.x; apy = a.y; if (D == 3) apz += f * ez;
     };
 
     // surface stress and penalty (Eqs. 24, 26, 30, 33); walls take no part
@@ -1004,12 +1083,14 @@ __device__ __forceinline__ void sweep_C(const CaseDesc &d, const CasePhys<T> &cp
     const T c0 = cp.c0, c0sq = cp.c0sq, vol_wall = cp.vol_wall;
     const T rho_i = sel(ki, rho0_0, rho0_1) + dri;
     const T p_i = c0sq * dri;
+    const KernelGeo<T> kgeo(cp);
     T s = 0;
     neighbors_aux<LIST, T, D>(d, cp, starts, nbr, cnt, snap, vel_new, i, si, pki,
         [&](uint32_t, const V4<T> &sj, const V4<T> &vj, T rx, T ry, T rz, T r2) {
-            const PairGeo<T> g = geo(cp, r2);
+            const PairGeo<T> g = kgeo(r2);
             const uint32_t kj = phase_of(w_bits(sj.w));
-            const T dvx = vi.x - vj.x, dvy = vi.y - vj.y, dvz = D == 3 ? vi.z - vj.z : T(0);
+            const L2<T> dvxy = fma2(l2(vj.x, vj.y), l2(T(-1), T(-1)), l2(vi.x, vi.y));
+            const T dvx = dvxy.x, dvy = dvxy.y, dvz = D == 3 ? vi.z - vj.z : T(0);
             // (v_i - v_j).e = U_R - U_L
             const T dve = (dvx * rx + dvy * ry + dvz * rz) * g.inv_r;
             if (kj == PH_WALL) {          // v* = v_w
@@ -1188,6 +1269,86 @@ __global__ void SPH_SWEEP_BOUNDS k_sweep_C(SweepArgs a, const V4<T> *snap, const
     const int64_t i = t.begin + threadIdx.x;
     const T dt = (T)a.st[t.c].dt;
     sweep_C<LIST, T, D>(d, phys<T>(d), dt, i, a.starts, a.nbr, a.cnt, snap, vel_new, drho, vel, pos);
+}
+
+// ---------------------------------------------------------- diagnostics
+// FP64 sums over one case's fluid particles: per-block partials (warp
+// shuffles, then the block's warps in order), then one block adds the
+// partials in block order, so the result does not depend on scheduling.
+// Quantities: 0-2 momentum, 3 kinetic, 4-5 count per phase, 6-8 first
+// moments, 9-14 second moments, 15 p_in, 16 p_out, 17 n_in, 18 n_out,
+// 19 non-finite count.
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_diag_partial(const CaseDesc *desc, int c, const V4<T> *pos,
+                                                      const V4<T> *vel, const T *drho, double cx, double cy,
+                                                      double cz, double r_in2, double r_out2, double *partial) {
+    const CaseDesc &d = desc[c];
+    const int64_t n = d.p_end - d.p_begin;
+    const int dim = d.dim;
+    double q[DIAG_Q];
+#pragma unroll
+    for (int k = 0; k < DIAG_Q; ++k) q[k] = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = d.p_begin + k;
+        const V4<T> p = pos[i];
+        const uint32_t pk = w_bits(p.w);
+        const uint32_t ph = phase_of(pk);
+        if (ph > 1) continue;
+        const int cc[3] = {dim == 3 ? cell_x<3>(pk) : cell_x<2>(pk), dim == 3 ? cell_y<3>(pk) : cell_y<2>(pk),
+                           dim == 3 ? cell_z<3>(pk) : 0};
+        const double off[3] = {(double)p.x, (double)p.y, (double)p.z};
+        double x[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < dim; ++a) x[a] = d.origin[a] + (double)cc[a] * d.cs + off[a];
+        const V4<T> v4 = vel[i];
+        const double v[3] = {(double)v4.x, (double)v4.y, dim == 3 ? (double)v4.z : 0.0};
+        const double dr = (double)drho[i];
+        const double m = d.pd.mass[ph];
+        const bool finite = isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]) && isfinite(v[0]) &&
+                            isfinite(v[1]) && isfinite(v[2]) && isfinite(dr);
+        if (!finite) { q[19] += 1.0; continue; }
+        q[0] += m * v[0]; q[1] += m * v[1]; q[2] += m * v[2];
+        q[3] += 0.5 * m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        q[4 + ph] += 1.0;
+        const double rx = x[0] - cx, ry = x[1] - cy, rz = dim == 3 ? x[2] - cz : 0.0;
+        const double r2 = rx * rx + ry * ry + rz * rz;
+        const double pr = d.c0 * d.c0 * dr;
+        if (ph == 0) {
+            q[6] += x[0]; q[7] += x[1]; q[8] += x[2];
+            q[9] += x[0] * x[0]; q[10] += x[1] * x[1]; q[11] += x[2] * x[2];
+            q[12] += x[0] * x[1]; q[13] += x[0] * x[2]; q[14] += x[1] * x[2];
+            if (r2 < r_in2) { q[15] += pr; q[17] += 1.0; }
+        } else if (r2 > r_out2) {
+            q[16] += pr; q[18] += 1.0;
+        }
+    }
+    __shared__ double sh[8][DIAG_Q];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < DIAG_Q; ++k) {
+        const double t = warp_sum_d(q[k]);
+        if (lane == 0) sh[w][k] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < DIAG_Q) {
+        double t = 0.0;
+        for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t += sh[ww][threadIdx.x];
+        partial[(int64_t)blockIdx.x * DIAG_Q + threadIdx.x] = t;
+    }
+}
+
+static __global__ void k_diag_final(const double *partial, int nblocks, double *out) {
+    if (threadIdx.x < DIAG_Q) {
+        double t = 0.0;
+        for (int b = 0; b < nblocks; ++b) t += partial[(int64_t)b * DIAG_Q + threadIdx.x];
+        out[threadIdx.x] = t;
+    }
 }
 
 // ------------------------------------------------------------ read-back

@@ -34,6 +34,36 @@ def laplace_jump(pos, p, phase, dx: float, h: float, drop_phase: int = 0, outer_
     return float(p[inner].mean() - p[outer].mean()), Reff
 
 
+def moments_from_diag(dg: dict, dim: int):
+    """(centroid, covariance) of the phase-0 particles from device sums."""
+    n = max(dg["count"][0], 1)
+    c = np.array(dg["first"]) / n
+    s = dg["second"]
+    M = np.array([[s[0], s[3], s[4]], [s[3], s[1], s[5]], [s[4], s[5], s[2]]]) / n
+    cov = M - np.outer(c, c)
+    return c[:dim], cov[:dim, :dim]
+
+
+def anisotropy_device(case, dim: int) -> float:
+    """Shape anisotropy of the drop from FP64 device reductions."""
+    from . import diagnose
+    _, cov = moments_from_diag(diagnose(case), dim)
+    if dim == 2:
+        return float(cov[0, 0] - cov[1, 1])
+    return float(cov[2, 2] - 0.5 * (cov[0, 0] + cov[1, 1]))
+
+
+def laplace_jump_device(case, dim: int, dx: float, h: float):
+    """(dp, R_eff) of the drop (phase 0) from two FP64 device reductions:
+    the first gives the centroid and R_eff, the second the sampling sums."""
+    from . import diagnose
+    first = diagnose(case)
+    c, _ = moments_from_diag(first, dim)
+    Reff = effective_radius(int(first["count"][0]), dx, dim)
+    dg = diagnose(case, tuple(c), 0.5 * Reff, Reff + 3.0 * h)
+    return float(dg["p_in"] / max(dg["n_in"], 1) - dg["p_out"] / max(dg["n_out"], 1)), Reff
+
+
 def anisotropy(pos, phase, drop_phase: int = 0) -> float:
     q = pos[phase == drop_phase]
     d = q - q.mean(axis=0)

@@ -57,6 +57,7 @@ class _Request:
     spec: object
     n_adv: Optional[int]
     t_end: Optional[float]
+    n_sub: Optional[int]
     params: dict
     submitted: float
     future: concurrent.futures.Future
@@ -97,14 +98,15 @@ class Server:
         return footprint_bytes(p, spec.n)
 
     def submit(self, spec, n_adv: Optional[int] = None, t_end: Optional[float] = None,
-               **params) -> concurrent.futures.Future:
-        """Queue a solve; it stops after n_adv advection steps or at the first
-        advection-step boundary with t >= t_end."""
-        if n_adv is None and t_end is None:
-            raise ValueError("give n_adv or t_end")
+               n_sub: Optional[int] = None, **params) -> concurrent.futures.Future:
+        """Queue a solve; it stops after n_adv advection steps, or at the first
+        advection-step boundary with t >= t_end, or with at least n_sub
+        acoustic substeps done (whichever rule is given first)."""
+        if n_adv is None and t_end is None and n_sub is None:
+            raise ValueError("give n_adv, t_end or n_sub")
         fut: concurrent.futures.Future = concurrent.futures.Future()
         with self.lock:
-            r = _Request(self.next_id, spec, n_adv, t_end, params, time.perf_counter(), fut)
+            r = _Request(self.next_id, spec, n_adv, t_end, n_sub, params, time.perf_counter(), fut)
             r.footprint = self.footprint(spec, params)
             if r.footprint > self.budget:
                 fut.set_exception(SphstError(-8, f"request needs {r.footprint} B, budget {self.budget:.0f} B"))
@@ -118,6 +120,8 @@ class Server:
         if info["status"] != OK:
             return True
         if r.n_adv is not None and r.done_steps >= r.n_adv:
+            return True
+        if r.n_sub is not None and info["n_sub"] >= r.n_sub:
             return True
         return r.t_end is not None and info["t"] >= r.t_end
 

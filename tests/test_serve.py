@@ -73,3 +73,23 @@ def test_admission_waits_for_memory():
     for f in (S.FIELD_POS, S.FIELD_VEL):
         assert np.array_equal(r1.fields[f], r2.fields[f])
     srv.close()
+
+
+@pytest.mark.gpu
+def test_substep_stopping_rule():
+    # a request that asks for n acoustic substeps retires at the first
+    # advection-step boundary with at least n substeps done
+    a = sphcases.small_droplet(2, 20)
+    srv = serve.Server(budget_bytes=1e12)
+    f = srv.submit(a, n_sub=40)
+    srv.run_until_idle(timeout=60)
+    r = f.result()
+    assert r.info["n_sub"] >= 40
+    h = S.case_from_spec(a)
+    n_adv = r.info["n_adv"]
+    S.step(h, n_adv - 1)
+    assert S.case_info(h)["n_sub"] < 40          # one advection step fewer is not enough
+    S.step(h, 1)
+    assert np.array_equal(r.fields[S.FIELD_POS], S.read_fields(h, S.FIELD_POS, 2))
+    S.destroy(h)
+    srv.close()
