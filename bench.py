@@ -21,8 +21,10 @@ all ranks' particle-substeps over the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -37,6 +39,33 @@ import numpy as np  # noqa: E402
 import sphcases  # noqa: E402
 
 METRIC = "particle-substeps/s"
+
+# ncu summaries record the DRAM traffic of a kernel together with a hash of
+# the kernel sources it was taken on; the bench reports it only while the
+# sources are unchanged
+KERNEL_SOURCES = ("paper_2503_16082_gb300/csrc/sphst_kernels.cuh", "paper_2503_16082_gb300/csrc/sphst_internal.cuh")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(summary: str, kernel: str):
+    """DRAM bytes per launch of `kernel` from a profiles/ summary, or None if
+    the summary is missing or was taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", summary)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
+    if not m or m.group(1) != kernel_source_hash():
+        return None
+    m = re.search(r"traffic_bytes_per_launch\[" + re.escape(kernel) + r"\]:\s*([0-9]+)", text)
+    return int(m.group(1)) if m else None
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 # algorithmic FP32 flops per neighbour pair of sweep B (derivation in DESIGN.md):
 FP64_PEAK_TFLOPS = 1.25      # nominal FP64 (non-tensor) rate of a GB300
@@ -218,7 +247,9 @@ def run_ours(args, dist: Dist):
                 "kernel": f"k_sweep_B<{'float' if f32 else 'double'}, {spec.dim}, {'false' if surf_in_b else 'true'}>",
                 "achieved": round(achieved, 3),
                 "peak": round(peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4),
+                "traffic": (recorded_traffic(f"sweeps_{args.workload}_f{args.precision}_{args.nbr}.md", "k_sweep_B")
+                            if f32 and not surf_in_b else None),
                 "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if f32
                                 else "nominal FP64 rate of a GB300"),
                 "flops_per_launch": flops, "pairs": pairs, "pairs_surface": pairs_surf,
