@@ -48,7 +48,9 @@ class Params(C.Structure):
                 ("gamma", C.c_double), ("xi", C.c_double),
                 ("rho0", C.c_double * 2), ("eta", C.c_double * 2),
                 ("nhat_eps", C.c_double), ("max_substeps", C.c_int64),
-                ("tvf_alpha", C.c_double), ("cfl_ad", C.c_double), ("cfl_ac", C.c_double)]
+                ("tvf_alpha", C.c_double), ("cfl_ad", C.c_double), ("cfl_ac", C.c_double),
+                ("periodic", C.c_int32), ("pad2_", C.c_int32),
+                ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3)]
 
 
 class Info(C.Structure):
@@ -108,7 +110,8 @@ def make_params(dim: int, dx: float, h: float, c0: float, gamma: float,
                 limiter: int = 0, grad_mode: int = 0, nbr_mode: Optional[int] = None,
                 n: int = 0, n_threads: int = 0, nhat_eps: float = 1e-4,
                 max_substeps: int = 0, tvf_alpha: float = 0.2,
-                penalty_form: int = 0, cfl_ad: float = 0.1, cfl_ac: float = 0.6) -> Params:
+                penalty_form: int = 0, cfl_ad: float = 0.1, cfl_ac: float = 0.6,
+                periodic: int = 0, box_lo=(0.0, 0.0, 0.0), box_hi=(0.0, 0.0, 0.0)) -> Params:
     """Build a parameter block.  nbr_mode None: brute force below 4096
     particles, uniform grid above."""
     p = Params()
@@ -123,6 +126,9 @@ def make_params(dim: int, dx: float, h: float, c0: float, gamma: float,
     p.tvf_alpha = tvf_alpha
     p.penalty_form = penalty_form
     p.cfl_ad, p.cfl_ac = cfl_ad, cfl_ac
+    p.periodic = periodic
+    for a in range(3):
+        p.box_lo[a], p.box_hi[a] = box_lo[a], box_hi[a]
     return p
 
 
@@ -131,6 +137,10 @@ def params_for_case(case, **kw) -> Params:
     rho0, eta = case.fluid_props()
     kw.setdefault("xi", case.xi)
     kw.setdefault("cfl_ac", getattr(case, "cfl_ac", 0.6))
+    if getattr(case, "periodic", 0):
+        kw.setdefault("periodic", case.periodic)
+        kw.setdefault("box_lo", tuple(case.lo) + (0.0,) * (3 - len(case.lo)))
+        kw.setdefault("box_hi", tuple(case.hi) + (0.0,) * (3 - len(case.hi)))
     return make_params(case.dim, case.dx, case.h_factor * case.dx, case.c0,
                        case.gamma, rho0=tuple(rho0), eta=tuple(eta), n=case.n, **kw)
 

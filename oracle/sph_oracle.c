@@ -41,6 +41,11 @@
  *   C-hat       (the contraction) A A^T/|A| = |gradCbar| r_ij nbar nbar^T with
  *               nbar = gradCbar/|gradCbar|; the flag penalty_form = 1 takes
  *               A^T A/|A| = |gradCbar| r_ij e e^T instead.
+ *   periodic    an axis flagged periodic (the shear drop of Section 5.2 is
+ *               periodic in x) wraps positions into [box_lo, box_hi) and takes
+ *               every pair vector as its minimum image; the key grid of a
+ *               periodic axis has floor(L / cs0) cells of width L / that count
+ *               (cs0 = 2h (1 + 2^-16)), starting at box_lo.
  *   TVF         Eq. 14 with the sign that moves a particle away from the side
  *               where its neighbours crowd: dr_i = -alpha h^2 sum_j (B_i + B_j)
  *               grad_i W_ij V_j.  With the stated grad W convention
@@ -88,6 +93,9 @@ typedef struct {
     double tvf_alpha;     /* transport-velocity coefficient (0.2 in Section 3.2); 0: off */
     double cfl_ad;        /* advection factor of Eq. 16 (0.1 as printed) */
     double cfl_ac;        /* acoustic factor of Eq. 17 (0.6 as printed) */
+    int32_t periodic;     /* bit d set: axis d is periodic on [box_lo[d], box_hi[d]) */
+    int32_t pad2_;
+    double box_lo[3], box_hi[3];
 } ora_params;
 
 typedef struct {
@@ -113,6 +121,28 @@ static double dot3(const double *a, const double *b, int dim)
 }
 
 static double norm3(const double *a, int dim) { return sqrt(dot3(a, a, dim)); }
+
+static int is_periodic(const ora_params *P, int d) { return (P->periodic >> d) & 1; }
+
+/* minimum image of a pair vector on the periodic axes */
+static void min_image(const ora_params *P, double *rv)
+{
+    for (int d = 0; d < P->dim; ++d) {
+        if (!is_periodic(P, d)) continue;
+        double L = P->box_hi[d] - P->box_lo[d];
+        if (rv[d] > 0.5 * L) rv[d] -= L;
+        else if (rv[d] < -0.5 * L) rv[d] += L;
+    }
+}
+
+/* a coordinate of a periodic axis brought back into [box_lo, box_hi) */
+static double wrap_coord(const ora_params *P, int d, double x)
+{
+    if (!is_periodic(P, d)) return x;
+    double L = P->box_hi[d] - P->box_lo[d];
+    double y = x - L * floor((x - P->box_lo[d]) / L);
+    return y >= P->box_hi[d] ? y - L : y;
+}
 
 static void set_threads(const ora_params *P)
 {
@@ -180,6 +210,45 @@ static int cmp_i32(const void *a, const void *b)
     return (x > y) - (x < y);
 }
 
+/* |x_i - x_j|^2 of the pair's minimum image */
+static double pair_dist2(const ora_params *P, const double *xi, const double *xj)
+{
+    double rv[3] = {0, 0, 0};
+    for (int d = 0; d < P->dim; ++d) rv[d] = xi[d] - xj[d];
+    min_image(P, rv);
+    double r2 = 0.0;
+    for (int d = 0; d < P->dim; ++d) r2 += rv[d] * rv[d];
+    return r2;
+}
+
+/* cell of a position in the search grid */
+static void grid_cell(const ora_params *P, const double *x, const double *lo, const double *cwd,
+                      const int64_t *nc, int64_t *ci)
+{
+    for (int d = 0; d < P->dim; ++d) {
+        ci[d] = (int64_t)floor((wrap_coord(P, d, x[d]) - lo[d]) / cwd[d]);
+        if (ci[d] >= nc[d]) ci[d] = nc[d] - 1;
+        if (ci[d] < 0) ci[d] = 0;
+    }
+}
+
+/* linear index of the neighbour cell ci + o (wrapped on periodic axes);
+ * 0 when it lies outside a non-periodic axis */
+static int grid_neighbour(const ora_params *P, const int64_t *ci, int64_t ox, int64_t oy, int64_t oz,
+                          const int64_t *nc, int64_t *c_out)
+{
+    int64_t c3[3] = {ci[0] + ox, ci[1] + oy, ci[2] + oz};
+    for (int d = 0; d < P->dim; ++d) {
+        if (c3[d] >= 0 && c3[d] < nc[d]) continue;
+        if (!is_periodic(P, d)) return 0;
+        c3[d] = (c3[d] + nc[d]) % nc[d];
+    }
+    int64_t c = 0;
+    for (int d = P->dim - 1; d >= 0; --d) c = c * nc[d] + c3[d];
+    *c_out = c;
+    return 1;
+}
+
 /* A neighbour of i is any j != i with 0 < r_ij < 2h.  Returns the total
  * number of pairs; fills counts[n] and, when idx != NULL and the total fits
  * in cap, the CSR column array (ascending j within each row).  Returns -1 on
@@ -193,10 +262,14 @@ int64_t ora_neighbors(const ora_params *P, int64_t n, const double *pos,
     int64_t *cell_of = NULL, *cell_start = NULL, *order = NULL;
     int64_t nc[3] = {1, 1, 1};
     double lo[3] = {0, 0, 0};
-    double cw = 2.0 * P->h;
+    double cwd[3] = {2.0 * P->h, 2.0 * P->h, 2.0 * P->h};
+    int brute = P->nbr_mode == 0 || n == 0;
+    for (int d = 0; d < dim; ++d)      /* a periodic axis shorter than 3 cells: brute force */
+        if (is_periodic(P, d) && floor((P->box_hi[d] - P->box_lo[d]) / (2.0 * P->h)) < 3.0) brute = 1;
 
-    if (P->nbr_mode == 1 && n > 0) {
-        /* plain uniform grid of cell width 2h over the bounding box */
+    if (!brute) {
+        /* plain uniform grid of cell width 2h over the bounding box; a
+         * periodic axis is cut into floor(L / 2h) cells that wrap around */
         double hi[3] = {0, 0, 0};
         for (int d = 0; d < dim; ++d) { lo[d] = pos[d]; hi[d] = pos[d]; }
         for (int64_t i = 0; i < n; ++i)
@@ -206,7 +279,14 @@ int64_t ora_neighbors(const ora_params *P, int64_t n, const double *pos,
             }
         int64_t total = 1;
         for (int d = 0; d < dim; ++d) {
-            nc[d] = (int64_t)floor((hi[d] - lo[d]) / cw) + 1;
+            if (is_periodic(P, d)) {
+                double L = P->box_hi[d] - P->box_lo[d];
+                lo[d] = P->box_lo[d];
+                nc[d] = (int64_t)floor(L / (2.0 * P->h));
+                cwd[d] = L / (double)nc[d];
+            } else {
+                nc[d] = (int64_t)floor((hi[d] - lo[d]) / cwd[d]) + 1;
+            }
             total *= nc[d];
         }
         cell_of = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
@@ -215,8 +295,9 @@ int64_t ora_neighbors(const ora_params *P, int64_t n, const double *pos,
         for (int64_t i = 0; i < n; ++i) {
             int64_t c = 0;
             for (int d = dim - 1; d >= 0; --d) {
-                int64_t k = (int64_t)floor((pos[3 * i + d] - lo[d]) / cw);
+                int64_t k = (int64_t)floor((wrap_coord(P, d, pos[3 * i + d]) - lo[d]) / cwd[d]);
                 if (k >= nc[d]) k = nc[d] - 1;
+                if (k < 0) k = 0;
                 c = c * nc[d] + k;
             }
             cell_of[i] = c;
@@ -236,41 +317,25 @@ int64_t ora_neighbors(const ora_params *P, int64_t n, const double *pos,
     for (int64_t i = 0; i < n; ++i) {
         int32_t cnt = 0;
         const double *xi = pos + 3 * i;
-        if (P->nbr_mode == 0) {
+        if (brute) {
             for (int64_t j = 0; j < n; ++j) {
                 if (j == i) continue;
-                double r2 = 0.0;
-                for (int d = 0; d < dim; ++d) {
-                    double t = xi[d] - pos[3 * j + d];
-                    r2 += t * t;
-                }
+                double r2 = pair_dist2(P, xi, pos + 3 * j);
                 if (r2 == 0.0) coincident = 1;
                 else if (r2 < R2) cnt++;
             }
         } else {
             int64_t ci[3] = {0, 0, 0};
-            for (int d = 0; d < dim; ++d) {
-                ci[d] = (int64_t)floor((xi[d] - lo[d]) / cw);
-                if (ci[d] >= nc[d]) ci[d] = nc[d] - 1;
-            }
+            grid_cell(P, xi, lo, cwd, nc, ci);
             for (int64_t oz = (dim == 3 ? -1 : 0); oz <= (dim == 3 ? 1 : 0); ++oz)
                 for (int64_t oy = -1; oy <= 1; ++oy)
                     for (int64_t ox = -1; ox <= 1; ++ox) {
-                        int64_t c3[3] = {ci[0] + ox, ci[1] + oy, ci[2] + oz};
-                        int ok = 1;
-                        for (int d = 0; d < dim; ++d)
-                            if (c3[d] < 0 || c3[d] >= nc[d]) ok = 0;
-                        if (!ok) continue;
                         int64_t c = 0;
-                        for (int d = dim - 1; d >= 0; --d) c = c * nc[d] + c3[d];
+                        if (!grid_neighbour(P, ci, ox, oy, oz, nc, &c)) continue;
                         for (int64_t s = cell_start[c]; s < cell_start[c + 1]; ++s) {
                             int64_t j = order[s];
                             if (j == i) continue;
-                            double r2 = 0.0;
-                            for (int d = 0; d < dim; ++d) {
-                                double t = xi[d] - pos[3 * j + d];
-                                r2 += t * t;
-                            }
+                            double r2 = pair_dist2(P, xi, pos + 3 * j);
                             if (r2 == 0.0) coincident = 1;
                             else if (r2 < R2) cnt++;
                         }
@@ -288,40 +353,24 @@ int64_t ora_neighbors(const ora_params *P, int64_t n, const double *pos,
         for (int64_t i = 0; i < n; ++i) {
             int64_t w = row[i];
             const double *xi = pos + 3 * i;
-            if (P->nbr_mode == 0) {
+            if (brute) {
                 for (int64_t j = 0; j < n; ++j) {
                     if (j == i) continue;
-                    double r2 = 0.0;
-                    for (int d = 0; d < dim; ++d) {
-                        double t = xi[d] - pos[3 * j + d];
-                        r2 += t * t;
-                    }
+                    double r2 = pair_dist2(P, xi, pos + 3 * j);
                     if (r2 > 0.0 && r2 < R2) idx[w++] = (int32_t)j;
                 }
             } else {
                 int64_t ci[3] = {0, 0, 0};
-                for (int d = 0; d < dim; ++d) {
-                    ci[d] = (int64_t)floor((xi[d] - lo[d]) / cw);
-                    if (ci[d] >= nc[d]) ci[d] = nc[d] - 1;
-                }
+                grid_cell(P, xi, lo, cwd, nc, ci);
                 for (int64_t oz = (dim == 3 ? -1 : 0); oz <= (dim == 3 ? 1 : 0); ++oz)
                     for (int64_t oy = -1; oy <= 1; ++oy)
                         for (int64_t ox = -1; ox <= 1; ++ox) {
-                            int64_t c3[3] = {ci[0] + ox, ci[1] + oy, ci[2] + oz};
-                            int ok = 1;
-                            for (int d = 0; d < dim; ++d)
-                                if (c3[d] < 0 || c3[d] >= nc[d]) ok = 0;
-                            if (!ok) continue;
                             int64_t c = 0;
-                            for (int d = dim - 1; d >= 0; --d) c = c * nc[d] + c3[d];
+                            if (!grid_neighbour(P, ci, ox, oy, oz, nc, &c)) continue;
                             for (int64_t s = cell_start[c]; s < cell_start[c + 1]; ++s) {
                                 int64_t j = order[s];
                                 if (j == i) continue;
-                                double r2 = 0.0;
-                                for (int d = 0; d < dim; ++d) {
-                                    double t = xi[d] - pos[3 * j + d];
-                                    r2 += t * t;
-                                }
+                                double r2 = pair_dist2(P, xi, pos + 3 * j);
                                 if (r2 > 0.0 && r2 < R2) idx[w++] = (int32_t)j;
                             }
                         }
@@ -340,15 +389,28 @@ int64_t ora_neighbors(const ora_params *P, int64_t n, const double *pos,
 /* cell keys (the library's Morton-ordered cell list, restated for checking) */
 /* ------------------------------------------------------------------------ */
 /* Cell width cs = 2h (1 + 2^-16); grid origin = bounding-box minimum minus
- * pad cells; cells per axis = floor((max - origin)/cs) + 1 + pad.  Cell
+ * pad cells; cells per axis = floor((max - origin)/cs) + 1 + pad.  With a
+ * periodic axis of length L: cs = L / floor(L / (2h (1 + 2^-16))) for every
+ * axis, and that axis starts at box_lo with exactly L / cs cells.  Cell
  * coordinates interleave into a Morton code with axis 0 in the lowest bit.
  * The canonical particle order sorts by (Morton code, insertion index). */
 void ora_grid(const ora_params *P, int64_t n, const double *pos, int32_t pad,
               double *origin3, double *cs_out, int32_t *ncell3)
 {
     double cs = 2.0 * P->h * (1.0 + 1.0 / 65536.0);
+    for (int d = 0; d < P->dim; ++d)   /* a periodic axis sets the width: L / floor(L / cs0) */
+        if (is_periodic(P, d)) {
+            double L = P->box_hi[d] - P->box_lo[d];
+            cs = L / floor(L / (2.0 * P->h * (1.0 + 1.0 / 65536.0)));
+        }
     for (int d = 0; d < 3; ++d) { origin3[d] = 0.0; ncell3[d] = 1; }
     for (int d = 0; d < P->dim; ++d) {
+        if (is_periodic(P, d)) {
+            double L = P->box_hi[d] - P->box_lo[d];
+            origin3[d] = P->box_lo[d];
+            ncell3[d] = (int32_t)floor(L / (2.0 * P->h * (1.0 + 1.0 / 65536.0)));
+            continue;
+        }
         double lo = pos[d], hi = pos[d];
         for (int64_t i = 1; i < n; ++i) {
             if (pos[3 * i + d] < lo) lo = pos[3 * i + d];
@@ -382,6 +444,16 @@ int64_t ora_cell_keys(const ora_params *P, int64_t n, const double *pos,
         int64_t c[3] = {0, 0, 0};
         int bad = 0;
         for (int d = 0; d < P->dim; ++d) {
+            if (is_periodic(P, d)) {
+                /* position brought into the period, then its cell (the last
+                 * cell also takes a position that rounds onto box_hi) */
+                double L = P->box_hi[d] - P->box_lo[d];
+                double rel = pos[3 * i + d] - origin3[d];
+                rel = rel - L * floor(rel / L);
+                c[d] = (int64_t)floor(rel / cs);
+                if (c[d] >= ncell3[d]) c[d] = ncell3[d] - 1;
+                continue;
+            }
             c[d] = (int64_t)floor((pos[3 * i + d] - origin3[d]) / cs);
             if (c[d] < 0 || c[d] >= ncell3[d]) bad = 1;
         }
@@ -522,6 +594,7 @@ static int pairs_build(const ora_params *P, int64_t n, const double *snap, pairs
             int64_t j = pp->col[k];
             double rv[3] = {0, 0, 0};
             for (int d = 0; d < P->dim; ++d) rv[d] = snap[3 * i + d] - snap[3 * j + d];
+            min_image(P, rv);
             double r = norm3(rv, P->dim);
             pp->r[k] = r;
             for (int d = 0; d < 3; ++d) pp->e[3 * k + d] = rv[d] / r;
@@ -982,7 +1055,7 @@ int ora_run(const ora_params *P, int64_t n, double *pos, double *vel, double *rh
             correction_matrix(P, &S, &pp, Bm);
             tvf_shift(P, &S, &pp, Bm, dr);
             for (int64_t i = 0; i < n; ++i)
-                for (int d = 0; d < dim; ++d) pos[3 * i + d] += dr[3 * i + d];
+                for (int d = 0; d < dim; ++d) pos[3 * i + d] = wrap_coord(P, d, pos[3 * i + d] + dr[3 * i + d]);
         }
 
         double t_in = 0.0;
@@ -1009,7 +1082,7 @@ int ora_run(const ora_params *P, int64_t n, double *pos, double *vel, double *rh
             for (int64_t i = 0; i < n; ++i) {
                 if (!is_fluid(kind[i])) continue;
                 rho[i] += dt * drho[i];
-                for (int d = 0; d < dim; ++d) pos[3 * i + d] += dt * vel[3 * i + d];
+                for (int d = 0; d < dim; ++d) pos[3 * i + d] = wrap_coord(P, d, pos[3 * i + d] + dt * vel[3 * i + d]);
             }
             t_in += dt;
             ++sub;

@@ -64,6 +64,7 @@ class Case:
     phases: List[Phase] = dataclasses.field(default_factory=list)
     t_end: Optional[float] = None  # physical end time of the workload, if any
     meta: dict = dataclasses.field(default_factory=dict)
+    periodic: int = 0             # bit a set: axis a is periodic on [lo[a], hi[a])
 
     @property
     def n(self) -> int:
@@ -226,6 +227,64 @@ def droplet_case(name: str, dim: int, lo, hi, dx: float, center, R: float, *,
     return Case(name=name, dim=dim, lo=lo, hi=hi, dx=dx, gamma=sigma, c0=c0,
                 h_factor=h_factor, xi=xi, phases=phases, t_end=t_end,
                 meta=dict(center=list(center)[:dim], R=R, shape=shape, amp=amp))
+
+
+def shear_drop_2d(Ca: float = 0.1, R: float = 1.0, L: float = 8.0, R_over_dp: int = 12,
+                  rho: float = 1.0, eta: float = 1.0, U: float = 0.5,
+                  t_end: float = 30.0) -> Case:
+    """Drop in a Couette flow (Section 5.2): an L x L box periodic in x,
+    no-slip walls at y = 0 and y = L moving with -U and +U, a drop of radius
+    R at the centre with the same density and viscosity as the outer fluid.
+    Shear rate G = 2U/L; the surface tension follows from the capillary number
+    Ca = G eta R / gamma.  The fluid starts on the Couette profile.  The
+    sound speed is ten times the larger of U and the capillary velocity
+    sqrt(gamma / (rho R))."""
+    dx = R / R_over_dp
+    G = 2.0 * U / L
+    gamma = G * eta * R / Ca
+    c0 = 10.0 * max(U, math.sqrt(gamma / (rho * R)))
+    lo, hi = [0.0, 0.0], [L, L]
+    p = lattice(lo, hi, dx)
+    inside = shape_mask(p, [0.5 * L, 0.5 * L], R)
+    vel = np.zeros_like(p)
+    vel[:, 0] = -U + G * p[:, 1]
+    shell = wall_shell(lo, hi, dx, sides=[1])
+    bottom = shell[shell[:, 1] < 0.0]
+    top = shell[shell[:, 1] > L]
+    phases = [Phase("fluid", p[inside], rho0=rho, eta=eta, vel=vel[inside]),
+              Phase("fluid", p[~inside], rho0=rho, eta=eta, vel=vel[~inside]),
+              Phase("wall", bottom, wall_vel=(-U, 0.0, 0.0)),
+              Phase("wall", top, wall_vel=(U, 0.0, 0.0))]
+    return Case(name=f"shear_drop_2d Ca={Ca:g}", dim=2, lo=lo, hi=hi, dx=dx, gamma=gamma, c0=c0,
+                phases=phases, t_end=t_end, periodic=1,
+                meta=dict(center=[0.5 * L, 0.5 * L], R=R, Ca=Ca, G=G, Re=rho * G * R * R / eta, U=U))
+
+
+def periodic_blob(dim: int = 2, n_side: int = 24, seed: int = 0, jitter: float = 0.1,
+                  vel_amp: float = 0.05, R_frac: float = 0.3, periodic: Optional[int] = None,
+                  rho_ratio: float = 1.0) -> Case:
+    """A drop in a unit box that is periodic along every axis flagged in
+    `periodic` (default: all) and walled along the others; jittered lattice
+    and random velocities, for neighbour and parity checks across the wrap."""
+    rng = np.random.default_rng(seed)
+    per = (1 << dim) - 1 if periodic is None else periodic
+    dx = 1.0 / n_side
+    lo, hi = [0.0] * dim, [1.0] * dim
+    p = lattice(lo, hi, dx)
+    p = p + rng.uniform(-jitter, jitter, p.shape) * dx
+    for a in range(dim):
+        if (per >> a) & 1:
+            p[:, a] = np.mod(p[:, a], 1.0)
+    inside = shape_mask(p, [0.5] * dim, R_frac)
+    vel = rng.uniform(-vel_amp, vel_amp, p.shape)
+    phases = [Phase("fluid", p[inside], rho0=rho_ratio, eta=0.05, vel=vel[inside]),
+              Phase("fluid", p[~inside], rho0=1.0, eta=0.05, vel=vel[~inside])]
+    walled = [a for a in range(dim) if not (per >> a) & 1]
+    if walled:
+        phases.append(Phase("wall", wall_shell(lo, hi, dx, sides=walled)))
+    return Case(name=f"periodic_blob_{dim}d", dim=dim, lo=lo, hi=hi, dx=dx, gamma=1.0, c0=20.0,
+                phases=phases, periodic=per, cfl_ac=0.4 if dim == 3 else 0.6,
+                meta=dict(center=[0.5] * dim, R=R_frac))
 
 
 # ----------------------------------------------------------------------------
