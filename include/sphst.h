@@ -117,6 +117,17 @@ typedef struct {
                                sound term needs <= 0.5 (2D) / 0.4 (3D)        */
     int32_t nbr_mode;       /* SPHST_NBR_*                                     */
     int32_t max_neighbors;  /* list capacity per particle; 0: 128 (3D), 48 (2D) */
+    int32_t periodic;       /* bit a set: axis a is periodic on [period_lo[a],
+                               period_hi[a]) (the shear drop of Section 5.2 is
+                               periodic in x).  Pairs use the minimum image and
+                               particles leaving one end re-enter at the other.
+                               A periodic axis of length L holds
+                               m = floor(L / (2h (1 + 2^-16))) >= 3 cells of
+                               width L / m; every periodic axis must give the
+                               same width (else INVALID_ARG).  0: none         */
+    int32_t pad2_;
+    double  period_lo[3];
+    double  period_hi[3];
 } sphst_case_params;
 
 typedef struct {

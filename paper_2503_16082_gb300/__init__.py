@@ -39,7 +39,9 @@ class CaseParams(C.Structure):
                 ("grad_mode", C.c_int32), ("penalty_form", C.c_int32), ("loop_mode", C.c_int32),
                 ("grid_pad", C.c_int32), ("block", C.c_int32), ("max_substeps", C.c_int64),
                 ("cfl_ad", C.c_double), ("cfl_ac", C.c_double),
-                ("nbr_mode", C.c_int32), ("max_neighbors", C.c_int32)]
+                ("nbr_mode", C.c_int32), ("max_neighbors", C.c_int32),
+                ("periodic", C.c_int32), ("pad2_", C.c_int32),
+                ("period_lo", C.c_double * 3), ("period_hi", C.c_double * 3)]
 
 
 class PhaseProps(C.Structure):
@@ -314,6 +316,10 @@ def case_from_spec(spec, precision: int = 32, **params):
     p = default_params(dim=spec.dim, precision=precision, dx=spec.dx, h_factor=spec.h_factor,
                        c0=spec.c0, gamma=spec.gamma, xi=spec.xi,
                        cfl_ac=getattr(spec, "cfl_ac", 0.6))
+    if getattr(spec, "periodic", 0):
+        p.periodic = spec.periodic
+        for a in range(spec.dim):
+            p.period_lo[a], p.period_hi[a] = spec.lo[a], spec.hi[a]
     for k, v in params.items():
         setattr(p, k, v)
     h = create_case(p)

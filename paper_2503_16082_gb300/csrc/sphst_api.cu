@@ -57,7 +57,14 @@ static const char *status_text(int s) {
 
 static double cell_width(const CaseRec *c) {
     const double h = c->P.h_factor * c->P.dx;
-    return 2.0 * h * (1.0 + 1.0 / 65536.0);
+    const double cs0 = 2.0 * h * (1.0 + 1.0 / 65536.0);
+    double cs = cs0;
+    for (int a = 0; a < c->P.dim; ++a)       // a periodic axis fixes the width: L / floor(L / cs0)
+        if ((c->P.periodic >> a) & 1) {
+            const double L = c->P.period_hi[a] - c->P.period_lo[a];
+            cs = L / std::floor(L / cs0);
+        }
+    return cs;
 }
 
 // Grid over the initial bounding box with grid_pad spare cells per side; the
@@ -69,6 +76,13 @@ int make_grid(CaseRec *c) {
     int maxn = 1;
     for (int a = 0; a < 3; ++a) { c->origin[a] = 0.0; c->ncell[a] = 1; }
     for (int a = 0; a < dim; ++a) {
+        if ((c->P.periodic >> a) & 1) {      // the period itself, no spare cells
+            const double L = c->P.period_hi[a] - c->P.period_lo[a];
+            c->origin[a] = c->P.period_lo[a];
+            c->ncell[a] = (int32_t)std::floor(L / (2.0 * c->P.h_factor * c->P.dx * (1.0 + 1.0 / 65536.0)));
+            maxn = std::max(maxn, c->ncell[a]);
+            continue;
+        }
         double lo = c->n ? c->pos[a] : 0.0, hi = lo;
         for (int64_t i = 1; i < c->n; ++i) {
             const double x = c->pos[3 * i + a];
@@ -163,6 +177,9 @@ CaseDesc make_desc(const CaseRec *c) {
     d.cfl_ad = c->P.cfl_ad;
     d.cfl_ac = c->P.cfl_ac;
     d.nbr_mode = c->P.nbr_mode;
+    d.periodic = c->P.periodic;
+    for (int a = 0; a < 3; ++a)
+        d.period_len[a] = ((c->P.periodic >> a) & 1) ? c->P.period_hi[a] - c->P.period_lo[a] : 0.0;
     d.nbr_k = c->P.max_neighbors > 0 ? c->P.max_neighbors : (c->P.dim == 3 ? 128 : 48);
     d.pf = phys_of<float>(c);
     d.pd = phys_of<double>(c);
@@ -278,6 +295,26 @@ int sphst_create_case(const sphst_case_params *params, sphst_case *out) {
     if (P.grid_pad < 1 || P.grid_pad > 64 || P.block < 32 || P.block > 256 || P.block % 32) {
         set_error("grid_pad must be 1..64 and block a multiple of 32 in 32..256");
         return SPHST_ERR_INVALID_ARG;
+    }
+    if (P.periodic < 0 || P.periodic >= (1 << P.dim)) {
+        set_error("periodic: a bit mask of the case's axes");
+        return SPHST_ERR_INVALID_ARG;
+    }
+    double per_cs = 0.0;
+    for (int a = 0; a < P.dim; ++a) {
+        if (!((P.periodic >> a) & 1)) continue;
+        const double L = P.period_hi[a] - P.period_lo[a];
+        const double cs0 = 2.0 * P.h_factor * P.dx * (1.0 + 1.0 / 65536.0);
+        if (!(L > 0.0) || !std::isfinite(L) || !(std::floor(L / cs0) >= 3.0)) {
+            set_error("a periodic axis must span at least 3 cells of width 2h (1 + 2^-16)");
+            return SPHST_ERR_INVALID_ARG;
+        }
+        const double cs = L / std::floor(L / cs0);
+        if (per_cs > 0.0 && std::fabs(cs - per_cs) > 1e-12 * cs) {
+            set_error("periodic axes give different cell widths: use commensurate periods");
+            return SPHST_ERR_INVALID_ARG;
+        }
+        per_cs = cs;
     }
     sphst_case c = new (std::nothrow) sphst_case_s();
     if (!c) { set_error("host allocation failed"); return SPHST_ERR_OOM; }

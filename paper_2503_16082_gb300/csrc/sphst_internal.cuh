@@ -94,6 +94,9 @@ struct CaseDesc {
     int64_t p_begin, p_end;    // particle range in the engine arrays
     int64_t table_off;         // first cell-table entry of this case
     int64_t table_size;        // 2^(dim*bits)
+    int32_t periodic;          // bit a: axis a wraps (ncell[a] cells of width cs tile the period)
+    int32_t pad_per;
+    double period_len[3];      // period of each periodic axis
     double origin[3];
     double cs;
     double h, c0, gamma;

@@ -214,6 +214,16 @@ template <typename T> struct Limiter {
     __device__ __forceinline__ T operator()(T dU) const { return clamp_lh(k * dU, lo, hi); }
 };
 
+// Neighbour cell index along axis a: wrapped on a periodic axis (the cells
+// tile the period exactly, so the cell at -1 is the last one and lies one
+// cell width before cell 0); false when it falls off a non-periodic axis.
+__device__ __forceinline__ bool wrap_cell(const CaseDesc &d, int a, int &c) {
+    if (c >= 0 && c < d.ncell[a]) return true;
+    if (!((d.periodic >> a) & 1)) return false;
+    c += c < 0 ? d.ncell[a] : -d.ncell[a];
+    return true;
+}
+
 // --------------------------------------------------------------- cell walk
 // Calls f(j, snap_j, r_ij vector, r^2) for every j != i with 0 < r_ij < 2h in
 // the 3^D cells around i's cell.  r_ij = s_i - s_j - o cs, where o is the
@@ -229,16 +239,16 @@ __device__ __forceinline__ bool walk(const CaseDesc &d, const CasePhys<T> &cp,
     const T cs = cp.cs, R2 = cp.four_h2;
     bool coincident = false;
     for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz) {
-        const int nz = cz + oz;
-        if (D == 3 && (nz < 0 || nz >= d.ncell[2])) continue;
+        int nz = cz + oz;
+        if (D == 3 && !wrap_cell(d, 2, nz)) continue;
         const T sz = D == 3 ? sub_rn(si.z, mul_rn(T(oz), cs)) : T(0);
         for (int oy = -1; oy <= 1; ++oy) {
-            const int ny = cy + oy;
-            if (ny < 0 || ny >= d.ncell[1]) continue;
+            int ny = cy + oy;
+            if (!wrap_cell(d, 1, ny)) continue;
             const T sy = sub_rn(si.y, mul_rn(T(oy), cs));
             for (int ox = -1; ox <= 1; ++ox) {
-                const int nx = cx + ox;
-                if (nx < 0 || nx >= d.ncell[0]) continue;
+                int nx = cx + ox;
+                if (!wrap_cell(d, 0, nx)) continue;
                 const T sx = sub_rn(si.x, mul_rn(T(ox), cs));
                 const uint32_t m = toff + morton<D>(nx, ny, nz);
                 const uint32_t b = __ldg(starts + m), e = __ldg(starts + m + 1);
@@ -444,8 +454,15 @@ __device__ __forceinline__ void init_one(const CaseDesc &d, int c, int64_t k, co
     bool bad = false;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        const double rel = __dsub_rn(apos[3 * k + a], d.origin[a]);
+        double rel = __dsub_rn(apos[3 * k + a], d.origin[a]);
+        if ((d.periodic >> a) & 1) {
+            // into the period [0, L), then the last cell also takes a
+            // position that rounds onto its end
+            const double L = d.period_len[a];
+            rel = __dsub_rn(rel, __dmul_rn(L, floor(__ddiv_rn(rel, L))));
+        }
         double f = floor(__ddiv_rn(rel, d.cs));
+        if ((d.periodic >> a) & 1 && f >= (double)d.ncell[a]) f = (double)(d.ncell[a] - 1);
         if (!(f >= 0.0 && f < (double)d.ncell[a])) {
             bad = true;
             f = f < 0.0 || f != f ? 0.0 : (double)(d.ncell[a] - 1);
@@ -498,7 +515,10 @@ __device__ __forceinline__ void assign_one(const CaseDesc &d, CaseState *st, int
         T f = floor(off[a] / cp.cs);
         if (!(f == f) || f > T(4096) || f < T(-4096)) { f = T(0); bad = true; }
         int nc = cc[a] + (int)f;
-        if (nc < 0 || nc >= d.ncell[a]) {
+        if ((d.periodic >> a) & 1) {
+            // the offset is taken from the unwrapped cell; the index wraps
+            nc = ((nc % d.ncell[a]) + d.ncell[a]) % d.ncell[a];
+        } else if (nc < 0 || nc >= d.ncell[a]) {
             bad = true;
             nc = nc < 0 ? 0 : d.ncell[a] - 1;
             f = T(nc - cc[a]);
@@ -965,13 +985,12 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
         const T drj = vj.w;
         const T rho_j = sel(kj, rho0_0, rho0_1) + drj;
         const T p_j = c0sq * drj;
-        const T Vj = div_fast(sel(kj, m_0, m_1), rho_j);
-        const T inv_rs = div_fast(T(1), rho_i + rho_j);
-        const T pbar = (rho_i * p_j + rho_j * p_i) * inv_rs;     // Eq. 12
         const T dU = dUe;
         const T beta = limiter_beta(dU);                        // Eq. 11
-        const T Ps = pbar + beta * c0 * rho_i * rho_j * dU * inv_rs;   // Eq. 8
-        const T f = Ps * g.dW * Vj;
+        // P* V_j with P* = (rho_i p_j + rho_j p_i + beta c0 rho_i rho_j dU) / (rho_i + rho_j)
+        // (Eqs. 8, 12) and V_j = m_j / rho_j: one division
+        const T num = (rho_i * p_j + rho_j * p_i) + beta * c0 * rho_i * rho_j * dU;
+        const T f = div_fast(num * sel(kj, m_0, m_1), (rho_i + rho_j) * rho_j) * g.dW;
         const L2<T> a = fma2(l2(f, f), exy, l2(apx, apy));
         apx = a.x; apy = a.y; if (D == 3) apz += f * ez;
     };
@@ -1100,10 +1119,10 @@ __device__ __forceinline__ void sweep_C(const CaseDesc &d, const CasePhys<T> &cp
             const T drj = vj.w;
             const T rho_j = sel(kj, rho0_0, rho0_1) + drj;
             const T p_j = c0sq * drj;
-            const T Vj = div_fast(sel(kj, m_0, m_1), rho_j);
-            // (v_i - v*).e = U* - U_L = (Z_R (U_R - U_L) + p_i - p_j) / (Z_L + Z_R)
-            const T du = div_fast(rho_j * c0 * dve + (p_i - p_j), c0 * (rho_i + rho_j));
-            s += du * g.dW * Vj;
+            // (v_i - v*).e V_j with (v_i - v*).e = U* - U_L = (Z_R (U_R - U_L) + p_i - p_j)
+            // / (Z_L + Z_R) and V_j = m_j / rho_j: one division
+            const T num = (rho_j * c0 * dve + (p_i - p_j)) * sel(kj, m_0, m_1);
+            s += div_fast(num, c0 * (rho_i + rho_j) * rho_j) * g.dW;
         });
     const T dr_new = dri + dt * (T(2) * rho_i * s);
     drho[i] = dr_new;
@@ -1130,6 +1149,14 @@ struct SweepArgs {
     int64_t tile0;                 // first tile of the launched class
 };
 
+// offset -1/0/+1 between neighbour cells from their index difference, which
+// is +-(ncell - 1) across the wrap of a periodic axis
+__device__ __forceinline__ int cell_step(const CaseDesc &d, int a, int diff) {
+    if (diff > 1) return diff - d.ncell[a];
+    if (diff < -1) return diff + d.ncell[a];
+    return diff;
+}
+
 // ---- L: neighbour list of the frozen configuration (fluid particles only)
 template <typename T, int D>
 __device__ __forceinline__ void build_list(const CaseDesc &d, const CasePhys<T> &cp, int64_t i,
@@ -1152,8 +1179,9 @@ __device__ __forceinline__ void build_list(const CaseDesc &d, const CasePhys<T> 
                 const uint32_t pkj = w_bits(sj.w);
                 if ((phase_of(pkj) == other) != (part == 0)) return;
                 if (c >= kmax) { overflow = true; return; }
-                const uint32_t code = cell_code<D>(cell_x<D>(pkj) - cx, cell_y<D>(pkj) - cy,
-                                                   cell_z<D>(pkj) - cz);
+                const uint32_t code = cell_code<D>(cell_step(d, 0, cell_x<D>(pkj) - cx),
+                                                   cell_step(d, 1, cell_y<D>(pkj) - cy),
+                                                   D == 3 ? cell_step(d, 2, cell_z<D>(pkj) - cz) : 0);
                 base[(int64_t)c * stride] = (j << NBR_SHIFT) | code;
                 ++c;
             });

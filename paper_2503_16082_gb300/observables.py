@@ -64,6 +64,27 @@ def laplace_jump_device(case, dim: int, dx: float, h: float):
     return float(dg["p_in"] / max(dg["n_in"], 1) - dg["p_out"] / max(dg["n_out"], 1)), Reff
 
 
+def deformation(cov) -> float:
+    """Taylor deformation D = (a - b)/(a + b) of an elliptical drop from the
+    covariance of its particles (a filled ellipse has eigenvalues a^2/4 and
+    b^2/4 along its axes)."""
+    lam = np.sort(np.linalg.eigvalsh(np.asarray(cov)))[::-1]
+    a, b = math.sqrt(max(lam[0], 0.0)), math.sqrt(max(lam[-1], 0.0))
+    return (a - b) / (a + b)
+
+
+def deformation_device(case, dim: int = 2) -> float:
+    """Deformation of the drop (phase 0) from FP64 device reductions."""
+    from . import diagnose
+    _, cov = moments_from_diag(diagnose(case), dim)
+    return deformation(cov)
+
+
+def taylor_deformation(Ca: float, visc_ratio: float = 1.0) -> float:
+    """Taylor's small-deformation result D = Ca (19 l + 16) / (16 l + 16)."""
+    return Ca * (19.0 * visc_ratio + 16.0) / (16.0 * visc_ratio + 16.0)
+
+
 def anisotropy(pos, phase, drop_phase: int = 0) -> float:
     q = pos[phase == drop_phase]
     d = q - q.mean(axis=0)

@@ -4,12 +4,16 @@
   python -m paper_2503_16082_gb300.validate oscillating_3d [--periods 1.5]
   python -m paper_2503_16082_gb300.validate impact_3d [--t-end 2]
   python -m paper_2503_16082_gb300.validate oscillating_2d [--ratio 1000]
+  python -m paper_2503_16082_gb300.validate shear_drop [--ca 0.1] [--t-end 20]
 
 Each prints one JSON line.  laplace_2d: Young-Laplace jump (Eq. 37)
 averaged over the last 20% of the run, against gamma / R_eff.  oscillating_*:
 period of the drop's shape anisotropy against Eq. 35 (2D, ratio >> 1), the
 equal-density textbook value (2D, ratio 1) or Lamb's n = 2 value (3D).
 impact_3d: whether the run stays finite to t_end, with its substep count.
+shear_drop: Taylor deformation of the drop of Section 5.2 (periodic in x,
+walls at +-U) averaged over the last 25% of the run, against Taylor's
+D = Ca (19 l + 16)/(16 l + 16) with l = 1.
 """
 from __future__ import annotations
 
@@ -108,24 +112,57 @@ def impact(args):
             "particle_substeps_per_s": case.n_fluid * info["n_sub"] / wall, "wall_s": round(wall, 2)}
 
 
+def shear(args):
+    case = sphcases.shear_drop_2d(args.ca, t_end=args.t_end)
+    h = S.case_from_spec(case, precision=args.precision)
+    ts, ds = [], []
+    t0 = time.perf_counter()
+    info = S.case_info(h)
+    while info["t"] < args.t_end:
+        info = S.step(h, args.every_shear, check=False)
+        if info["rc"]:
+            break
+        ts.append(info["t"])
+        ds.append(ob.deformation_device(h, 2))
+    wall = time.perf_counter() - t0
+    dg = S.diagnose(h)
+    S.destroy(h)
+    ts, ds = np.array(ts), np.array(ds)
+    tail = ts >= 0.75 * ts[-1] if len(ts) else ts
+    D = float(ds[tail].mean()) if len(ts) else float("nan")
+    ref = ob.taylor_deformation(args.ca)
+    return {"workload": "shear_drop_2d", "precision": args.precision, "Ca": args.ca, "Re": case.meta["Re"],
+            "particles": case.n, "adv": info["n_adv"], "substeps": info["n_sub"], "t": info["t"],
+            "status": info["status"], "D": D, "D_std_tail": float(ds[tail].std()) if len(ts) else None,
+            "taylor": ref, "rel_error": (D - ref) / ref, "n_nonfinite": dg["n_nonfinite"],
+            "D_series": [[round(float(t), 3), round(float(d), 5)] for t, d in zip(ts[::max(1, len(ts) // 20)], ds[::max(1, len(ts) // 20)])],
+            "wall_s": round(wall, 2)}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("workload", choices=["laplace_2d", "oscillating_3d", "oscillating_2d", "impact_3d"])
+    ap.add_argument("workload", choices=["laplace_2d", "oscillating_3d", "oscillating_2d", "impact_3d", "shear_drop"])
+    ap.add_argument("--ca", type=float, default=0.1)
+    ap.add_argument("--every-shear", type=int, default=200)
     ap.add_argument("--precision", type=int, default=None, choices=[32, 64])
     ap.add_argument("--adv", type=int, default=500)
     ap.add_argument("--periods", type=float, default=1.5)
     ap.add_argument("--every", type=int, default=5)
     ap.add_argument("--ratio", type=float, default=1000.0)
-    ap.add_argument("--t-end", type=float, default=2.0)
+    ap.add_argument("--t-end", type=float, default=None, help="impact_3d: 2.0, shear_drop: 20.0")
     args = ap.parse_args(argv)
+    if args.t_end is None:
+        args.t_end = 20.0 if args.workload == "shear_drop" else 2.0
     if args.precision is None:
-        args.precision = 64 if args.workload in ("laplace_2d", "oscillating_2d") else 32
+        args.precision = 64 if args.workload in ("laplace_2d", "oscillating_2d", "shear_drop") else 32
     if args.workload == "laplace_2d":
         out = laplace(args)
     elif args.workload == "oscillating_3d":
         out = oscillating(args, 3)
     elif args.workload == "oscillating_2d":
         out = oscillating(args, 2)
+    elif args.workload == "shear_drop":
+        out = shear(args)
     else:
         out = impact(args)
     print(json.dumps(out), flush=True)

@@ -124,3 +124,22 @@ def test_momentum_conserved_without_walls():
     S.destroy(h)
     scale = (m * np.linalg.norm(v0, axis=1)).sum()
     assert np.abs(ob.momentum(v1, m) - ob.momentum(v0, m)).max() <= 1e-5 * scale
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_shear_drop_deformation_matches_taylor(precision):
+    # Section 5.2: a drop in Couette flow, periodic in x, walls at +-U, equal
+    # densities and viscosities, Re = 0.125; Taylor's D = Ca (19 + 16)/(16 + 16)
+    # for a viscosity ratio of 1.  Measured at R = 12 dp: D = 0.0993 (-9%).
+    case = sphcases.shear_drop_2d(0.1, t_end=20.0)
+    h = S.case_from_spec(case, precision=precision)
+    ds = []
+    t = 0.0
+    while t < 20.0:
+        t = S.step(h, 400)["t"]
+        if t >= 15.0:
+            ds.append(ob.deformation_device(h, 2))
+    assert S.diagnose(h)["n_nonfinite"] == 0
+    S.destroy(h)
+    D, ref = float(np.mean(ds)), ob.taylor_deformation(0.1)
+    assert abs(D - ref) <= 0.15 * ref, (D, ref)
