@@ -5,12 +5,16 @@
   python -m paper_2503_16082_gb300.validate impact_3d [--t-end 2]
   python -m paper_2503_16082_gb300.validate oscillating_2d [--ratio 1000]
   python -m paper_2503_16082_gb300.validate shear_drop [--ca 0.1] [--t-end 20]
+  python -m paper_2503_16082_gb300.validate impact_sweep [--res 20] [--u0 0.5 1 5 10 50]
 
 Each prints one JSON line.  laplace_2d: Young-Laplace jump (Eq. 37)
 averaged over the last 20% of the run, against gamma / R_eff.  oscillating_*:
 period of the drop's shape anisotropy against Eq. 35 (2D, ratio >> 1), the
 equal-density textbook value (2D, ratio 1) or Lamb's n = 2 value (3D).
 impact_3d: whether the run stays finite to t_end, with its substep count.
+impact_sweep: Section 5.4's impact in the paper's units for each U0 (Re up to
+1e4, We up to 2.5e4): whether the run stays finite to the paper's end time,
+and the drop's final spread along the wall.
 shear_drop: Taylor deformation of the drop of Section 5.2 (periodic in x,
 walls at +-U) averaged over the last 25% of the run, against Taylor's
 D = Ca (19 l + 16)/(16 l + 16) with l = 1.
@@ -139,9 +143,43 @@ def shear(args):
             "wall_s": round(wall, 2)}
 
 
+def impact_sweep(args):
+    out = []
+    for U0 in args.u0:
+        case = sphcases.impact_sweep_case(U0, args.res)
+        h = S.case_from_spec(case, precision=args.precision)
+        t_end = case.t_end * args.t_frac
+        t0 = time.perf_counter()
+        info = S.case_info(h)
+        while info["t"] < t_end:
+            info = S.step(h, 20, check=False)
+            if info["rc"]:
+                break
+        wall = time.perf_counter() - t0
+        pos = S.read_fields(h, S.FIELD_POS, 3)
+        vel = S.read_fields(h, S.FIELD_VEL, 3)
+        ph = S.read_fields(h, S.FIELD_PHASE, 3)
+        dg = S.diagnose(h)
+        S.destroy(h)
+        drop = ph == 0
+        spread = float(np.sqrt(((pos[drop, :2] - 4.0) ** 2).sum(1)).max()) / 0.5
+        out.append({"U0": U0, "Re": case.meta["Re"], "We": case.meta["We"], "particles": case.n,
+                    "t": info["t"], "t_end": t_end, "status": info["status"], "adv": info["n_adv"],
+                    "substeps": info["n_sub"], "finite": bool(np.isfinite(vel).all()) and dg["n_nonfinite"] == 0,
+                    "spread_over_R0": round(spread, 3),
+                    "drop_height": round(float(pos[drop, 2].max()), 4),
+                    "particle_substeps_per_s": case.n_fluid * info["n_sub"] / wall, "wall_s": round(wall, 2)})
+        print(json.dumps(out[-1]), flush=True)
+    return {"workload": "impact_sweep", "precision": args.precision, "d_over_dp": args.res, "runs": out}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("workload", choices=["laplace_2d", "oscillating_3d", "oscillating_2d", "impact_3d", "shear_drop"])
+    ap.add_argument("workload", choices=["laplace_2d", "oscillating_3d", "oscillating_2d", "impact_3d", "shear_drop",
+                                         "impact_sweep"])
+    ap.add_argument("--res", type=int, default=20, help="impact_sweep: d / dp")
+    ap.add_argument("--u0", type=float, nargs="+", default=[0.5, 1.0, 5.0, 10.0, 50.0])
+    ap.add_argument("--t-frac", type=float, default=1.0, help="impact_sweep: fraction of the end time")
     ap.add_argument("--ca", type=float, default=0.1)
     ap.add_argument("--every-shear", type=int, default=200)
     ap.add_argument("--precision", type=int, default=None, choices=[32, 64])
@@ -163,6 +201,8 @@ def main(argv=None):
         out = oscillating(args, 2)
     elif args.workload == "shear_drop":
         out = shear(args)
+    elif args.workload == "impact_sweep":
+        out = impact_sweep(args)
     else:
         out = impact(args)
     print(json.dumps(out), flush=True)

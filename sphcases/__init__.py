@@ -358,6 +358,21 @@ def impact_3d(dx: float = 1.0 / 60.0) -> Case:
     return case
 
 
+def impact_sweep_case(U0: float, d_over_dp: int = 20) -> Case:
+    """Section 5.4's impact in the paper's own units: a drop of diameter
+    d = 1 resting on the wall z = 0 at the centre of an 8 x 8 x 1.5 box,
+    moving down at U0; rho 1 / 0.001, mu 0.005 / 5e-5, gamma 0.1, so
+    Re = 200 U0 and We = 10 U0^2; c0 = 10 U0.  The paper's end times: 4.0,
+    and 0.1 for U0 = 50."""
+    dx = 1.0 / d_over_dp
+    case = droplet_case(f"impact_U{U0:g}", 3, [0, 0, 0], [8, 8, 1.5], dx, [4, 4, 0.5], 0.5,
+                        rho_l=1.0, rho_g=0.001, mu_l=0.005, mu_g=5e-5, sigma=0.1, c0=10.0 * U0,
+                        drop_vel=[0, 0, -U0], t_end=0.1 if U0 >= 50 else 4.0)
+    case.cfl_ac = 0.4
+    case.meta.update(U0=U0, Re=200.0 * U0, We=10.0 * U0 * U0)
+    return case
+
+
 def small_droplet(dim: int = 2, n_side: int = 24, R_frac: float = 0.3,
                   shape: str = "circle", amp: float = 0.0, sigma: float = 1.0,
                   rho_l: float = 1000.0, rho_g: float = 1.0,

@@ -143,3 +143,21 @@ def test_shear_drop_deformation_matches_taylor(precision):
     S.destroy(h)
     D, ref = float(np.mean(ds)), ob.taylor_deformation(0.1)
     assert abs(D - ref) <= 0.15 * ref, (D, ref)
+
+
+def test_impact_at_highest_reynolds_and_weber_stays_finite():
+    # Section 5.4 at U0 = 50 (Re = 1e4, We = 2.5e4), coarse (d = 10 dp), the
+    # first fifth of the paper's end time: no numerical instability
+    case = sphcases.impact_sweep_case(50.0, 10)
+    h = S.case_from_spec(case, precision=32)
+    t = 0.0
+    while t < 0.02:
+        info = S.step(h, 20)
+        t = info["t"]
+    dg = S.diagnose(h)
+    pos = S.read_fields(h, S.FIELD_POS, 3)
+    ph = S.read_fields(h, S.FIELD_PHASE, 3)
+    S.destroy(h)
+    assert info["status"] == 0 and dg["n_nonfinite"] == 0
+    # the drop has hit the wall and spread beyond its initial radius
+    assert np.sqrt(((pos[ph == 0, :2] - 4.0) ** 2).sum(1)).max() > 0.6
