@@ -254,6 +254,11 @@ def run_ours(args, dist: Dist):
                                 else "nominal FP64 rate of a GB300"),
                 "flops_per_launch": flops, "pairs": pairs, "pairs_surface": pairs_surf,
                 "avg_launch_ms": round(b_avg * 1e3, 4)}
+    try:                                   # measured FMA roof beside the derived one
+        roofline["peak_measured_fma"] = round(S.fma_peak(args.precision)["tflops"], 2)
+        roofline["frac_of_measured_fma"] = round(achieved / roofline["peak_measured_fma"], 4)
+    except Exception as e:                 # noqa: BLE001 - report, keep the bench line
+        roofline["peak_measured_fma"] = f"unavailable: {e}"
     if not surf_in_b and prof["sweep_S"][1]:
         s_avg = prof["sweep_S"][0] / prof["sweep_S"][1] / 1e3
         roofline["sweep_S"] = {"avg_launch_ms": round(s_avg * 1e3, 4),

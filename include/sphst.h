@@ -317,6 +317,13 @@ typedef struct {
 int sphst_diagnose(sphst_case c, const double *center, double r_in, double r_out,
                    sphst_diagnostics *out);
 
+/* Measured fused multiply-add throughput of the current GPU in TFLOP/s
+ * (precision 32 or 64): independent FMA chains on every SM, the best of three
+ * timed launches after a warm-up; kernel_ms (optional) receives that launch's
+ * duration.  It is the arithmetic roof of the pair sweeps.  Errors:
+ * INVALID_ARG, CUDA. */
+int sphst_fma_peak(int32_t precision, double *tflops, double *kernel_ms);
+
 /* Device bytes one case of n particles needs (particle arrays, cell table,
  * scratch), for admission control.  Errors: INVALID_ARG. */
 int sphst_footprint_bytes(const sphst_case_params *params, int64_t n_particles,

@@ -105,6 +105,7 @@ EXPORTS = {
     "sphst_batch_destroy": (C.c_int, [C.c_void_p]),
     "sphst_footprint_bytes": (C.c_int, [C.POINTER(CaseParams), C.c_int64, C.POINTER(C.c_int64)]),
     "sphst_diagnose": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.POINTER(Diagnostics)]),
+    "sphst_fma_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
 }
 
 _lib = None
@@ -238,6 +239,13 @@ def diagnose(case, center=(0.0, 0.0, 0.0), r_in: float = 0.0, r_out: float = flo
     out = Diagnostics()
     _check(load().sphst_diagnose(case, c.ctypes.data, float(r_in), float(r_out), C.byref(out)), "diagnose")
     return out.as_dict()
+
+
+def fma_peak(precision: int = 32) -> dict:
+    """Measured FMA throughput of the GPU (sphst_fma_peak)."""
+    tf, ms = C.c_double(0.0), C.c_double(0.0)
+    _check(load().sphst_fma_peak(precision, C.byref(tf), C.byref(ms)), "fma_peak")
+    return {"tflops": tf.value, "kernel_ms": ms.value}
 
 
 PROFILE_GROUPS = ("rebuild", "setup", "criterion", "sweep_A", "sweep_B", "sweep_C", "sweep_S")

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsphst.so")
-SOURCES = ["sphst_api.cu", "sphst_f32.cu", "sphst_f64.cu", "sphst_noalloc.cu"]
+SOURCES = ["sphst_api.cu", "sphst_f32.cu", "sphst_f64.cu", "sphst_noalloc.cu", "sphst_peak.cu"]
 HEADERS = ["sphst_internal.cuh", "sphst_kernels.cuh", "sphst_engine.cuh", "sphst_engine_impl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
@@ -34,9 +34,14 @@ def _stale(target: str, deps) -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile and link; SPHST_NVCC_DEFINES (e.g. "-DSPHST_SWEEP_MINB=4")
-    adds tuning defines (pass force=True when it changes)."""
+    adds tuning defines.  The defines of the last build are recorded, and a
+    change of them rebuilds everything."""
     os.makedirs(BUILD, exist_ok=True)
     extra = os.environ.get("SPHST_NVCC_DEFINES", "").split()
+    stamp = os.path.join(BUILD, "defines.txt")
+    recorded = open(stamp).read() if os.path.exists(stamp) else None
+    if recorded != " ".join(extra):
+        force = True
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(HERE, "..", "include", "sphst.h")]
     objs = []
     jobs = []
@@ -60,6 +65,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         tmp = LIB + f".tmp{os.getpid()}"
         run([nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-lcudart"])
         os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(" ".join(extra))
     return LIB
 
 

@@ -82,3 +82,11 @@ def test_diagnostics_before_first_step_and_device_observables():
     x0 = pos[ph == 0]
     assert abs(an_dev - an_host) <= 1e-12 * float((x0 ** 2).mean())
     S.destroy(h)
+
+
+def test_fma_peak_is_plausible():
+    # 152 SMs x 128 FP32 lanes x 2 flop x ~2 GHz ~ 80 TFLOP/s; FP64 far lower
+    f32 = S.fma_peak(32)["tflops"]
+    f64 = S.fma_peak(64)["tflops"]
+    assert 20.0 < f32 < 200.0, f32
+    assert 0.05 < f64 < f32, f64
