@@ -50,7 +50,8 @@ class Params(C.Structure):
                 ("nhat_eps", C.c_double), ("max_substeps", C.c_int64),
                 ("tvf_alpha", C.c_double), ("cfl_ad", C.c_double), ("cfl_ac", C.c_double),
                 ("periodic", C.c_int32), ("pad2_", C.c_int32),
-                ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3)]
+                ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
+                ("vstar_form", C.c_int32), ("pad3_", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -111,7 +112,8 @@ def make_params(dim: int, dx: float, h: float, c0: float, gamma: float,
                 n: int = 0, n_threads: int = 0, nhat_eps: float = 1e-4,
                 max_substeps: int = 0, tvf_alpha: float = 0.2,
                 penalty_form: int = 0, cfl_ad: float = 0.1, cfl_ac: float = 0.6,
-                periodic: int = 0, box_lo=(0.0, 0.0, 0.0), box_hi=(0.0, 0.0, 0.0)) -> Params:
+                periodic: int = 0, box_lo=(0.0, 0.0, 0.0), box_hi=(0.0, 0.0, 0.0),
+                vstar_form: int = 0) -> Params:
     """Build a parameter block.  nbr_mode None: brute force below 4096
     particles, uniform grid above."""
     p = Params()
@@ -127,6 +129,7 @@ def make_params(dim: int, dx: float, h: float, c0: float, gamma: float,
     p.penalty_form = penalty_form
     p.cfl_ad, p.cfl_ac = cfl_ad, cfl_ac
     p.periodic = periodic
+    p.vstar_form = vstar_form
     for a in range(3):
         p.box_lo[a], p.box_hi[a] = box_lo[a], box_hi[a]
     return p

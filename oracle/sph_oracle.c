@@ -76,11 +76,14 @@
 /* ------------------------------------------------------------------------ */
 typedef struct {
     int32_t dim;          /* 2 or 3 */
-    int32_t limiter;      /* 0: dimensionless reading of Eq. 11; 1: beta = 1; 2: beta = 0 */
+    int32_t limiter;      /* 0: dimensionless reading of Eq. 11; 1: beta = 1; 2: beta = 0;
+                             3: Eq. 11 as printed, (P_L + P_R) kept */
     int32_t grad_mode;    /* 0: common colour side for gradCbar; 1: as printed */
     int32_t nbr_mode;     /* 0: O(N^2) search; 1: uniform grid */
     int32_t n_threads;    /* <= 0: OpenMP default */
-    int32_t penalty_form; /* 0: C-hat = C I - A A^T/|A|; 1: C I - A^T A/|A| */
+    int32_t penalty_form; /* 0: C-hat = C I - A A^T/|A|; 1: C I - A^T A/|A|;
+                             2: the scalar C_ij - gradCbar.r_ij of Eq. 29 times I
+                             (not momentum-conserving, an ablation) */
     double dx;            /* initial particle spacing dp */
     double h;             /* smoothing length (1.3 dp in Section 5) */
     double c0;            /* one sound speed for all phases (Section 2) */
@@ -96,6 +99,8 @@ typedef struct {
     int32_t periodic;     /* bit d set: axis d is periodic on [box_lo[d], box_hi[d]) */
     int32_t pad2_;
     double box_lo[3], box_hi[3];
+    int32_t vstar_form;   /* 0: normal component -U* (reading); 1: Eq. 8 as printed */
+    int32_t pad3_;
 } ora_params;
 
 typedef struct {
@@ -493,7 +498,8 @@ static double limiter_beta(const ora_params *P, rstate L, rstate R)
 {
     if (P->limiter == 1) return 1.0;
     if (P->limiter == 2) return 0.0;
-    double x = (L.rho + R.rho) * (L.U - R.U) / (L.rho * L.c + R.rho * R.c);
+    double num = P->limiter == 3 ? L.p + R.p : L.rho + R.rho;   /* 3: as printed */
+    double x = num * (L.U - R.U) / (L.rho * L.c + R.rho * R.c);
     double b = 3.0 * (x > 0.0 ? x : 0.0);
     return b < 1.0 ? b : 1.0;
 }
@@ -522,7 +528,7 @@ static double riemann_Ustar(rstate L, rstate R)
 /* Eq. 8, first line, with Eq. 12's pair averages.  reading: with
  * U = -v.e_ij (Eq. 10) the star velocity has normal component -U* along
  * e_ij and keeps the tangential part of the averaged velocity. */
-static void riemann_vstar(rstate L, rstate R, double rho_i, const double *v_i,
+static void riemann_vstar(const ora_params *P, rstate L, rstate R, double rho_i, const double *v_i,
                           double rho_j, const double *v_j, const double *e,
                           int dim, double *vstar)
 {
@@ -530,7 +536,8 @@ static void riemann_vstar(rstate L, rstate R, double rho_i, const double *v_i,
     double Ubar = (L.rho * L.U + R.rho * R.U) / (L.rho + R.rho);
     for (int d = 0; d < dim; ++d) {
         double vbar = (rho_i * v_i[d] + rho_j * v_j[d]) / (rho_i + rho_j);
-        vstar[d] = -Us * e[d] + (vbar + Ubar * e[d]);
+        vstar[d] = P->vstar_form == 1 ? Us * e[d] + (vbar - Ubar * e[d])     /* as printed */
+                                      : -Us * e[d] + (vbar + Ubar * e[d]);
     }
 }
 
@@ -549,7 +556,7 @@ void ora_riemann_pair(const ora_params *P, double rho_i, double p_i,
     out[2] = limiter_beta(P, L, R);
     out[3] = pbar;
     double vs[3] = {0, 0, 0};
-    riemann_vstar(L, R, rho_i, v_i, rho_j, v_j, e, dim, vs);
+    riemann_vstar(P, L, R, rho_i, v_i, rho_j, v_j, e, dim, vs);
     for (int d = 0; d < 3; ++d) out[4 + d] = vs[d];
 }
 
@@ -783,10 +790,12 @@ static void pressure_surface_acc(const ora_params *P, const state_t *S,
                         AtA[3 * a + b] = s;
                     }
                 double Chat[9] = {0};
+                double gr = dot3(gbar, rvec, dim);            /* Eq. 29: scalar C-hat */
                 for (int a = 0; a < dim; ++a)
                     for (int b = 0; b < dim; ++b)
-                        Chat[3 * a + b] = (a == b ? Cij : 0.0)
-                                          - (normA > 0.0 ? AtA[3 * a + b] / normA : 0.0);
+                        Chat[3 * a + b] = P->penalty_form == 2
+                            ? (a == b ? Cij - gr : 0.0)
+                            : (a == b ? Cij : 0.0) - (normA > 0.0 ? AtA[3 * a + b] / normA : 0.0);
                 /* projection: T-bar (same phase) or N-bar (other phase) */
                 double M[9] = {0};
                 for (int a = 0; a < dim; ++a)
@@ -845,7 +854,7 @@ static void continuity_rate(const ora_params *P, const state_t *S, const pairs_t
                     double rho_j = S->rho[j], p_j = pressure_of(P, S, j);
                     rstate L = {rho_i, -dot3(vi, e, dim), p_i, c0};
                     rstate R = {rho_j, -dot3(vj, e, dim), p_j, c0};
-                    riemann_vstar(L, R, rho_i, vi, rho_j, vj, e, dim, vs);
+                    riemann_vstar(P, L, R, rho_i, vi, rho_j, vj, e, dim, vs);
                 } else {
                     for (int d = 0; d < dim; ++d) vs[d] = vj[d];
                 }
