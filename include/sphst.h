@@ -61,6 +61,7 @@ extern "C" {
 #define SPHST_LIMITER_DENSITY 0
 #define SPHST_LIMITER_NONE    1      /* beta = 1: full acoustic dissipation  */
 #define SPHST_LIMITER_ZERO    2      /* beta = 0: P* is the pair average     */
+#define SPHST_LIMITER_PRINTED 3      /* (P_L + P_R) kept as printed          */
 /* Eq. 28 average colour gradient of a pair of different phases: COMMON takes
  * j's colour on i's side, (gradC_i - gradC_j)/2; PRINTED is (gradC_i + gradC_j)/2 */
 #define SPHST_GRAD_COMMON  0
@@ -69,6 +70,14 @@ extern "C" {
  * (= |gradCbar| r_ij nbar nbar^T); EE as A^T A/|A| (= |gradCbar| r_ij e e^T) */
 #define SPHST_PENALTY_NN 0
 #define SPHST_PENALTY_EE 1
+/* the scalar C_ij - gradCbar . r_ij of Eq. 29 (the paper's first penalty,
+ * which it notes does not conserve momentum), for ablation */
+#define SPHST_PENALTY_SCALAR 2
+/* Eq. 8's star velocity: CORRECTED takes the normal component as -U* along
+ * e_ij (U = -v.e_ij, Eq. 10) and the tangential part of the pair average;
+ * PRINTED is U* e_ij + (vbar - Ubar e_ij) as printed */
+#define SPHST_VSTAR_CORRECTED 0
+#define SPHST_VSTAR_PRINTED   1
 /* acoustic substep loop: GRAPH runs it as a device-driven while loop inside a
  * CUDA graph (no host round trip per substep); HOST polls a device flag after
  * every substep */
@@ -125,7 +134,7 @@ typedef struct {
                                m = floor(L / (2h (1 + 2^-16))) >= 3 cells of
                                width L / m; every periodic axis must give the
                                same width (else INVALID_ARG).  0: none         */
-    int32_t pad2_;
+    int32_t vstar_form;     /* SPHST_VSTAR_* (continuity, Eq. 6)               */
     double  period_lo[3];
     double  period_hi[3];
 } sphst_case_params;

@@ -24,9 +24,10 @@ ERR_NONFINITE, ERR_TIMEOUT, ERR_OVER_BUDGET, ERR_DOMAIN = -6, -7, -8, -9
 ERR_COINCIDENT, ERR_STALLED, ERR_CAPACITY, ERR_NEIGHBORS = -10, -11, -12, -13
 NBR_LIST, NBR_CELLS = 0, 1
 FLUID, WALL = 0, 1
-LIMITER_DENSITY, LIMITER_NONE, LIMITER_ZERO = 0, 1, 2
+LIMITER_DENSITY, LIMITER_NONE, LIMITER_ZERO, LIMITER_PRINTED = 0, 1, 2, 3
 GRAD_COMMON, GRAD_PRINTED = 0, 1
-PENALTY_NN, PENALTY_EE = 0, 1
+PENALTY_NN, PENALTY_EE, PENALTY_SCALAR = 0, 1, 2
+VSTAR_CORRECTED, VSTAR_PRINTED = 0, 1
 LOOP_GRAPH, LOOP_HOST = 0, 1
 FIELD_POS, FIELD_VEL, FIELD_RHO, FIELD_PRESSURE, FIELD_PHASE, FIELD_GRADC, FIELD_ACC_VISC = range(7)
 VECTOR_FIELDS = (FIELD_POS, FIELD_VEL, FIELD_GRADC, FIELD_ACC_VISC)
@@ -40,7 +41,7 @@ class CaseParams(C.Structure):
                 ("grid_pad", C.c_int32), ("block", C.c_int32), ("max_substeps", C.c_int64),
                 ("cfl_ad", C.c_double), ("cfl_ac", C.c_double),
                 ("nbr_mode", C.c_int32), ("max_neighbors", C.c_int32),
-                ("periodic", C.c_int32), ("pad2_", C.c_int32),
+                ("periodic", C.c_int32), ("vstar_form", C.c_int32),
                 ("period_lo", C.c_double * 3), ("period_hi", C.c_double * 3)]
 
 

@@ -139,7 +139,7 @@ template <typename T> static CasePhys<T> phys_of(const CaseRec *c) {
     p.inv_c0 = (T)(1.0 / P.c0);
     p.gamma = (T)P.gamma;
     // limiter (Eq. 11): density reading min(max(3 dU / c0, 0), 1); beta = 1; beta = 0
-    p.beta_k = (T)(P.limiter == SPHST_LIMITER_DENSITY ? 3.0 / P.c0 : 0.0);
+    p.beta_k = (T)((P.limiter == SPHST_LIMITER_DENSITY || P.limiter == SPHST_LIMITER_PRINTED) ? 3.0 / P.c0 : 0.0);
     p.beta_lo = (T)(P.limiter == SPHST_LIMITER_NONE ? 1.0 : 0.0);
     p.beta_hi = (T)(P.limiter == SPHST_LIMITER_ZERO ? 0.0 : 1.0);
     p.xi = (T)xi;
@@ -178,6 +178,7 @@ CaseDesc make_desc(const CaseRec *c) {
     d.cfl_ac = c->P.cfl_ac;
     d.nbr_mode = c->P.nbr_mode;
     d.periodic = c->P.periodic;
+    d.vstar_printed = c->P.vstar_form == SPHST_VSTAR_PRINTED;
     for (int a = 0; a < 3; ++a)
         d.period_len[a] = ((c->P.periodic >> a) & 1) ? c->P.period_hi[a] - c->P.period_lo[a] : 0.0;
     d.nbr_k = c->P.max_neighbors > 0 ? c->P.max_neighbors : (c->P.dim == 3 ? 128 : 48);
@@ -190,7 +191,7 @@ int64_t footprint(const sphst_case_params *P, int64_t n) {
     const int64_t tsz = P->precision == 64 ? 8 : 4;
     const int64_t kmax = P->nbr_mode == SPHST_NBR_LIST
                              ? (P->max_neighbors > 0 ? P->max_neighbors : (P->dim == 3 ? 128 : 48)) : 0;
-    const int64_t per = 9 * 4 * tsz + 2 * tsz + 4 * 4 + 4 * kmax + 4 + 1;  // V4 arrays, scalars, ints, list, band
+    const int64_t per = 9 * 4 * tsz + 2 * tsz + 4 * 4 + 4 * kmax + 4 + 1 + 8;  // V4 arrays, scalars, ints, list, band + band list
     // cell table: cells ~ n / 2.6^d per axis padded to a power of two
     const double side = std::pow((double)std::max<int64_t>(n, 1), 1.0 / P->dim) / 2.6 + 2.0 * P->grid_pad + 2.0;
     int bits = 0;
@@ -283,8 +284,9 @@ int sphst_create_case(const sphst_case_params *params, sphst_case *out) {
         set_error("dx, h_factor, c0, cfl_ad and cfl_ac must be > 0; gamma and tvf_alpha >= 0; xi finite");
         return SPHST_ERR_INVALID_ARG;
     }
-    if (P.limiter < 0 || P.limiter > 2 || P.grad_mode < 0 || P.grad_mode > 1 ||
-        P.penalty_form < 0 || P.penalty_form > 1 || P.loop_mode < 0 || P.loop_mode > 1) {
+    if (P.limiter < 0 || P.limiter > 3 || P.grad_mode < 0 || P.grad_mode > 1 ||
+        P.penalty_form < 0 || P.penalty_form > 2 || P.loop_mode < 0 || P.loop_mode > 1 ||
+        P.vstar_form < 0 || P.vstar_form > 1) {
         set_error("unknown reading or loop flag");
         return SPHST_ERR_INVALID_ARG;
     }

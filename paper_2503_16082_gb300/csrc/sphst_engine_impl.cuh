@@ -45,6 +45,9 @@ template <typename T> struct EngineT : Engine {
     uint32_t *starts = nullptr, *block_sums = nullptr;
     uint32_t *nbr = nullptr, *nbr_cnt = nullptr;   // neighbour lists (ELL per case) and counts
     uint8_t *band = nullptr;                        // interface band of the frozen configuration
+    uint64_t *band_list = nullptr;                  // band particles per list class (case << 32 | index)
+    uint32_t *band_count = nullptr;                 // entries of each class's band list
+    int64_t band_base[2] = {0, 0};                  // first entry of each list class
     int64_t nbr_total = 0;
     bool any_list = false;
     // cases
@@ -158,6 +161,7 @@ template <typename T> struct EngineT : Engine {
         size_t o_read = take((size_t)std::max<int64_t>(max_case_n, 1) * 3 * sizeof(double));
         size_t o_nbr = take((size_t)std::max<int64_t>(nbr_total, 1) * 4), o_ncnt = take(nn * 4);
         size_t o_band = take(nn);
+        size_t o_blist = take(nn * 8), o_bcount = take(64);
         size_t o_diag = take((size_t)(DIAG_BLOCKS + 1) * DIAG_Q * sizeof(double));
         cudaError_t e = cudaMalloc(&arena, off);
         if (e != cudaSuccess) {
@@ -181,6 +185,8 @@ template <typename T> struct EngineT : Engine {
         nbr = (uint32_t *)(b + o_nbr);
         nbr_cnt = (uint32_t *)(b + o_ncnt);
         band = (uint8_t *)(b + o_band);
+        band_list = (uint64_t *)(b + o_blist);
+        band_count = (uint32_t *)(b + o_bcount);
         d_diag = (double *)(b + o_diag);
         SPH_CK(cudaMemsetAsync(arena, 0, off, stream));
         // tiles, grouped by class
@@ -195,6 +201,11 @@ template <typename T> struct EngineT : Engine {
             }
             cls_n[k] = (int64_t)tiles.size() - cls_b[k];
         }
+        // band lists of the two list classes, one after the other
+        int64_t np0 = 0;
+        for (int64_t t = cls_b[0]; t < cls_b[0] + cls_n[0]; ++t) np0 += tiles[t].n;
+        band_base[0] = 0;
+        band_base[1] = np0;
         SPH_CK(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, stream));
         SPH_CK(cudaMemcpyAsync(d_desc, h_desc.data(), sizeof(CaseDesc) * ncases, cudaMemcpyHostToDevice, stream));
         // fill each case
@@ -285,7 +296,8 @@ template <typename T> struct EngineT : Engine {
         k_gather<T><<<pgrid, nthr, 0, stream>>>(n, perm, pos, vel, drho, id, snap, vel_new, drho_old, rank);
         k_copy_back<T><<<pgrid, nthr, 0, stream>>>(n, snap, vel_new, drho_old, rank, pos, vel, drho, id);
         SPH_CLASSES(2, k_build_list, snap, nbr, nbr_cnt);
-        SPH_CLASSES(2, k_band, snap, band);
+        SPH_CK(cudaMemsetAsync(band_count, 0, 2 * sizeof(uint32_t), stream));
+        SPH_CLASSES(2, k_band, snap, band, band_list + band_base[k_], band_count + k_);
         if (any_tvf) SPH_CLASSES(4, k_sweep_M, snap, drho, bmat);
         SPH_CLASSES(4, k_sweep_V, snap, drho, vel, bmat, acc_visc, pos);
         SPH_CK(cudaGetLastError());
@@ -295,7 +307,7 @@ template <typename T> struct EngineT : Engine {
     int launch_body(cudaGraphConditionalHandle h, int use_handle) {
         k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, h, use_handle);
         SPH_CLASSES(4, k_sweep_A, snap, drho, gradC);
-        SPH_CLASSES(2, k_sweep_S, band, snap, vel, gradC, acc_surf);
+        SPH_CLASSES(2, k_sweep_S, band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
         SPH_CLASSES(4, k_sweep_B, band, snap, vel, gradC, acc_visc, acc_surf, vel_new);
         SPH_CLASSES(4, k_sweep_C, snap, vel_new, drho, vel, pos);
         SPH_CK(cudaGetLastError());
@@ -416,7 +428,8 @@ template <typename T> struct EngineT : Engine {
         });
         timed(0, 2 * nlist, [&] {
             SPH_CLASSES(2, k_build_list, snap, nbr, nbr_cnt);
-            SPH_CLASSES(2, k_band, snap, band);
+            cudaMemsetAsync(band_count, 0, 2 * sizeof(uint32_t), stream);
+            SPH_CLASSES(2, k_band, snap, band, band_list + band_base[k_], band_count + k_);
         });
         timed(1, any_tvf ? 2 * ncls : ncls, [&] {
             if (any_tvf) SPH_CLASSES(4, k_sweep_M, snap, drho, bmat);
@@ -425,7 +438,9 @@ template <typename T> struct EngineT : Engine {
         for (;;) {
             timed(2, 1, [&] { k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, 0, 0); });
             timed(3, ncls, [&] { SPH_CLASSES(4, k_sweep_A, snap, drho, gradC); });
-            timed(6, nlist, [&] { SPH_CLASSES(2, k_sweep_S, band, snap, vel, gradC, acc_surf); });
+            timed(6, nlist, [&] {
+                SPH_CLASSES(2, k_sweep_S, band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
+            });
             timed(4, ncls, [&] { SPH_CLASSES(4, k_sweep_B, band, snap, vel, gradC, acc_visc, acc_surf, vel_new); });
             timed(5, ncls, [&] { SPH_CLASSES(4, k_sweep_C, snap, vel_new, drho, vel, pos); });
             if (rc) break;

@@ -95,7 +95,7 @@ struct CaseDesc {
     int64_t table_off;         // first cell-table entry of this case
     int64_t table_size;        // 2^(dim*bits)
     int32_t periodic;          // bit a: axis a wraps (ncell[a] cells of width cs tile the period)
-    int32_t pad_per;
+    int32_t vstar_printed;     // Eq. 8's v* as printed (else: normal component -U*)
     double period_len[3];      // period of each periodic axis
     double origin[3];
     double cs;

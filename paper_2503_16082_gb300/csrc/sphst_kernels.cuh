@@ -245,15 +245,21 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return v;
 }
 
-// Eq. 11 dissipation limiter, branch-free: min(max(k dU, lo), hi) with the
-// case's (k, lo, hi) = (3 / c0, 0, 1) for the density reading, (0, 1, 1) for
-// beta = 1 and (0, 0, 0) for beta = 0
+// Eq. 11 dissipation limiter, branch-free: min(max(k dU w, lo), hi) with the
+// case's (k, lo, hi) = (3 / c0, 0, 1) for the density reading and the printed
+// form, (0, 1, 1) for beta = 1 and (0, 0, 0) for beta = 0; w = 1, or for the
+// printed form (P_L + P_R)/(rho_L + rho_R) of the pair
 __device__ __forceinline__ float clamp_lh(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
 __device__ __forceinline__ double clamp_lh(double x, double lo, double hi) { return fmin(fmax(x, lo), hi); }
 template <typename T> struct Limiter {
     T k, lo, hi;
-    __device__ __forceinline__ explicit Limiter(const CasePhys<T> &cp) : k(cp.beta_k), lo(cp.beta_lo), hi(cp.beta_hi) {}
-    __device__ __forceinline__ T operator()(T dU) const { return clamp_lh(k * dU, lo, hi); }
+    bool printed;
+    __device__ __forceinline__ Limiter(const CasePhys<T> &cp, int mode)
+        : k(cp.beta_k), lo(cp.beta_lo), hi(cp.beta_hi), printed(mode == 3) {}
+    __device__ __forceinline__ T operator()(T dU, T psum, T rhosum) const {
+        const T x = printed ? k * dU * div_fast(psum, rhosum) : k * dU;
+        return clamp_lh(x, lo, hi);
+    }
 };
 
 // Neighbour cell index along axis a: wrapped on a periodic axis (the cells
@@ -1002,7 +1008,7 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
     const T rho_i = sel(ki, cp.rho0[0], cp.rho0[1]) + dri;
     const T p_i = cp.c0sq * dri;
     T apx = 0, apy = 0, apz = 0, asx = 0, asy = 0, asz = 0;
-    const Limiter<T> limiter_beta(cp);
+    const Limiter<T> limiter_beta(cp, d.limiter);
     const T c0 = cp.c0, c0sq = cp.c0sq, vol_wall = cp.vol_wall;
     const T rho0_0 = cp.rho0[0], rho0_1 = cp.rho0[1], m_0 = cp.mass[0], m_1 = cp.mass[1];
     const KernelGeo<T> kgeo(cp);
@@ -1019,7 +1025,7 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
         if (kj == PH_WALL) {
             // mirror state behind a wall moving with v_w: rho_i, p_i, 2 U_w - U_L
             const T dU = T(2) * dUe;
-            const T beta = limiter_beta(dU);
+            const T beta = limiter_beta(dU, p_i, rho_i);       // mirror state: rho_R, p_R = rho_i, p_i
             const T Ps = p_i + beta * rho_i * c0 * dU * T(0.5);
             const T f = Ps * g.dW * vol_wall;
             const L2<T> a = fma2(l2(f, f), exy, l2(apx, apy));
@@ -1030,7 +1036,7 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
         const T rho_j = sel(kj, rho0_0, rho0_1) + drj;
         const T p_j = c0sq * drj;
         const T dU = dUe;
-        const T beta = limiter_beta(dU);                        // Eq. 11
+        const T beta = limiter_beta(dU, p_i + p_j, rho_i + rho_j);   // Eq. 11
         // P* V_j with P* = (rho_i p_j + rho_j p_i + beta c0 rho_i rho_j dU) / (rho_i + rho_j)
         // (Eqs. 8, 12) and V_j = m_j / rho_j: one division
         const T num = (rho_i * p_j + rho_j * p_i) + beta * c0 * rho_i * rho_j * dU;
@@ -1076,7 +1082,9 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
             const T fac = g.r * (bx * ex + by * ey + bz * ez) * inv_bn;
             cx = Cij * ex - fac * bx; cy = Cij * ey - fac * by; cz = Cij * ez - fac * bz;
         } else {
-            const T s = Cij - b2 * inv_bn * g.r;
+            // EE: (C_ij - |gradCbar| r) e; SCALAR (Eq. 29): (C_ij - gradCbar . r_ij) e
+            const T s = d.penalty_form == 1 ? Cij - b2 * inv_bn * g.r
+                                            : Cij - g.r * (bx * ex + by * ey + bz * ez);
             cx = s * ex; cy = s * ey; cz = s * ez;
         }
         // N-bar C-hat e = (n_i (n_i.c) + n_j (n_j.c)) / 2
@@ -1147,6 +1155,10 @@ __device__ __forceinline__ void sweep_C(const CaseDesc &d, const CasePhys<T> &cp
     const T rho_i = sel(ki, rho0_0, rho0_1) + dri;
     const T p_i = c0sq * dri;
     const KernelGeo<T> kgeo(cp);
+    // the pressure difference enters with the sign of the v* reading; the
+    // sign is folded into p_i and c0^2 once
+    const T psign = d.vstar_printed ? T(-1) : T(1);
+    const T sp_i = psign * p_i, sc0sq = psign * c0sq;
     T s = 0;
     neighbors_aux<LIST, T, D>(d, cp, starts, nbr, cnt, snap, vel_new, i, si, pki,
         [&](uint32_t, const V4<T> &sj, const V4<T> &vj, T rx, T ry, T rz, T r2) {
@@ -1162,10 +1174,10 @@ __device__ __forceinline__ void sweep_C(const CaseDesc &d, const CasePhys<T> &cp
             }
             const T drj = vj.w;
             const T rho_j = sel(kj, rho0_0, rho0_1) + drj;
-            const T p_j = c0sq * drj;
             // (v_i - v*).e V_j with (v_i - v*).e = U* - U_L = (Z_R (U_R - U_L) + p_i - p_j)
-            // / (Z_L + Z_R) and V_j = m_j / rho_j: one division
-            const T num = (rho_j * c0 * dve + (p_i - p_j)) * sel(kj, m_0, m_1);
+            // / (Z_L + Z_R) and V_j = m_j / rho_j: one division.  The printed v*
+            // gives (Z_R (U_R - U_L) - (p_i - p_j)) / (Z_L + Z_R) instead.
+            const T num = (rho_j * c0 * dve + (sp_i - sc0sq * drj)) * sel(kj, m_0, m_1);
             s += div_fast(num, c0 * (rho_i + rho_j) * rho_j) * g.dW;
         });
     const T dr_new = dri + dt * (T(2) * rho_i * s);
@@ -1237,22 +1249,36 @@ __device__ __forceinline__ void build_list(const CaseDesc &d, const CasePhys<T> 
 }
 
 // ---- interface band of the frozen configuration: i, or one of its
-// neighbours, has neighbours of the other fluid phase
+// neighbours, has neighbours of the other fluid phase.  Band particles are
+// also appended, as (case << 32 | index), to the class's list that the
+// surface sweep walks (warp-aggregated atomics; the order is irrelevant
+// because every particle's sum is its own).
 template <typename T, int D, bool LIST>
-__global__ void __launch_bounds__(256) k_band(SweepArgs a, const V4<T> *snap, uint8_t *band) {
+__global__ void __launch_bounds__(256) k_band(SweepArgs a, const V4<T> *snap, uint8_t *band,
+                                              uint64_t *blist, uint32_t *bcount) {
     const Tile t = a.tiles[a.tile0 + blockIdx.x];
-    if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
-    const CaseDesc &d = a.desc[t.c];
+    const bool live = (int)threadIdx.x < t.n && a.st[t.c].active;
     const int64_t i = t.begin + threadIdx.x;
-    const uint32_t ci = a.cnt[i];
-    bool b = (ci >> 16) != 0;
-    if (!b && d.n_fluid_phases == 2) {
-        const int64_t stride = d.p_end - d.p_begin;
-        const uint32_t *p = a.nbr + d.nbr_base + (i - d.p_begin);
-        const uint32_t c = ci & CNT_MASK;
-        for (uint32_t k = 0; k < c && !b; ++k, p += stride) b = (a.cnt[ld_list(p) >> NBR_SHIFT] >> 16) != 0;
+    bool b = false;
+    if (live) {
+        const CaseDesc &d = a.desc[t.c];
+        const uint32_t ci = a.cnt[i];
+        b = (ci >> 16) != 0;
+        if (!b && d.n_fluid_phases == 2) {
+            const int64_t stride = d.p_end - d.p_begin;
+            const uint32_t *p = a.nbr + d.nbr_base + (i - d.p_begin);
+            const uint32_t c = ci & CNT_MASK;
+            for (uint32_t k = 0; k < c && !b; ++k, p += stride) b = (a.cnt[ld_list(p) >> NBR_SHIFT] >> 16) != 0;
+        }
+        band[i] = b ? 1 : 0;
     }
-    band[i] = b ? 1 : 0;
+    const unsigned m = __ballot_sync(0xffffffffu, b);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(bcount, (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (b) blist[base + __popc(m & ((1u << lane) - 1u))] = ((uint64_t)(uint32_t)t.c << 32) | (uint64_t)(uint32_t)i;
 }
 
 template <typename T, int D, bool LIST>
@@ -1294,14 +1320,20 @@ __global__ void SPH_SWEEP_BOUNDS k_sweep_A(SweepArgs a, const V4<T> *snap, const
     sweep_A<LIST, T, D>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, gradC);
 }
 
-// surface sum of the band particles (list classes only), before B
+// surface sum of the band particles (list classes only), before B: one
+// thread per entry of the class's compacted band list, so warps are full of
+// band particles; threads past the list's length exit at once
 template <typename T, int D, bool LIST>
-__global__ void SPH_SWEEP_BOUNDS k_sweep_S(SweepArgs a, const uint8_t *band, const V4<T> *snap, const V4<T> *vel,
+__global__ void SPH_SWEEP_BOUNDS k_sweep_S(SweepArgs a, const uint64_t *blist, const uint32_t *bcount,
+                                           const uint8_t *band, const V4<T> *snap, const V4<T> *vel,
                                            const V4<T> *gradC, V4<T> *acc_surf) {
-    const Tile t = a.tiles[a.tile0 + blockIdx.x];
-    if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
-    const CaseDesc &d = a.desc[t.c];
-    const int64_t i = t.begin + threadIdx.x;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (int64_t)*bcount) return;
+    const uint64_t e = blist[k];
+    const int c = (int)(e >> 32);
+    const int64_t i = (int64_t)(uint32_t)e;
+    if (!a.st[c].active) return;
+    const CaseDesc &d = a.desc[c];
     uint32_t ph;
     sweep_B<LIST, 2, T, D>(d, phys<T>(d), T(0), i, a.starts, a.nbr, a.cnt, band, snap, vel, gradC, nullptr,
                            acc_surf, nullptr, &ph);

@@ -140,6 +140,8 @@ def test_fp32_one_advection_step(dim):
     (dict(penalty_form=1), dict(penalty_form=1)),
     (dict(tvf_alpha=0.0), dict(tvf_alpha=0.0)),
     (dict(xi=0.0), dict(xi=0.0)),
+    (dict(limiter=3), dict(limiter=3)),
+    (dict(penalty_form=2), dict(penalty_form=2)),
 ])
 def test_fp64_readings_flags(opts, ora):
     case = small(2)
@@ -147,6 +149,28 @@ def test_fp64_readings_flags(opts, ora):
     assert info["n_sub"] == oinfo["n_sub"]
     for key in ("pos", "vel", "rho", "gradC"):
         assert rel_err(g, o, pos0, kind, key, case) <= 1e-12, key
+
+
+def test_fp64_printed_vstar_one_substep():
+    # the printed v* of Eq. 8 is anti-diffusive and diverges within an
+    # advection step; compared over one acoustic substep of a state with
+    # density (pressure) differences, where it departs from the default
+    case = sphcases.free_blob(dim=2, n_side=20, seed=5, vel_amp=0.05, rho_ratio=10.0, rho_jitter=1e-3)
+    pos, vel, rho, kind = case.flat()
+    out = {}
+    for form in (0, 1):
+        h = gpu_case(case, 64, vstar_form=form, max_substeps=1)
+        S.step(h, 1, check=False)
+        out[form] = S.read_fields(h, S.FIELD_RHO, 2)
+        S.destroy(h)
+    P = oracle.params_for_case(case, vstar_form=1, max_substeps=1)
+    _, _, orho, oinfo, _, _ = oracle.run(P, pos, vel, rho, kind, 1)
+    assert oinfo["n_sub"] == 1
+    fl = kind < 2
+    rho0 = np.asarray(case.fluid_props()[0])[kind[fl]]
+    a, b = out[1][fl] - rho0, orho[fl] - rho0
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+    assert np.abs(out[0][fl] - out[1][fl]).max() > 1e-9 * np.abs(b).max()
 
 
 @pytest.mark.parametrize("precision", [32, 64])
