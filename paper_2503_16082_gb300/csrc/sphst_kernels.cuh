@@ -1226,23 +1226,48 @@ __device__ __forceinline__ void build_list(const CaseDesc &d, const CasePhys<T> 
     uint32_t *base = nbr + d.nbr_base + (i - d.p_begin);
     const uint32_t kmax = (uint32_t)d.nbr_k;
     const uint32_t other = phase_of(pki) ^ 1u;
-    uint32_t c = 0, c_other = 0;
-    bool overflow = false, coinc = false;
-    // two walks: neighbours of the other fluid phase, then all the rest
-    for (int part = 0; part < 2; ++part) {
-        coinc |= walk<T, D>(d, cp, starts, snap, i, si, pki,
-            [&](uint32_t j, const V4<T> &sj, T, T, T, T) {
-                const uint32_t pkj = w_bits(sj.w);
-                if ((phase_of(pkj) == other) != (part == 0)) return;
-                if (c >= kmax) { overflow = true; return; }
-                const uint32_t code = cell_code<D>(cell_step(d, 0, cell_x<D>(pkj) - cx),
-                                                   cell_step(d, 1, cell_y<D>(pkj) - cy),
-                                                   D == 3 ? cell_step(d, 2, cell_z<D>(pkj) - cz) : 0);
-                base[(int64_t)c * stride] = (j << NBR_SHIFT) | code;
-                ++c;
-            });
-        if (part == 0) c_other = c;
+    const auto entry_of = [&](uint32_t j, uint32_t pkj) {
+        const uint32_t code = cell_code<D>(cell_step(d, 0, cell_x<D>(pkj) - cx),
+                                           cell_step(d, 1, cell_y<D>(pkj) - cy),
+                                           D == 3 ? cell_step(d, 2, cell_z<D>(pkj) - cz) : 0);
+        return (j << NBR_SHIFT) | code;
+    };
+    // one walk: the rest goes straight to the list, other-phase entries to a
+    // small buffer; then, where there are any, the rest moves up and the
+    // buffer goes in front (each part keeps the walk order)
+    constexpr uint32_t OBUF = 32;
+    uint32_t obuf[OBUF];
+    uint32_t c_rest = 0, c_other = 0;
+    bool coinc = walk<T, D>(d, cp, starts, snap, i, si, pki,
+        [&](uint32_t j, const V4<T> &sj, T, T, T, T) {
+            const uint32_t pkj = w_bits(sj.w);
+            if (phase_of(pkj) == other) {
+                if (c_other < OBUF) obuf[c_other] = entry_of(j, pkj);
+                ++c_other;
+            } else {
+                if (c_rest < kmax) base[(int64_t)c_rest * stride] = entry_of(j, pkj);
+                ++c_rest;
+            }
+        });
+    uint32_t c = c_rest + c_other;
+    bool overflow = c > kmax;
+    if (!overflow && c_other > OBUF) {
+        // rare: more other-phase neighbours than the buffer holds; two walks
+        c = 0;
+        for (int part = 0; part < 2; ++part) {
+            coinc |= walk<T, D>(d, cp, starts, snap, i, si, pki,
+                [&](uint32_t j, const V4<T> &sj, T, T, T, T) {
+                    const uint32_t pkj = w_bits(sj.w);
+                    if ((phase_of(pkj) == other) != (part == 0)) return;
+                    base[(int64_t)c * stride] = entry_of(j, pkj);
+                    ++c;
+                });
+        }
+    } else if (!overflow && c_other > 0) {
+        for (uint32_t k = c_rest; k-- > 0;) base[(int64_t)(k + c_other) * stride] = base[(int64_t)k * stride];
+        for (uint32_t k = 0; k < c_other; ++k) base[(int64_t)k * stride] = obuf[k];
     }
+    if (overflow) c = kmax;
     cnt[i] = c | (c_other << 16);
     if (coinc) atomicCAS(status, 0, DEV_ERR_COINCIDENT);
     if (overflow) atomicCAS(status, 0, DEV_ERR_NBR_OVERFLOW);
