@@ -850,25 +850,23 @@ static __global__ void k_adv_end(int ncases, CaseState *st) {
 
 // ================================================================= sweeps
 // ---- M: correction matrix of Eq. 15, B_i = -(sum_j r_ij (x) grad_i W_ij V_j)^-1
-template <bool LIST, typename T, int D>
-__device__ __forceinline__ void sweep_M(const CaseDesc &d, const CasePhys<T> &cp, int64_t i,
-                                        const uint32_t *starts, const uint32_t *nbr, const uint32_t *cnt, const V4<T> *snap, const T *drho,
-                                        V4<T> *bmat, int32_t *status) {
-    const V4<T> si = ld4(snap + i);
-    const uint32_t pki = w_bits(si.w);
-    if (phase_of(pki) == PH_WALL) return;
+template <typename T> struct Moment {
     T m00 = 0, m01 = 0, m02 = 0, m11 = 0, m12 = 0, m22 = 0;
-    const bool coinc = neighbors<LIST, T, D>(d, cp, starts, nbr, cnt, snap, i, si, pki,
-        [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
-            const PairGeo<T> g = geo(cp, r2);
-            const uint32_t kj = phase_of(w_bits(sj.w));
-            const T Vj = kj == PH_WALL ? cp.vol_wall : div_fast(cp.mass[kj], cp.rho0[kj] + drho[j]);
-            // r (x) dW e V = (dW V / r) r_vec (x) r_vec
-            const T s = g.dW * Vj * g.inv_r;
-            m00 += s * rx * rx; m01 += s * rx * ry; m11 += s * ry * ry;
-            if (D == 3) { m02 += s * rx * rz; m12 += s * ry * rz; m22 += s * rz * rz; }
-        });
-    if (coinc) atomicCAS(status, 0, DEV_ERR_COINCIDENT);
+    // adds r (x) dW e V = (dW V / r) r_vec (x) r_vec of one neighbour
+    template <int D>
+    __device__ __forceinline__ void add(const CaseDesc &, const CasePhys<T> &cp, const T *drho, uint32_t j,
+                                        uint32_t kj, T rx, T ry, T rz, T r2) {
+        const PairGeo<T> g = geo(cp, r2);
+        const T Vj = kj == PH_WALL ? cp.vol_wall : div_fast(cp.mass[kj], cp.rho0[kj] + drho[j]);
+        const T s = g.dW * Vj * g.inv_r;
+        m00 += s * rx * rx; m01 += s * rx * ry; m11 += s * ry * ry;
+        if (D == 3) { m02 += s * rx * rz; m12 += s * ry * rz; m22 += s * rz * rz; }
+    }
+};
+
+template <typename T, int D>
+__device__ __forceinline__ void store_B(const Moment<T> &M, int64_t i, V4<T> *bmat) {
+    const T m00 = M.m00, m01 = M.m01, m02 = M.m02, m11 = M.m11, m12 = M.m12, m22 = M.m22;
     T b00, b01, b02 = 0, b11, b12 = 0, b22 = 0;
     T det;
     if (D == 2) {
@@ -891,6 +889,22 @@ __device__ __forceinline__ void sweep_M(const CaseDesc &d, const CasePhys<T> &cp
     bmat[2 * i + 1] = V4<T>{b12, b22, T(0), T(0)};
 }
 
+template <bool LIST, typename T, int D>
+__device__ __forceinline__ void sweep_M(const CaseDesc &d, const CasePhys<T> &cp, int64_t i,
+                                        const uint32_t *starts, const uint32_t *nbr, const uint32_t *cnt, const V4<T> *snap, const T *drho,
+                                        V4<T> *bmat, int32_t *status) {
+    const V4<T> si = ld4(snap + i);
+    const uint32_t pki = w_bits(si.w);
+    if (phase_of(pki) == PH_WALL) return;
+    Moment<T> M;
+    const bool coinc = neighbors<LIST, T, D>(d, cp, starts, nbr, cnt, snap, i, si, pki,
+        [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
+            M.template add<D>(d, cp, drho, j, phase_of(w_bits(sj.w)), rx, ry, rz, r2);
+        });
+    if (coinc) atomicCAS(status, 0, DEV_ERR_COINCIDENT);
+    store_B<T, D>(M, i, bmat);
+}
+
 // ---- V: viscous acceleration (Eq. 13) and transport shift (Eq. 14)
 template <bool LIST, typename T, int D>
 __device__ __forceinline__ void sweep_V(const CaseDesc &d, const CasePhys<T> &cp, int64_t i,
@@ -901,35 +915,40 @@ __device__ __forceinline__ void sweep_V(const CaseDesc &d, const CasePhys<T> &cp
     const uint32_t pki = w_bits(si.w);
     const uint32_t ki = phase_of(pki);
     if (ki == PH_WALL) return;
-    const T rho_i = cp.rho0[ki] + drho[i];
-    const T eta_i = cp.eta[ki];
     const V4<T> vi = vel[i];
+    const T rho_i = sel(ki, cp.rho0[0], cp.rho0[1]) + vi.w;
+    // the pair viscosity 2 eta_i eta_j / (eta_i + eta_j) takes one value per
+    // fluid of j; walls use eta_i
+    const T eta_i = sel(ki, cp.eta[0], cp.eta[1]);
+    const T etab0 = T(2) * eta_i * cp.eta[0] / (eta_i + cp.eta[0]);
+    const T etab1 = T(2) * eta_i * cp.eta[1] / (eta_i + cp.eta[1]);
+    const T rho0_0 = cp.rho0[0], rho0_1 = cp.rho0[1], m_0 = cp.mass[0], m_1 = cp.mass[1];
+    const T vol_wall = cp.vol_wall;
+    const KernelGeo<T> kgeo(cp);
     const bool tvf = d.tvf_on != 0;
     V4<T> Bi0 = {0, 0, 0, 0}, Bi1 = {0, 0, 0, 0};
     if (tvf) { Bi0 = bmat[2 * i]; Bi1 = bmat[2 * i + 1]; }
     T ax = 0, ay = 0, az = 0, sx = 0, sy = 0, sz = 0;
-    const bool coinc = neighbors<LIST, T, D>(d, cp, starts, nbr, cnt, snap, i, si, pki,
-        [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
-            const PairGeo<T> g = geo(cp, r2);
+    const bool coinc = neighbors_aux<LIST, T, D>(d, cp, starts, nbr, cnt, snap, vel, i, si, pki,
+        [&](uint32_t j, const V4<T> &sj, const V4<T> &vj, T rx, T ry, T rz, T r2) {
+            const PairGeo<T> g = kgeo(r2);
             const uint32_t kj = phase_of(w_bits(sj.w));
-            const V4<T> vj = vel[j];
             T eta_bar, Vj;
             V4<T> Bj0 = Bi0, Bj1 = Bi1;
             if (kj == PH_WALL) {
                 eta_bar = eta_i;
-                Vj = cp.vol_wall;
+                Vj = vol_wall;
             } else {
-                const T eta_j = cp.eta[kj];
-                eta_bar = T(2) * eta_i * eta_j / (eta_i + eta_j);
-                Vj = div_fast(cp.mass[kj], cp.rho0[kj] + vj.w);
+                eta_bar = sel(kj, etab0, etab1);
+                Vj = div_fast(sel(kj, m_0, m_1), sel(kj, rho0_0, rho0_1) + vj.w);
                 if (tvf) { Bj0 = bmat[2 * j]; Bj1 = bmat[2 * j + 1]; }
             }
-            const T f = eta_bar * g.dW * Vj * g.inv_r;     // eta (v_ij / r) dW V
+            const T w = g.dW * Vj * g.inv_r;                 // grad W V = w r_vec
+            const T f = eta_bar * w;                          // eta (v_ij / r) dW V
             ax += f * (vi.x - vj.x);
             ay += f * (vi.y - vj.y);
             if (D == 3) az += f * (vi.z - vj.z);
             if (tvf) {
-                const T w = g.dW * Vj * g.inv_r;             // grad W V = w r_vec
                 const T gx = w * rx, gy = w * ry, gz = w * rz;
                 // (B_i + B_j) grad W V with symmetric B = [b00 b01 b02; b01 b11 b12; b02 b12 b22]
                 const T s00 = Bi0.x + Bj0.x, s01 = Bi0.y + Bj0.y, s02 = Bi0.z + Bj0.z;
