@@ -5,6 +5,9 @@ benchmark's CPU-baseline leg use it; the product path never does.  The
 arithmetic lives in ``sph_oracle.c`` (plain C, FP64, OpenMP over particles);
 this module only builds it with gcc and marshals numpy arrays through ctypes.
 
+``SPH_ORACLE_LIB`` may name a separately built library of the same source;
+the pin-strength test uses it to load copies with planted mistakes.
+
 Parity unpinned (see the header of ``sph_oracle.c``): the magnitude of the
 penalty force, the wall model and the integrator are fixed only by agreement
 with the CUDA path and the integral observables.
@@ -64,8 +67,10 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            lib = C.CDLL(_LIB_PATH)
+            # SPH_ORACLE_LIB: a separately built library of the same source
+            # (the pin-strength test loads deliberately broken copies)
+            path = os.environ.get("SPH_ORACLE_LIB") or build()
+            lib = C.CDLL(path)
             P = C.POINTER
             d, i32, i64 = C.c_double, C.c_int32, C.c_int64
             dp, ip, lp = P(C.c_double), P(C.c_int32), P(C.c_int64)

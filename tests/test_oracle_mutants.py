@@ -1,0 +1,66 @@
+"""Strength of the oracle's pins: plausible mistakes are planted, one at a
+time, in a copy of the oracle's source (never in the oracle itself), the
+copy is compiled on the CPU, and the CPU pins are run against it; every
+planted mistake must make at least one pin fail.
+
+The mistakes: a wrong kernel normalisation or derivative sign, a flipped
+pressure force, the neighbour's stress dropped from Eq. 26, the colour
+weight phi_i replaced by phi_j (Eq. 22), an arithmetic instead of a
+harmonic pair viscosity (Eq. 13), the pressure difference of U* (Eq. 9)
+reversed, the density update reversed (Eq. 6).  An unmodified copy passes
+the same harness."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "sph_oracle.c")
+PINS = ["test_oracle_kernel.py", "test_oracle_neighbors.py", "test_oracle_riemann.py",
+        "test_oracle_invariants.py", "test_oracle_dynamics.py", "test_oracle_periodic.py",
+        "test_oracle_reading_flags.py", "test_oracle_weights.py", "test_golden.py"]
+
+MUTANTS = {
+    "kernel normalisation": ("return dim == 2 ? 7.0 / (4.0 * ORA_PI * h * h)",
+                             "return dim == 2 ? 8.0 / (4.0 * ORA_PI * h * h)"),
+    "kernel derivative sign": ("return -5.0 * wendland_alpha(dim, h) * q * t * t * t / h;",
+                               "return 5.0 * wendland_alpha(dim, h) * q * t * t * t / h;"),
+    "pressure force sign": ("a_p[d] += -2.0 / rho_i * Ps * gradW[d] * Vj;",
+                            "a_p[d] += 2.0 / rho_i * Ps * gradW[d] * Vj;"),
+    "neighbour stress dropped": ("? si.Pi[3 * a + b] + sj.Pi[3 * a + b] + pen",
+                                 "? si.Pi[3 * a + b] + si.Pi[3 * a + b] + pen"),
+    "colour weight of j": ("g[d] += 2.0 * phi_i * Cij * pp->dW[k] * pp->e[3 * k + d] * Vj;",
+                           "g[d] += 2.0 * (1.0 - phi_i) * Cij * pp->dW[k] * pp->e[3 * k + d] * Vj;"),
+    "arithmetic pair viscosity": ("? 2.0 * P->eta[ki] * P->eta[kj] / (P->eta[ki] + P->eta[kj])",
+                                  "? 0.5 * (P->eta[ki] + P->eta[kj])"),
+    "U* pressure difference reversed": ("return (zl * L.U + zr * R.U + L.p - R.p) / (zl + zr);",
+                                        "return (zl * L.U + zr * R.U - L.p + R.p) / (zl + zr);"),
+    "density update reversed": ("rho[i] += dt * drho[i];", "rho[i] -= dt * drho[i];"),
+}
+
+
+def run_pins_on(source: str, tmp_path):
+    mutant_src = tmp_path / "copy.c"
+    mutant_src.write_text(source)
+    lib = tmp_path / "libcopy.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                    str(mutant_src), "-o", str(lib), "-lm"], check=True)
+    env = dict(os.environ, SPH_ORACLE_LIB=str(lib))
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                           *[os.path.join(ROOT, "tests", f) for f in PINS]],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+
+
+def test_unmodified_copy_passes(tmp_path):
+    r = run_pins_on(open(SRC).read(), tmp_path)
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    good, bad = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(good) == 1, name
+    r = run_pins_on(src.replace(good, bad), tmp_path)
+    assert r.returncode != 0, f"no pin caught: {name}\n{r.stdout[-2000:]}"
