@@ -39,7 +39,7 @@ template <typename T> struct EngineT : Engine {
     // particle arrays
     V4<T> *pos = nullptr, *snap = nullptr, *vel = nullptr, *vel_new = nullptr;
     V4<T> *gradC = nullptr, *acc_visc = nullptr, *acc_surf = nullptr, *bmat = nullptr;
-    T *drho = nullptr, *drho_old = nullptr;
+    T *drho = nullptr, *drho_old = nullptr;        // drho_old: rebuild scratch (sorted copy)
     uint32_t *id = nullptr, *key = nullptr, *rank = nullptr, *perm = nullptr;
     // cell table + scan scratch
     uint32_t *starts = nullptr, *block_sums = nullptr;

@@ -3,14 +3,18 @@
 // Rebuild (once per advection step, Section 3.3): cell assignment with Morton
 // keys, a counting sort over the dense cell table (histogram by atomics,
 // exclusive scan, scatter), a per-cell sort by insertion index that makes the
-// order canonical, and a gather of the particle arrays.
+// order canonical, a gather of the particle arrays, the neighbour list of the
+// frozen configuration and the interface band.
 //
 // Pair sweeps (gather-only: every thread owns one particle and sums over its
 // neighbours, so there are no atomics on particle data):
 //   M  correction matrix B_i (Eq. 15)                     once per advection step
 //   V  viscous acceleration (Eq. 13) + transport shift (Eq. 14)  once per advection step
 //   A  colour gradient (Eq. 22)                           every acoustic substep
-//   B  pressure (Eqs. 7-12) + surface (Eqs. 24, 26, 33) + kick   every substep
+//   S  surface stress + penalty (Eqs. 24, 26, 30, 33) of the interface band
+//                                                         every substep (list cases)
+//   B  pressure (Eqs. 7-12) (+ the surface terms with the cell walk) + kick
+//                                                         every substep
 //   C  continuity (Eq. 6) + drift                         every substep
 // Time-step control (Eqs. 16-18) runs in FP64 in one-thread-per-case kernels.
 #pragma once
@@ -217,7 +221,7 @@ __device__ __forceinline__ uint32_t ld_list(const uint32_t *p) {
 __device__ __forceinline__ double bits_to_d(unsigned long long b) { return __longlong_as_double((long long)b); }
 
 // explicitly rounded operations for the pair geometry, so that the cell walk
-// and the neighbour list produce bitwise-identical r_ij and r^2
+// and the neighbour list produce bitwise-identical r_ij and r^2 for a pair
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
