@@ -44,6 +44,7 @@ template <typename T> struct EngineT : Engine {
     // cell table + scan scratch
     uint32_t *starts = nullptr, *block_sums = nullptr;
     uint32_t *nbr = nullptr, *nbr_cnt = nullptr;   // neighbour lists (ELL per case) and counts
+    V4<T> *lgeo = nullptr;                          // (e_ij, W'_ij) of each list entry (SPHST_LIST_GEO)
     uint8_t *band = nullptr;                        // interface band of the frozen configuration
     uint64_t *band_list = nullptr;                  // band particles per list class (case << 32 | index)
     uint32_t *band_count = nullptr;                 // entries of each class's band list
@@ -160,6 +161,7 @@ template <typename T> struct EngineT : Engine {
         size_t o_flag = take(64);
         size_t o_read = take((size_t)std::max<int64_t>(max_case_n, 1) * 3 * sizeof(double));
         size_t o_nbr = take((size_t)std::max<int64_t>(nbr_total, 1) * 4), o_ncnt = take(nn * 4);
+        size_t o_lgeo = take(SPHST_LIST_GEO ? (size_t)std::max<int64_t>(nbr_total, 1) * sizeof(V4<T>) : 0);
         size_t o_band = take(nn);
         size_t o_blist = take(nn * 8), o_bcount = take(64);
         size_t o_diag = take((size_t)(DIAG_BLOCKS + 1) * DIAG_Q * sizeof(double));
@@ -184,6 +186,7 @@ template <typename T> struct EngineT : Engine {
         d_read = (double *)(b + o_read);
         nbr = (uint32_t *)(b + o_nbr);
         nbr_cnt = (uint32_t *)(b + o_ncnt);
+        lgeo = SPHST_LIST_GEO ? (V4<T> *)(b + o_lgeo) : nullptr;
         band = (uint8_t *)(b + o_band);
         band_list = (uint64_t *)(b + o_blist);
         band_count = (uint32_t *)(b + o_bcount);
@@ -296,6 +299,7 @@ template <typename T> struct EngineT : Engine {
         k_gather<T><<<pgrid, nthr, 0, stream>>>(n, perm, pos, vel, drho, id, snap, vel_new, drho_old, rank);
         k_copy_back<T><<<pgrid, nthr, 0, stream>>>(n, snap, vel_new, drho_old, rank, pos, vel, drho, id);
         SPH_CLASSES(2, k_build_list, snap, nbr, nbr_cnt);
+        if (SPHST_LIST_GEO) SPH_CLASSES(2, k_list_geo, snap, lgeo);
         SPH_CK(cudaMemsetAsync(band_count, 0, 2 * sizeof(uint32_t), stream));
         SPH_CLASSES(2, k_band, snap, band, band_list + band_base[k_], band_count + k_);
         if (any_tvf) SPH_CLASSES(4, k_sweep_M, snap, drho, bmat);
@@ -306,10 +310,10 @@ template <typename T> struct EngineT : Engine {
 
     int launch_body(cudaGraphConditionalHandle h, int use_handle) {
         k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, h, use_handle);
-        SPH_CLASSES(4, k_sweep_A, snap, drho, gradC);
+        SPH_CLASSES(4, k_sweep_A, snap, drho, lgeo, gradC);
         SPH_CLASSES(2, k_sweep_S, band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
-        SPH_CLASSES(4, k_sweep_B, band, snap, vel, gradC, acc_visc, acc_surf, vel_new);
-        SPH_CLASSES(4, k_sweep_C, snap, vel_new, drho, vel, pos);
+        SPH_CLASSES(4, k_sweep_B, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo);
+        SPH_CLASSES(4, k_sweep_C, snap, vel_new, drho, vel, pos, lgeo);
         SPH_CK(cudaGetLastError());
         return SPHST_OK;
     }
@@ -426,8 +430,9 @@ template <typename T> struct EngineT : Engine {
             k_gather<T><<<pgrid, nthr, 0, stream>>>(n, perm, pos, vel, drho, id, snap, vel_new, drho_old, rank);
             k_copy_back<T><<<pgrid, nthr, 0, stream>>>(n, snap, vel_new, drho_old, rank, pos, vel, drho, id);
         });
-        timed(0, 2 * nlist, [&] {
+        timed(0, (SPHST_LIST_GEO ? 3 : 2) * nlist, [&] {
             SPH_CLASSES(2, k_build_list, snap, nbr, nbr_cnt);
+            if (SPHST_LIST_GEO) SPH_CLASSES(2, k_list_geo, snap, lgeo);
             cudaMemsetAsync(band_count, 0, 2 * sizeof(uint32_t), stream);
             SPH_CLASSES(2, k_band, snap, band, band_list + band_base[k_], band_count + k_);
         });
@@ -437,12 +442,12 @@ template <typename T> struct EngineT : Engine {
         });
         for (;;) {
             timed(2, 1, [&] { k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, 0, 0); });
-            timed(3, ncls, [&] { SPH_CLASSES(4, k_sweep_A, snap, drho, gradC); });
+            timed(3, ncls, [&] { SPH_CLASSES(4, k_sweep_A, snap, drho, lgeo, gradC); });
             timed(6, nlist, [&] {
                 SPH_CLASSES(2, k_sweep_S, band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
             });
-            timed(4, ncls, [&] { SPH_CLASSES(4, k_sweep_B, band, snap, vel, gradC, acc_visc, acc_surf, vel_new); });
-            timed(5, ncls, [&] { SPH_CLASSES(4, k_sweep_C, snap, vel_new, drho, vel, pos); });
+            timed(4, ncls, [&] { SPH_CLASSES(4, k_sweep_B, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo); });
+            timed(5, ncls, [&] { SPH_CLASSES(4, k_sweep_C, snap, vel_new, drho, vel, pos, lgeo); });
             if (rc) break;
             int flag = 0;
             cudaError_t e = cudaMemcpy(&flag, d_loop_flag, sizeof(int), cudaMemcpyDeviceToHost);

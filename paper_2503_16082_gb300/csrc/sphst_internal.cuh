@@ -14,6 +14,18 @@
 
 namespace sphst {
 
+// SPHST_LIST_GEO 1: with the neighbour list, the pair geometry of the frozen
+// configuration (unit vector e_ij and kernel derivative W'_ij) is computed
+// once per advection step and stored beside the list; the per-substep
+// sweeps A, B and C stream it instead of recomputing it from positions.
+// Measured on the 3D drop (1.19M particles): sweep B 0.36 -> 0.41-0.45 ms,
+// sweep C 0.30 -> 0.38-0.43 ms, rebuild +0.5 ms.  The 20 bytes per pair come
+// from HBM with its latency, the recomputation from positions that hit in
+// L1; off.
+#ifndef SPHST_LIST_GEO
+#define SPHST_LIST_GEO 0
+#endif
+
 // ------------------------------------------------------------------ vectors
 template <typename T> struct V4;
 template <> struct __align__(16) V4<float> { float x, y, z, w; };

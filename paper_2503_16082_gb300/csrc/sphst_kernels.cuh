@@ -38,6 +38,8 @@
 //                      unchanged, sweep C 40% slower; off)
 //   SPHST_PIPE         1: sweeps B and C load the next neighbour's position and
 //                      state while the current pair is evaluated
+//   SPHST_GEO_L2PF     >0: with SPHST_LIST_GEO, L2 prefetch of the stored
+//                      geometry that many entries ahead
 #ifndef SPHST_LIST_PREFETCH
 #define SPHST_LIST_PREFETCH 1
 #endif
@@ -58,6 +60,9 @@
 #endif
 #ifndef SPHST_SWEEP_MINB
 #define SPHST_SWEEP_MINB 0
+#endif
+#ifndef SPHST_GEO_L2PF
+#define SPHST_GEO_L2PF 0
 #endif
 #ifndef SPHST_LIST_UNROLL
 #define SPHST_LIST_UNROLL 1
@@ -466,6 +471,71 @@ __device__ __forceinline__ bool neighbors(const CaseDesc &d, const CasePhys<T> &
     } else {
         return walk<T, D>(d, cp, starts, snap, i, si, pki, f);
     }
+}
+
+// ---- stored pair geometry (SPHST_LIST_GEO): entry k of particle i holds
+// (e_ij, W'_ij) of the frozen configuration at the list's own position, so
+// it streams beside the list.  W' < 0 for every pair (0 < q < 2); an entry
+// whose neighbour is a wall particle stores -W' instead, so the sign bit
+// tells walls from fluid without reading the neighbour's packed phase.  The
+// other fluid phase's entries come first (cnt >> 16 of them), so the phase
+// of a fluid neighbour is known from k.
+__device__ __forceinline__ bool geo_wall(float w) { return (__float_as_uint(w) >> 31) == 0u; }
+__device__ __forceinline__ bool geo_wall(double w) { return __double_as_longlong(w) >= 0; }
+template <typename T> __device__ __forceinline__ V4<T> ld_geo(const V4<T> *p) { return *p; }
+template <> __device__ __forceinline__ V4<float> ld_geo<float>(const V4<float> *p) {
+#if SPHST_LIST_LDCS
+    const float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
+    return V4<float>{v.x, v.y, v.z, v.w};
+#else
+    return ld4(p);
+#endif
+}
+
+// f(other, j, G) for the list entries of i with their stored geometry G;
+// other: j belongs to the other fluid phase
+template <int PART, typename T, typename F>
+__device__ __forceinline__ void walk_geo(const CaseDesc &d, const uint32_t *__restrict__ nbr,
+                                         const uint32_t *__restrict__ cnt, const V4<T> *__restrict__ lgeo,
+                                         int64_t i, F &&f) {
+    const int64_t stride = d.p_end - d.p_begin;
+    const int64_t off = d.nbr_base + (i - d.p_begin);
+    const uint32_t *p = nbr + off;
+    const V4<T> *q = lgeo + off;
+    const uint32_t ci = cnt[i];
+    const uint32_t c_other = ci >> 16;
+    const uint32_t c = PART == PART_OTHER ? c_other : ci & CNT_MASK;
+#if SPHST_LIST_PREFETCH
+    uint32_t next = c ? ld_list(p) : 0u;
+#endif
+    V4<T> g1 = c ? ld_geo(q) : V4<T>{};
+#pragma unroll kListUnroll
+    for (uint32_t k = 0; k < c; ++k) {
+#if SPHST_LIST_PREFETCH
+        const uint32_t e = next;
+        p += stride;
+        if (k + 1 < c) next = ld_list(p);
+#else
+        const uint32_t e = ld_list(p);
+        p += stride;
+#endif
+#if SPHST_GEO_L2PF > 0
+        if (k + SPHST_GEO_L2PF < c) asm volatile("prefetch.global.L2 [%0];" ::"l"(q + SPHST_GEO_L2PF * stride));
+#endif
+        const V4<T> G = g1;                       // geometry one entry ahead
+        if (k + 1 < c) g1 = ld_geo(q + stride);
+        q += stride;
+        f(PART == PART_OTHER || k < c_other, e >> NBR_SHIFT, G);
+    }
+}
+
+// f(other, j, G, aux_j): walk_geo with the neighbour's aux word
+template <typename T, typename F>
+__device__ __forceinline__ void walk_geo_aux(const CaseDesc &d, const uint32_t *__restrict__ nbr,
+                                             const uint32_t *__restrict__ cnt, const V4<T> *__restrict__ lgeo,
+                                             const V4<T> *__restrict__ aux, int64_t i, F &&f) {
+    walk_geo<PART_ALL, T>(d, nbr, cnt, lgeo, i,
+                          [&](bool other, uint32_t j, const V4<T> &G) { f(other, j, G, ld4(aux + j)); });
 }
 
 // kernel radial derivative and unit vector of one pair
@@ -978,7 +1048,7 @@ __device__ __forceinline__ void sweep_V(const CaseDesc &d, const CasePhys<T> &cp
 template <bool LIST, typename T, int D>
 __device__ __forceinline__ void sweep_A(const CaseDesc &d, const CasePhys<T> &cp, int64_t i,
                                         const uint32_t *starts, const uint32_t *nbr, const uint32_t *cnt, const V4<T> *snap, const T *drho,
-                                        V4<T> *gradC) {
+                                        const V4<T> *lgeo, V4<T> *gradC) {
     const V4<T> si = ld4(snap + i);
     const uint32_t pki = w_bits(si.w);
     const uint32_t ki = phase_of(pki);
@@ -987,6 +1057,14 @@ __device__ __forceinline__ void sweep_A(const CaseDesc &d, const CasePhys<T> &cp
         const uint32_t other = ki ^ 1u;
         const T two_phi = cp.two_phi[ki];
         const T m_o = cp.mass[other], rho0_o = cp.rho0[other];
+        if constexpr (LIST && SPHST_LIST_GEO) {
+            walk_geo<PART_OTHER, T>(d, nbr, cnt, lgeo, i, [&](bool, uint32_t j, const V4<T> &G) {
+                const T s = two_phi * G.w * div_fast(m_o, rho0_o + drho[j]);
+                g.x += s * G.x;
+                g.y += s * G.y;
+                if (D == 3) g.z += s * G.z;
+            });
+        } else
         neighbors<LIST, T, D, PART_OTHER>(d, cp, starts, nbr, cnt, snap, i, si, pki,
             [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
                 if (!LIST && phase_of(w_bits(sj.w)) != other) return;
@@ -1019,7 +1097,7 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
                                           const uint8_t *band, const V4<T> *snap,
                                           const V4<T> *vel, const V4<T> *gradC,
                                           const V4<T> *acc_visc, V4<T> *acc_surf, V4<T> *vel_new,
-                                          uint32_t *phase_out) {
+                                          const V4<T> *lgeo, uint32_t *phase_out) {
     const V4<T> si = ld4(snap + i);
     const uint32_t pki = w_bits(si.w);
     const uint32_t ki = phase_of(pki);
@@ -1036,36 +1114,41 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
     const T rho0_0 = cp.rho0[0], rho0_1 = cp.rho0[1], m_0 = cp.mass[0], m_1 = cp.mass[1];
     const KernelGeo<T> kgeo(cp);
 
-    // pressure (Eqs. 7-12); walls by their mirror state
-    const auto pressure = [&](uint32_t, const V4<T> &sj, const V4<T> &vj, T rx, T ry, T rz, T r2) {
-        const PairGeo<T> g = kgeo(r2);
-        const L2<T> exy = mul2(l2(rx, ry), l2(g.inv_r, g.inv_r));
-        const T ex = exy.x, ey = exy.y, ez = D == 3 ? rz * g.inv_r : T(0);
-        const uint32_t kj = phase_of(w_bits(sj.w));
+    // pressure (Eqs. 7-12) of one pair from e_ij, W'_ij, the neighbour's
+    // kind (wall, or fluid of rest density rho0_j and mass m_j) and state
+    const auto pressure_pair = [&](L2<T> exy, T ez, T dW, bool wall, T rho0_j, T m_j, const V4<T> &vj) {
         // U_L - U_R = (v_j - v_i).e  (Eq. 10, U = -v.e)
         const L2<T> dvxy = fma2(l2(vi.x, vi.y), l2(T(-1), T(-1)), l2(vj.x, vj.y));
-        const T dUe = dvxy.x * ex + dvxy.y * ey + (D == 3 ? (vj.z - vi.z) * ez : T(0));
-        if (kj == PH_WALL) {
+        const T dUe = dvxy.x * exy.x + dvxy.y * exy.y + (D == 3 ? (vj.z - vi.z) * ez : T(0));
+        if (wall) {
             // mirror state behind a wall moving with v_w: rho_i, p_i, 2 U_w - U_L
             const T dU = T(2) * dUe;
             const T beta = limiter_beta(dU, p_i, rho_i);       // mirror state: rho_R, p_R = rho_i, p_i
             const T Ps = p_i + beta * rho_i * c0 * dU * T(0.5);
-            const T f = Ps * g.dW * vol_wall;
+            const T f = Ps * dW * vol_wall;
             const L2<T> a = fma2(l2(f, f), exy, l2(apx, apy));
             apx = a.x; apy = a.y; if (D == 3) apz += f * ez;
             return;
         }
         const T drj = vj.w;
-        const T rho_j = sel(kj, rho0_0, rho0_1) + drj;
+        const T rho_j = rho0_j + drj;
         const T p_j = c0sq * drj;
         const T dU = dUe;
         const T beta = limiter_beta(dU, p_i + p_j, rho_i + rho_j);   // Eq. 11
         // P* V_j with P* = (rho_i p_j + rho_j p_i + beta c0 rho_i rho_j dU) / (rho_i + rho_j)
         // (Eqs. 8, 12) and V_j = m_j / rho_j: one division
         const T num = (rho_i * p_j + rho_j * p_i) + beta * c0 * rho_i * rho_j * dU;
-        const T f = div_fast(num * sel(kj, m_0, m_1), (rho_i + rho_j) * rho_j) * g.dW;
+        const T f = div_fast(num * m_j, (rho_i + rho_j) * rho_j) * dW;
         const L2<T> a = fma2(l2(f, f), exy, l2(apx, apy));
         apx = a.x; apy = a.y; if (D == 3) apz += f * ez;
+    };
+    // walls by their mirror state
+    const auto pressure = [&](uint32_t, const V4<T> &sj, const V4<T> &vj, T rx, T ry, T rz, T r2) {
+        const PairGeo<T> g = kgeo(r2);
+        const L2<T> exy = mul2(l2(rx, ry), l2(g.inv_r, g.inv_r));
+        const uint32_t kj = phase_of(w_bits(sj.w));
+        pressure_pair(exy, D == 3 ? rz * g.inv_r : T(0), g.dW, kj == PH_WALL, sel(kj, rho0_0, rho0_1),
+                      sel(kj, m_0, m_1), vj);
     };
 
     // surface stress and penalty (Eqs. 24, 26, 30, 33); walls take no part
@@ -1138,6 +1221,15 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
         acc_surf[i] = V4<T>{asx, asy, asz, T(0)};
         return 0.0;
     } else if constexpr (PASS == 1) {
+        if constexpr (LIST && SPHST_LIST_GEO) {
+            const T rho0_o = sel(ki ^ 1u, rho0_0, rho0_1), rho0_s = sel(ki, rho0_0, rho0_1);
+            const T m_o = sel(ki ^ 1u, m_0, m_1), m_s = sel(ki, m_0, m_1);
+            walk_geo_aux<T>(d, nbr, cnt, lgeo, vel, i, [&](bool other, uint32_t, const V4<T> &G, const V4<T> &vj) {
+                const bool wall = geo_wall(G.w);
+                pressure_pair(l2(G.x, G.y), G.z, wall ? -G.w : G.w, wall, other ? rho0_o : rho0_s,
+                              other ? m_o : m_s, vj);
+            });
+        } else
         neighbors_aux<LIST, T, D>(d, cp, starts, nbr, cnt, snap, vel, i, si, pki, pressure);
         if (surface_on && band[i]) {
             const V4<T> as = acc_surf[i];
@@ -1166,7 +1258,7 @@ template <bool LIST, typename T, int D>
 __device__ __forceinline__ void sweep_C(const CaseDesc &d, const CasePhys<T> &cp, T dt, int64_t i,
                                         const uint32_t *starts, const uint32_t *nbr, const uint32_t *cnt, const V4<T> *snap,
                                         const V4<T> *vel_new, T *drho,
-                                        V4<T> *vel, V4<T> *pos) {
+                                        V4<T> *vel, V4<T> *pos, const V4<T> *lgeo) {
     const V4<T> si = ld4(snap + i);
     const uint32_t pki = w_bits(si.w);
     const uint32_t ki = phase_of(pki);
@@ -1183,25 +1275,38 @@ __device__ __forceinline__ void sweep_C(const CaseDesc &d, const CasePhys<T> &cp
     const T psign = d.vstar_printed ? T(-1) : T(1);
     const T sp_i = psign * p_i, sc0sq = psign * c0sq;
     T s = 0;
+    // one pair from (v_i - v_j).e = U_R - U_L, W'_ij, the neighbour's kind and
+    // its density deviation
+    const auto pair = [&](T dve, T dW, bool wall, T rho0_j, T m_j, T drj) {
+        if (wall) {                   // v* = v_w
+            s += dve * dW * vol_wall;
+            return;
+        }
+        const T rho_j = rho0_j + drj;
+        // (v_i - v*).e V_j with (v_i - v*).e = U* - U_L = (Z_R (U_R - U_L) + p_i - p_j)
+        // / (Z_L + Z_R) and V_j = m_j / rho_j: one division.  The printed v*
+        // gives (Z_R (U_R - U_L) - (p_i - p_j)) / (Z_L + Z_R) instead.
+        const T num = (rho_j * c0 * dve + (sp_i - sc0sq * drj)) * m_j;
+        s += div_fast(num, c0 * (rho_i + rho_j) * rho_j) * dW;
+    };
+    if constexpr (LIST && SPHST_LIST_GEO) {
+        const T rho0_o = sel(ki ^ 1u, rho0_0, rho0_1), rho0_s = sel(ki, rho0_0, rho0_1);
+        const T m_o = sel(ki ^ 1u, m_0, m_1), m_s = sel(ki, m_0, m_1);
+        walk_geo_aux<T>(d, nbr, cnt, lgeo, vel_new, i, [&](bool other, uint32_t, const V4<T> &G, const V4<T> &vj) {
+            const L2<T> dvxy = fma2(l2(vj.x, vj.y), l2(T(-1), T(-1)), l2(vi.x, vi.y));
+            const T dve = dvxy.x * G.x + dvxy.y * G.y + (D == 3 ? (vi.z - vj.z) * G.z : T(0));
+            const bool wall = geo_wall(G.w);
+            pair(dve, wall ? -G.w : G.w, wall, other ? rho0_o : rho0_s, other ? m_o : m_s, vj.w);
+        });
+    } else
     neighbors_aux<LIST, T, D>(d, cp, starts, nbr, cnt, snap, vel_new, i, si, pki,
         [&](uint32_t, const V4<T> &sj, const V4<T> &vj, T rx, T ry, T rz, T r2) {
             const PairGeo<T> g = kgeo(r2);
             const uint32_t kj = phase_of(w_bits(sj.w));
             const L2<T> dvxy = fma2(l2(vj.x, vj.y), l2(T(-1), T(-1)), l2(vi.x, vi.y));
             const T dvx = dvxy.x, dvy = dvxy.y, dvz = D == 3 ? vi.z - vj.z : T(0);
-            // (v_i - v_j).e = U_R - U_L
-            const T dve = (dvx * rx + dvy * ry + dvz * rz) * g.inv_r;
-            if (kj == PH_WALL) {          // v* = v_w
-                s += dve * g.dW * vol_wall;
-                return;
-            }
-            const T drj = vj.w;
-            const T rho_j = sel(kj, rho0_0, rho0_1) + drj;
-            // (v_i - v*).e V_j with (v_i - v*).e = U* - U_L = (Z_R (U_R - U_L) + p_i - p_j)
-            // / (Z_L + Z_R) and V_j = m_j / rho_j: one division.  The printed v*
-            // gives (Z_R (U_R - U_L) - (p_i - p_j)) / (Z_L + Z_R) instead.
-            const T num = (rho_j * c0 * dve + (sp_i - sc0sq * drj)) * sel(kj, m_0, m_1);
-            s += div_fast(num, c0 * (rho_i + rho_j) * rho_j) * g.dW;
+            pair((dvx * rx + dvy * ry + dvz * rz) * g.inv_r, g.dW, kj == PH_WALL, sel(kj, rho0_0, rho0_1),
+                 sel(kj, m_0, m_1), vj.w);
         });
     const T dr_new = dri + dt * (T(2) * rho_i * s);
     drho[i] = dr_new;
@@ -1338,6 +1443,40 @@ __global__ void __launch_bounds__(256) k_build_list(SweepArgs a, const V4<T> *sn
     build_list<T, D>(d, phys<T>(d), i, a.starts, snap, nbr, cnt, &a.st[t.c].status);
 }
 
+// ---- G: the stored pair geometry of the list (SPHST_LIST_GEO), once per
+// advection step after the list build.  e_ij and W'_ij are formed by the
+// same operations as in the list walk, so the sweeps that read them see the
+// values they would have computed.
+template <typename T, int D, bool LIST>
+__global__ void __launch_bounds__(256) k_list_geo(SweepArgs a, const V4<T> *snap, V4<T> *lgeo) {
+    const Tile t = a.tiles[a.tile0 + blockIdx.x];
+    if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
+    const CaseDesc &d = a.desc[t.c];
+    const CasePhys<T> &cp = phys<T>(d);
+    const int64_t i = t.begin + threadIdx.x;
+    const V4<T> si = ld4(snap + i);
+    if (phase_of(w_bits(si.w)) == PH_WALL) return;
+    const int64_t stride = d.p_end - d.p_begin;
+    const int64_t off = d.nbr_base + (i - d.p_begin);
+    const uint32_t *p = a.nbr + off;
+    V4<T> *q = lgeo + off;
+    const uint32_t c = a.cnt[i] & CNT_MASK;
+    const T cs = cp.cs;
+    const KernelGeo<T> kgeo(cp);
+    for (uint32_t k = 0; k < c; ++k, p += stride, q += stride) {
+        const uint32_t e = ld_list(p);
+        const V4<T> sj = ld4(snap + (e >> NBR_SHIFT));
+        const L2<T> tt = fma2(neg_code_off2(e & 3u, (e >> 2) & 3u, T()), l2(cs, cs), l2(si.x, si.y));
+        const L2<T> rxy = fma2(l2(sj.x, sj.y), l2(T(-1), T(-1)), tt);
+        T rz = T(0);
+        if (D == 3) rz = sub_rn(fma_rn(-code_off((e >> 4) & 3u, T()), cs, si.z), sj.z);
+        const PairGeo<T> g = kgeo(norm2<T, D>(rxy.x, rxy.y, rz));
+        const L2<T> exy = mul2(rxy, l2(g.inv_r, g.inv_r));
+        const bool wall = phase_of(w_bits(sj.w)) == PH_WALL;
+        *q = V4<T>{exy.x, exy.y, D == 3 ? rz * g.inv_r : T(0), wall ? -g.dW : g.dW};
+    }
+}
+
 template <typename T, int D, bool LIST>
 __global__ void SPH_SWEEP_BOUNDS k_sweep_M(SweepArgs a, const V4<T> *snap, const T *drho, V4<T> *bmat) {
     const Tile t = a.tiles[a.tile0 + blockIdx.x];
@@ -1360,12 +1499,13 @@ __global__ void SPH_SWEEP_BOUNDS k_sweep_V(SweepArgs a, const V4<T> *snap, const
 }
 
 template <typename T, int D, bool LIST>
-__global__ void SPH_SWEEP_BOUNDS k_sweep_A(SweepArgs a, const V4<T> *snap, const T *drho, V4<T> *gradC) {
+__global__ void SPH_SWEEP_BOUNDS k_sweep_A(SweepArgs a, const V4<T> *snap, const T *drho, const V4<T> *lgeo,
+                                           V4<T> *gradC) {
     const Tile t = a.tiles[a.tile0 + blockIdx.x];
     if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
     const CaseDesc &d = a.desc[t.c];
     const int64_t i = t.begin + threadIdx.x;
-    sweep_A<LIST, T, D>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, gradC);
+    sweep_A<LIST, T, D>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, lgeo, gradC);
 }
 
 // surface sum of the band particles (list classes only), before B: one
@@ -1384,13 +1524,13 @@ __global__ void SPH_SWEEP_BOUNDS k_sweep_S(SweepArgs a, const uint64_t *blist, c
     const CaseDesc &d = a.desc[c];
     uint32_t ph;
     sweep_B<LIST, 2, T, D>(d, phys<T>(d), T(0), i, a.starts, a.nbr, a.cnt, band, snap, vel, gradC, nullptr,
-                           acc_surf, nullptr, &ph);
+                           acc_surf, nullptr, nullptr, &ph);
 }
 
 template <typename T, int D, bool LIST>
 __global__ void SPH_SWEEPB_BOUNDS k_sweep_B(SweepArgs a, const uint8_t *band, const V4<T> *snap, const V4<T> *vel,
                                             const V4<T> *gradC, const V4<T> *acc_visc, V4<T> *acc_surf,
-                                            V4<T> *vel_new) {
+                                            V4<T> *vel_new, const V4<T> *lgeo) {
     const Tile t = a.tiles[a.tile0 + blockIdx.x];
     if (!a.st[t.c].active) return;                 // uniform per block
     const CaseDesc &d = a.desc[t.c];
@@ -1400,7 +1540,7 @@ __global__ void SPH_SWEEPB_BOUNDS k_sweep_B(SweepArgs a, const uint8_t *band, co
         const int64_t i = t.begin + threadIdx.x;
         const T dt = (T)a.st[t.c].dt;
         v2 = sweep_B<LIST, LIST ? 1 : 0, T, D>(d, phys<T>(d), dt, i, a.starts, a.nbr, a.cnt, band, snap, vel,
-                                               gradC, acc_visc, acc_surf, vel_new, &ph);
+                                               gradC, acc_visc, acc_surf, vel_new, lgeo, &ph);
     }
     unsigned long long m0 = ph == 0 ? (unsigned long long)__double_as_longlong(v2) : 0ull;
     unsigned long long m1 = ph == 1 ? (unsigned long long)__double_as_longlong(v2) : 0ull;
@@ -1414,13 +1554,13 @@ __global__ void SPH_SWEEPB_BOUNDS k_sweep_B(SweepArgs a, const uint8_t *band, co
 
 template <typename T, int D, bool LIST>
 __global__ void SPH_SWEEP_BOUNDS k_sweep_C(SweepArgs a, const V4<T> *snap, const V4<T> *vel_new, T *drho,
-                                           V4<T> *vel, V4<T> *pos) {
+                                           V4<T> *vel, V4<T> *pos, const V4<T> *lgeo) {
     const Tile t = a.tiles[a.tile0 + blockIdx.x];
     if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
     const CaseDesc &d = a.desc[t.c];
     const int64_t i = t.begin + threadIdx.x;
     const T dt = (T)a.st[t.c].dt;
-    sweep_C<LIST, T, D>(d, phys<T>(d), dt, i, a.starts, a.nbr, a.cnt, snap, vel_new, drho, vel, pos);
+    sweep_C<LIST, T, D>(d, phys<T>(d), dt, i, a.starts, a.nbr, a.cnt, snap, vel_new, drho, vel, pos, lgeo);
 }
 
 // ---------------------------------------------------------- diagnostics

@@ -237,7 +237,8 @@ def test_profiled_launch_counts():
     S.destroy(h)
     for g in ("criterion", "sweep_A", "sweep_S", "sweep_B", "sweep_C"):
         assert prof[g][1] == n_sub, g
-    assert prof["rebuild"][1] == 10          # keys, 3 scans, scatter, cell sort, gather, copy-back, list, band
+    # keys, 3 scans, scatter, cell sort, gather, copy-back, list, band
+    assert prof["rebuild"][1] == 10
 
 
 @pytest.mark.parametrize("dim", [2, 3])
