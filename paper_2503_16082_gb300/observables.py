@@ -8,6 +8,12 @@
   drop's centroid), mean spacing of same-direction crossings, linearly
   interpolated.
 * Total momentum of the fluids.
+* Interface disorder: the share of fluid particles whose fluid neighbours
+  (r < 2h) belong mostly to the other fluid.  On a sharp interface every
+  particle has at most about half of its neighbours across it; particles
+  that have crossed into the other fluid, or interface particles arranged in
+  a zero-surface-energy pattern (Section 4: the surface stress alone exerts
+  no force on them), have more.
 """
 from __future__ import annotations
 
@@ -108,6 +114,28 @@ def period_from_signal(t: Sequence[float], s: Sequence[float]) -> float:
     return float(np.mean(np.diff(ups)))
 
 
+def stray_fraction(pos, phase, h: float, fluid_phases=(0, 1)) -> float:
+    """Share of fluid particles with more than half of their fluid
+    neighbours (0 < r < 2h) from the other fluid phase."""
+    from scipy.spatial import cKDTree
+
+    fl = np.isin(phase, fluid_phases)
+    q = np.asarray(pos)[fl]
+    ph = np.asarray(phase)[fl]
+    if len(q) == 0:
+        return 0.0
+    pairs = cKDTree(q).query_pairs(2.0 * h, output_type="ndarray")
+    if len(pairs) == 0:
+        return 0.0
+    n_all = np.zeros(len(q))
+    n_other = np.zeros(len(q))
+    cross = (ph[pairs[:, 0]] != ph[pairs[:, 1]]).astype(float)
+    for c in (0, 1):
+        np.add.at(n_all, pairs[:, c], 1.0)
+        np.add.at(n_other, pairs[:, c], cross)
+    return float(np.mean(n_other > 0.5 * np.maximum(n_all, 1.0)))
+
+
 def momentum(vel, mass) -> np.ndarray:
     return (np.asarray(mass)[:, None] * vel).sum(axis=0)
 
@@ -125,19 +153,30 @@ def period_lamb_3d(R: float, rho_in: float, rho_out: float, gamma: float) -> flo
 def fit_period(t: Sequence[float], s: Sequence[float], guess: float, skip: float = 0.05) -> float:
     """Period of s(t) ~ c + exp(-l t) (a cos w t + b sin w t), fitted by a grid
     search over (w, l) around 2 pi / guess with linear least squares for
-    (a, b, c); the first `skip` fraction of the record is ignored."""
+    (a, b, c), then refined by a simplex search from the best grid point;
+    the first `skip` fraction of the record is ignored."""
+    from scipy.optimize import minimize
+
     t = np.asarray(t, dtype=float)
     s = np.asarray(s, dtype=float)
     keep = t >= t[0] + skip * (t[-1] - t[0])
     t, s = t[keep], s[keep]
     w0 = 2.0 * math.pi / guess
-    best = (np.inf, float("nan"))
+
+    def resid(x):
+        w, lam = x
+        e = np.exp(-lam * (t - t[0]))
+        A = np.stack([np.ones_like(t), e * np.cos(w * t), e * np.sin(w * t)], axis=1)
+        coef, *_ = np.linalg.lstsq(A, s, rcond=None)
+        return float(((A @ coef - s) ** 2).sum())
+
+    best = (np.inf, (w0, 0.0))
     for w in np.linspace(0.3 * w0, 3.0 * w0, 541):
         for lam in np.linspace(0.0, 2.0 * w0, 21):
-            e = np.exp(-lam * (t - t[0]))
-            A = np.stack([np.ones_like(t), e * np.cos(w * t), e * np.sin(w * t)], axis=1)
-            coef, res, *_ = np.linalg.lstsq(A, s, rcond=None)
-            r = float(((A @ coef - s) ** 2).sum())
+            r = resid((w, lam))
             if r < best[0]:
-                best = (r, 2.0 * math.pi / w)
-    return best[1]
+                best = (r, (w, lam))
+    x = minimize(resid, np.array(best[1]), method="Nelder-Mead",
+                 options={"xatol": 1e-7 * w0, "fatol": 1e-14 * max(best[0], 1e-300), "maxiter": 400}).x
+    w = x[0] if resid(x) <= best[0] else best[1][0]
+    return 2.0 * math.pi / w

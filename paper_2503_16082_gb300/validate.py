@@ -3,7 +3,7 @@
   python -m paper_2503_16082_gb300.validate laplace_2d [--precision 64] [--adv 500]
   python -m paper_2503_16082_gb300.validate oscillating_3d [--periods 1.5]
   python -m paper_2503_16082_gb300.validate impact_3d [--t-end 2]
-  python -m paper_2503_16082_gb300.validate oscillating_2d [--ratio 1000]
+  python -m paper_2503_16082_gb300.validate oscillating_2d [--ratio 1000] [--r-over-dp 12] [--xi 0]
   python -m paper_2503_16082_gb300.validate shear_drop [--ca 0.1] [--t-end 20]
   python -m paper_2503_16082_gb300.validate impact_sweep [--res 20] [--u0 0.5 1 5 10 50]
 
@@ -11,6 +11,9 @@ Each prints one JSON line.  laplace_2d: Young-Laplace jump (Eq. 37)
 averaged over the last 20% of the run, against gamma / R_eff.  oscillating_*:
 period of the drop's shape anisotropy against Eq. 35 (2D, ratio >> 1), the
 equal-density textbook value (2D, ratio 1) or Lamb's n = 2 value (3D).
+The 2D drop also reports the interface disorder (share of fluid particles
+whose neighbours belong mostly to the other fluid) at the end of the run and
+its maximum over the run; --xi 0 switches the penalty of Eqs. 29-33 off.
 impact_3d: whether the run stays finite to t_end, with its substep count.
 impact_sweep: Section 5.4's impact in the paper's units for each U0 (Re up to
 1e4, We up to 2.5e4): whether the run stays finite to the paper's end time,
@@ -71,11 +74,14 @@ def oscillating(args, dim):
         R, rho_in, rho_out = 0.5, 1000.0, 1.0
         tau = ob.period_lamb_3d(R, rho_in, rho_out, case.gamma)
     else:
-        case = sphcases.oscillating_2d(ratio=args.ratio)
+        case = sphcases.oscillating_2d(ratio=args.ratio, R_over_dp=args.r_over_dp)
         tau = ob.period_2d_drop(0.2, 1.0, 1.0) * (math.sqrt(2.0) if args.ratio == 1 else 1.0)
+    if args.xi is not None:
+        case.xi = args.xi
     h = S.case_from_spec(case, precision=args.precision)
     phase = S.read_fields(h, S.FIELD_PHASE, dim)
-    ts, an = [], []
+    hk = case.h_factor * case.dx
+    ts, an, stray = [], [], []
     t0 = time.perf_counter()
     t_end = args.periods * tau
     info = S.case_info(h)
@@ -84,8 +90,13 @@ def oscillating(args, dim):
         if info["rc"]:
             break
         ts.append(info["t"])
-        an.append(ob.anisotropy(S.read_fields(h, S.FIELD_POS, dim), phase))
+        pos = S.read_fields(h, S.FIELD_POS, dim)
+        an.append(ob.anisotropy(pos, phase))
+        if dim == 2 and len(ts) % 10 == 1:
+            stray.append(ob.stray_fraction(pos, phase, hk))
     wall = time.perf_counter() - t0
+    if dim == 2:
+        stray.append(ob.stray_fraction(S.read_fields(h, S.FIELD_POS, dim), phase, hk))
     S.destroy(h)
     s = np.array(an) - np.mean(an)
     cr = [ts[k - 1] + (ts[k] - ts[k - 1]) * (-s[k - 1]) / (s[k] - s[k - 1])
@@ -95,7 +106,10 @@ def oscillating(args, dim):
             "adv": info["n_adv"], "substeps": info["n_sub"], "t": info["t"], "status": info["status"],
             "zero_crossings": [round(c, 4) for c in cr], "period": period, "theory": tau,
             "rel_error": (period - tau) / tau if period == period else None,
-            "anisotropy_amplitude": float(np.abs(s).max()) if len(s) else None, "wall_s": round(wall, 2)}
+            "anisotropy_amplitude": float(np.abs(s).max()) if len(s) else None,
+            **({"R_over_dp": args.r_over_dp, "xi": case.xi, "stray_end": stray[-1], "stray_max": max(stray)}
+               if dim == 2 else {}),
+            "wall_s": round(wall, 2)}
 
 
 def impact(args):
@@ -187,6 +201,8 @@ def main(argv=None):
     ap.add_argument("--periods", type=float, default=1.5)
     ap.add_argument("--every", type=int, default=5)
     ap.add_argument("--ratio", type=float, default=1000.0)
+    ap.add_argument("--r-over-dp", type=int, default=12, help="oscillating_2d: R / dp")
+    ap.add_argument("--xi", type=float, default=None, help="penalty coefficient (default: from the density ratio)")
     ap.add_argument("--t-end", type=float, default=None, help="impact_3d: 2.0, shear_drop: 20.0")
     args = ap.parse_args(argv)
     if args.t_end is None:
