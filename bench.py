@@ -94,16 +94,31 @@ class ClockSampler:
     def __init__(self, gpu: int):
         self.gpu = gpu
         self.proc = None
+        self.first = 0
         self.path = tempfile.mktemp(suffix=".csv")
 
+    def _lines(self) -> int:
+        try:
+            with open(self.path) as f:
+                return sum(1 for _ in f)
+        except OSError:
+            return 0
+
     def start(self):
+        """Start sampling every 100 ms; returns once the first sample is in,
+        and marks the samples before the timed region as not under load."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.time()
+        while self._lines() == 0 and time.time() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.02)
+        self.first = self._lines()
 
     def stop(self):
         if not self.proc:
@@ -114,9 +129,9 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         rows = []
-        for line in open(self.path):
+        for k, line in enumerate(open(self.path)):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
+            if k >= self.first and len(parts) >= 9:
                 rows.append(parts)
         os.unlink(self.path)
         if not rows:
@@ -464,7 +479,7 @@ def run_serve(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="oscillating_3d")
