@@ -28,6 +28,10 @@
 //   SPHST_SWEEP_MINB   >0: minimum resident 256-thread blocks per SM for the
 //                      sweeps (caps registers per thread)
 //   SPHST_SWEEPB_MINB  the same for sweep B alone (default 4: 64 registers)
+//   SPHST_SWEEPAS_MINB the same for sweeps A and S (default 4: with the
+//                      64-register room the compiler keeps more loads in
+//                      flight; measured: A 35 -> 28 us, S 93 -> 89 us on the
+//                      3D drop)
 //   SPHST_LIST_UNROLL  unroll factor of the neighbour-list loop
 //   SPHST_LIST_PREFETCH 1: load list entry k+1 while pair k is evaluated
 //   SPHST_FAST_DIV     1: FP32 pair divisions through the SFU reciprocal
@@ -61,6 +65,9 @@
 #ifndef SPHST_SWEEP_MINB
 #define SPHST_SWEEP_MINB 0
 #endif
+#ifndef SPHST_SWEEPAS_MINB
+#define SPHST_SWEEPAS_MINB 4
+#endif
 #ifndef SPHST_GEO_L2PF
 #define SPHST_GEO_L2PF 0
 #endif
@@ -78,6 +85,11 @@
 // sweep B is latency-bound on neighbour gathers: capping it at 64 registers
 // (4 blocks of 256 per SM) doubles its resident warps (measured 1.38 -> 0.96
 // ms on 1.19M particles); the lighter sweeps A and C are faster uncapped
+#if SPHST_SWEEPAS_MINB > 0
+#define SPH_SWEEPAS_BOUNDS __launch_bounds__(256, SPHST_SWEEPAS_MINB)
+#else
+#define SPH_SWEEPAS_BOUNDS __launch_bounds__(256)
+#endif
 #if SPHST_SWEEPB_MINB > 0
 #define SPH_SWEEPB_BOUNDS __launch_bounds__(256, SPHST_SWEEPB_MINB)
 #else
@@ -1499,7 +1511,7 @@ __global__ void SPH_SWEEP_BOUNDS k_sweep_V(SweepArgs a, const V4<T> *snap, const
 }
 
 template <typename T, int D, bool LIST>
-__global__ void SPH_SWEEP_BOUNDS k_sweep_A(SweepArgs a, const V4<T> *snap, const T *drho, const V4<T> *lgeo,
+__global__ void SPH_SWEEPAS_BOUNDS k_sweep_A(SweepArgs a, const V4<T> *snap, const T *drho, const V4<T> *lgeo,
                                            V4<T> *gradC) {
     const Tile t = a.tiles[a.tile0 + blockIdx.x];
     if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
@@ -1512,7 +1524,7 @@ __global__ void SPH_SWEEP_BOUNDS k_sweep_A(SweepArgs a, const V4<T> *snap, const
 // thread per entry of the class's compacted band list, so warps are full of
 // band particles; threads past the list's length exit at once
 template <typename T, int D, bool LIST>
-__global__ void SPH_SWEEP_BOUNDS k_sweep_S(SweepArgs a, const uint64_t *blist, const uint32_t *bcount,
+__global__ void SPH_SWEEPAS_BOUNDS k_sweep_S(SweepArgs a, const uint64_t *blist, const uint32_t *bcount,
                                            const uint8_t *band, const V4<T> *snap, const V4<T> *vel,
                                            const V4<T> *gradC, V4<T> *acc_surf) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
