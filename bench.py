@@ -210,6 +210,8 @@ def run_ours(args, dist: Dist):
 
     nbr_mode = S.NBR_CELLS if args.nbr == "cells" else S.NBR_LIST
     extra = {"block": args.block} if args.block else {}
+    if args.lanes:
+        extra["lanes"] = args.lanes
     h = S.case_from_spec(spec, precision=args.precision, nbr_mode=nbr_mode, **extra)
     S.set_stream(h, stream.cuda_stream)
     S.step(h, args.warmup)                       # engine set-up, graph capture, warm-up
@@ -489,6 +491,8 @@ def main():
     ap.add_argument("--nbr", default="list", choices=["list", "cells"],
                     help="neighbour source of the sweeps (list built per advection step, or cell walk)")
     ap.add_argument("--block", type=int, default=0, help="particles per tile / threads per block (0: library default)")
+    ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="lanes per particle in sweeps A, B, C with the list (0: library default, 1)")
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"],
                     help="single: the headline line; batch / serve: the batched and served workloads")
     ap.add_argument("--cases", type=int, default=512)
@@ -512,7 +516,8 @@ def main():
     config = {"workload": args.workload, "particles": None, "fluid_particles": None,
               "step": "one advection step (rebuild + all acoustic substeps)",
               "l2": "inputs larger than L2 (~170 MB FP32 working set vs 129 MB L2)",
-              "parallelism": f"replicas x{max(ws, 1)}", "neighbours": args.nbr}
+              "parallelism": f"replicas x{max(ws, 1)}", "neighbours": args.nbr,
+              "block": args.block or 128, "lanes": args.lanes or 1}
     dtype = "f32" if args.precision == 32 else "f64"
 
     if args.impl == "reference":

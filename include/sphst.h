@@ -118,7 +118,8 @@ typedef struct {
     int32_t penalty_form;   /* SPHST_PENALTY_*                                 */
     int32_t loop_mode;      /* SPHST_LOOP_*                                    */
     int32_t grid_pad;       /* spare cells around the initial bounding box (>= 1) */
-    int32_t block;          /* threads per block of the pair sweeps, 32..1024  */
+    int32_t block;          /* threads per block of the pair sweeps: a multiple
+                               of 32 in 32..256                                */
     int64_t max_substeps;   /* per advection step before SPHST_ERR_STALLED     */
     double  cfl_ad;         /* factor of the advection criterion, Eq. 16 (0.1) */
     double  cfl_ac;         /* factor of the acoustic criterion, Eq. 17 (0.6);
@@ -137,6 +138,15 @@ typedef struct {
     int32_t vstar_form;     /* SPHST_VSTAR_* (continuity, Eq. 6)               */
     double  period_lo[3];
     double  period_hi[3];
+    int32_t lanes;          /* lanes per particle in the per-substep sweeps
+                               with the neighbour list: 1, 2 or 4.  With L > 1
+                               the L lanes of a particle split its list and
+                               add their partial sums (fixed order, so runs
+                               repeat bit for bit; results differ from L = 1
+                               by the rounding of the reordered sum).  More
+                               lanes spread small cases over more of the GPU.
+                               Speed only; a batch uses its first case's     */
+    int32_t pad2_;
 } sphst_case_params;
 
 typedef struct {
@@ -159,7 +169,7 @@ typedef struct {
 
 /* Fill *p with the defaults: dim 2, precision 32, h_factor 1.3, c0 10,
  * gamma 1, xi -1 (derived), tvf_alpha 0.2, readings 0, graph loop,
- * grid_pad 2, block 128, max_substeps 1000000, cfl_ad 0.1, cfl_ac 0.6,
+ * grid_pad 2, block 128, lanes 1, max_substeps 1000000, cfl_ad 0.1, cfl_ac 0.6,
  * neighbour lists with the default capacity; dx must still be set. */
 void sphst_default_params(sphst_case_params *p);
 
@@ -337,6 +347,11 @@ int sphst_fma_peak(int32_t precision, double *tflops, double *kernel_ms);
  * scratch), for admission control.  Errors: INVALID_ARG. */
 int sphst_footprint_bytes(const sphst_case_params *params, int64_t n_particles,
                           int64_t *bytes_out);
+
+/* sizeof of the three structures of this header as the library was built,
+ * so a binding can check its layout before the first call.  Any pointer may
+ * be NULL.  Never fails. */
+int sphst_struct_sizes(int64_t *params_bytes, int64_t *phase_props_bytes, int64_t *step_info_bytes);
 
 #ifdef __cplusplus
 }

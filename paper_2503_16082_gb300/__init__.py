@@ -42,7 +42,8 @@ class CaseParams(C.Structure):
                 ("cfl_ad", C.c_double), ("cfl_ac", C.c_double),
                 ("nbr_mode", C.c_int32), ("max_neighbors", C.c_int32),
                 ("periodic", C.c_int32), ("vstar_form", C.c_int32),
-                ("period_lo", C.c_double * 3), ("period_hi", C.c_double * 3)]
+                ("period_lo", C.c_double * 3), ("period_hi", C.c_double * 3),
+                ("lanes", C.c_int32), ("pad2_", C.c_int32)]
 
 
 class PhaseProps(C.Structure):
@@ -107,6 +108,7 @@ EXPORTS = {
     "sphst_footprint_bytes": (C.c_int, [C.POINTER(CaseParams), C.c_int64, C.POINTER(C.c_int64)]),
     "sphst_diagnose": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.POINTER(Diagnostics)]),
     "sphst_fma_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "sphst_struct_sizes": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
 }
 
 _lib = None
@@ -128,6 +130,12 @@ def load():
                 fn = getattr(lib, name)
                 fn.restype = res
                 fn.argtypes = args
+            sizes = [C.c_int64() for _ in range(3)]
+            lib.sphst_struct_sizes(*[C.byref(v) for v in sizes])
+            want = [C.sizeof(CaseParams), C.sizeof(PhaseProps), C.sizeof(StepInfo)]
+            if [v.value for v in sizes] != want:
+                raise RuntimeError(f"libsphst structure sizes {[v.value for v in sizes]} differ from the "
+                                   f"binding's {want}: rebuild the library")
             _lib = lib
     return _lib
 

@@ -266,6 +266,7 @@ void sphst_default_params(sphst_case_params *p) {
     p->loop_mode = SPHST_LOOP_GRAPH;
     p->grid_pad = 2;
     p->block = 128;
+    p->lanes = 1;
     p->max_substeps = 1000000;
     p->cfl_ad = 0.1;
     p->cfl_ac = 0.6;
@@ -295,8 +296,9 @@ int sphst_create_case(const sphst_case_params *params, sphst_case *out) {
         set_error("nbr_mode must be 0 or 1 and max_neighbors 0..1024");
         return SPHST_ERR_INVALID_ARG;
     }
-    if (P.grid_pad < 1 || P.grid_pad > 64 || P.block < 32 || P.block > 256 || P.block % 32) {
-        set_error("grid_pad must be 1..64 and block a multiple of 32 in 32..256");
+    if (P.grid_pad < 1 || P.grid_pad > 64 || P.block < 32 || P.block > 256 || P.block % 32 ||
+        (P.lanes != 1 && P.lanes != 2 && P.lanes != 4)) {
+        set_error("grid_pad must be 1..64, block a multiple of 32 in 32..256 and lanes 1, 2 or 4");
         return SPHST_ERR_INVALID_ARG;
     }
     if (P.periodic < 0 || P.periodic >= (1 << P.dim)) {
@@ -561,6 +563,13 @@ int sphst_debug_neighbor_counts(sphst_case c, int32_t *counts, int64_t capacity)
     if (!c->r.engine) { set_error("case not stepped yet"); return SPHST_ERR_STATE; }
     if (capacity < c->r.n) { set_error("destination buffer too small"); return SPHST_ERR_CAPACITY; }
     return c->r.engine->debug_counts(c->r.slot, counts);
+}
+
+int sphst_struct_sizes(int64_t *params_bytes, int64_t *phase_props_bytes, int64_t *step_info_bytes) {
+    if (params_bytes) *params_bytes = (int64_t)sizeof(sphst_case_params);
+    if (phase_props_bytes) *phase_props_bytes = (int64_t)sizeof(sphst_phase_props);
+    if (step_info_bytes) *step_info_bytes = (int64_t)sizeof(sphst_step_info);
+    return SPHST_OK;
 }
 
 int sphst_footprint_bytes(const sphst_case_params *params, int64_t n, int64_t *bytes_out) {

@@ -35,6 +35,27 @@ enum ArrayId { A_POS = 0, A_VEL, A_DRHO, A_ID, A_GRADC, A_ACCV };
         }                                                                              \
     }
 
+// SPH_CLASSES_L: the same for sweeps A, B and C, whose list classes run with
+// `lanes` lanes per particle (L blocks per tile).
+#define SPH_LANES(KERN, D, ...)                                                                   \
+    switch (lanes) {                                                                              \
+    case 2: KERN<T, D, true, 2><<<g_ * 2, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
+    case 4: KERN<T, D, true, 4><<<g_ * 4, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
+    default: KERN<T, D, true, 1><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;               \
+    }
+#define SPH_CLASSES_L(NCLS, KERN, ...)                                                 \
+    for (int k_ = 0; k_ < (NCLS); ++k_) {                                              \
+        if (!cls_n[k_]) continue;                                                      \
+        const SweepArgs a_ = sweep_args(k_);                                           \
+        const unsigned g_ = (unsigned)cls_n[k_];                                       \
+        switch (k_) {                                                                  \
+        case 0: SPH_LANES(KERN, 3, __VA_ARGS__) break;                                 \
+        case 1: SPH_LANES(KERN, 2, __VA_ARGS__) break;                                 \
+        case 2: KERN<T, 3, false><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;   \
+        default: KERN<T, 2, false><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;  \
+        }                                                                              \
+    }
+
 template <typename T> struct EngineT : Engine {
     // particle arrays
     V4<T> *pos = nullptr, *snap = nullptr, *vel = nullptr, *vel_new = nullptr;
@@ -61,7 +82,7 @@ template <typename T> struct EngineT : Engine {
     void *arena = nullptr;
     int64_t n = 0, table_total = 0, n_tiles = 0, max_case_n = 0;
     int64_t cls_b[4] = {0, 0, 0, 0}, cls_n[4] = {0, 0, 0, 0};   // tile range of each class
-    int ncases = 0, block = 128;
+    int ncases = 0, block = 128, lanes = 1;
     bool any_tvf = false;
     int loop_mode = SPHST_LOOP_GRAPH;
     std::vector<CaseDesc> h_desc;
@@ -97,6 +118,8 @@ template <typename T> struct EngineT : Engine {
         members = cases;
         ncases = (int)cases.size();
         block = blk;
+        lanes = cases.empty() ? 1 : cases[0]->P.lanes;
+        if (lanes != 2 && lanes != 4) lanes = 1;
         if (user_stream) {
             stream = user_stream;
         } else {
@@ -310,10 +333,10 @@ template <typename T> struct EngineT : Engine {
 
     int launch_body(cudaGraphConditionalHandle h, int use_handle) {
         k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, h, use_handle);
-        SPH_CLASSES(4, k_sweep_A, snap, drho, lgeo, gradC);
+        SPH_CLASSES_L(4, k_sweep_A, snap, drho, lgeo, gradC);
         SPH_CLASSES(2, k_sweep_S, band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
-        SPH_CLASSES(4, k_sweep_B, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo);
-        SPH_CLASSES(4, k_sweep_C, snap, vel_new, drho, vel, pos, lgeo);
+        SPH_CLASSES_L(4, k_sweep_B, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo);
+        SPH_CLASSES_L(4, k_sweep_C, snap, vel_new, drho, vel, pos, lgeo);
         SPH_CK(cudaGetLastError());
         return SPHST_OK;
     }
@@ -442,12 +465,12 @@ template <typename T> struct EngineT : Engine {
         });
         for (;;) {
             timed(2, 1, [&] { k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, 0, 0); });
-            timed(3, ncls, [&] { SPH_CLASSES(4, k_sweep_A, snap, drho, lgeo, gradC); });
+            timed(3, ncls, [&] { SPH_CLASSES_L(4, k_sweep_A, snap, drho, lgeo, gradC); });
             timed(6, nlist, [&] {
                 SPH_CLASSES(2, k_sweep_S, band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
             });
-            timed(4, ncls, [&] { SPH_CLASSES(4, k_sweep_B, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo); });
-            timed(5, ncls, [&] { SPH_CLASSES(4, k_sweep_C, snap, vel_new, drho, vel, pos, lgeo); });
+            timed(4, ncls, [&] { SPH_CLASSES_L(4, k_sweep_B, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo); });
+            timed(5, ncls, [&] { SPH_CLASSES_L(4, k_sweep_C, snap, vel_new, drho, vel, pos, lgeo); });
             if (rc) break;
             int flag = 0;
             cudaError_t e = cudaMemcpy(&flag, d_loop_flag, sizeof(int), cudaMemcpyDeviceToHost);

@@ -352,29 +352,31 @@ __device__ __forceinline__ uint32_t cell_code(int ox, int oy, int oz) {
     return (uint32_t)(ox + 1) | ((uint32_t)(oy + 1) << 2) | (D == 3 ? ((uint32_t)(oz + 1) << 4) : 0u);
 }
 
-template <int PART, typename T, int D, typename F>
+// With L lanes per particle, lane `sub` of the particle's group takes the
+// entries sub, sub + L, sub + 2L, ... of its list.
+template <int PART, typename T, int D, int L = 1, typename F>
 __device__ __forceinline__ void walk_list(const CaseDesc &d, const CasePhys<T> &cp,
                                           const uint32_t *__restrict__ nbr,
                                           const uint32_t *__restrict__ cnt,
                                           const V4<T> *__restrict__ snap, int64_t i,
-                                          const V4<T> &si, F &&f) {
+                                          const V4<T> &si, F &&f, uint32_t sub = 0) {
     const int64_t stride = d.p_end - d.p_begin;
-    const uint32_t *p = nbr + d.nbr_base + (i - d.p_begin);
+    const uint32_t *p = nbr + d.nbr_base + (i - d.p_begin) + (int64_t)sub * stride;
     const uint32_t c = PART == PART_OTHER ? cnt[i] >> 16 : cnt[i] & CNT_MASK;
     const T cs = cp.cs;
     const L2Pol pol = l2_policies();
 #if SPHST_LIST_PREFETCH
-    uint32_t next = c ? ld_list(p, pol) : 0u;
+    uint32_t next = sub < c ? ld_list(p, pol) : 0u;
 #endif
 #pragma unroll kListUnroll
-    for (uint32_t k = 0; k < c; ++k) {
+    for (uint32_t k = sub; k < c; k += L) {
 #if SPHST_LIST_PREFETCH
         const uint32_t e = next;
-        p += stride;
-        if (k + 1 < c) next = ld_list(p, pol);
+        p += L * stride;
+        if (k + L < c) next = ld_list(p, pol);
 #else
         const uint32_t e = ld_list(p, pol);
-        p += stride;
+        p += L * stride;
 #endif
         const uint32_t j = e >> NBR_SHIFT;
         const V4<T> sj = ld4_keep(snap + j, pol);
@@ -392,15 +394,15 @@ __device__ __forceinline__ void walk_list(const CaseDesc &d, const CasePhys<T> &
 // The list walk with one more per-neighbour array: f(j, s_j, aux_j, r_ij, r^2).
 // With SPHST_PIPE the entry two ahead and the position and aux word of the
 // next neighbour are in flight while the current pair is evaluated.
-template <typename T, int D, typename F>
+template <typename T, int D, int L = 1, typename F>
 __device__ __forceinline__ void walk_list_aux(const CaseDesc &d, const CasePhys<T> &cp,
                                               const uint32_t *__restrict__ nbr,
                                               const uint32_t *__restrict__ cnt,
                                               const V4<T> *__restrict__ snap,
                                               const V4<T> *__restrict__ aux, int64_t i,
-                                              const V4<T> &si, F &&f) {
+                                              const V4<T> &si, F &&f, uint32_t sub = 0) {
     const int64_t stride = d.p_end - d.p_begin;
-    const uint32_t *p = nbr + d.nbr_base + (i - d.p_begin);
+    const uint32_t *p = nbr + d.nbr_base + (i - d.p_begin) + (int64_t)sub * stride;
     const uint32_t c = cnt[i] & CNT_MASK;
     const T cs = cp.cs;
     const L2Pol pol = l2_policies();
@@ -414,6 +416,7 @@ __device__ __forceinline__ void walk_list_aux(const CaseDesc &d, const CasePhys<
         f(e >> NBR_SHIFT, sj, aj, rx, ry, rz, norm2<T, D>(rx, ry, rz));
     };
 #if SPHST_PIPE
+    static_assert(L == 1, "the two-deep pipeline walks one list per thread");
     if (c == 0) return;
     uint32_t e = ld_list(p, pol);
     p += stride;
@@ -435,17 +438,17 @@ __device__ __forceinline__ void walk_list_aux(const CaseDesc &d, const CasePhys<
     }
 #else
 #if SPHST_LIST_PREFETCH
-    uint32_t next = c ? ld_list(p, pol) : 0u;
+    uint32_t next = sub < c ? ld_list(p, pol) : 0u;
 #endif
 #pragma unroll kListUnroll
-    for (uint32_t k = 0; k < c; ++k) {
+    for (uint32_t k = sub; k < c; k += L) {
 #if SPHST_LIST_PREFETCH
         const uint32_t e = next;
-        p += stride;
-        if (k + 1 < c) next = ld_list(p, pol);
+        p += L * stride;
+        if (k + L < c) next = ld_list(p, pol);
 #else
         const uint32_t e = ld_list(p, pol);
-        p += stride;
+        p += L * stride;
 #endif
         const uint32_t j = e >> NBR_SHIFT;
         pair(e, ld4_keep(snap + j, pol), ld4_keep(aux + j, pol));
@@ -455,13 +458,14 @@ __device__ __forceinline__ void walk_list_aux(const CaseDesc &d, const CasePhys<
 
 // neighbours of i with aux[j] loaded for f(j, s_j, aux_j, r_ij, r^2), from the
 // list or the cell walk
-template <bool LIST, typename T, int D, typename F>
+template <bool LIST, typename T, int D, int L = 1, typename F>
 __device__ __forceinline__ bool neighbors_aux(const CaseDesc &d, const CasePhys<T> &cp,
                                               const uint32_t *starts, const uint32_t *nbr,
                                               const uint32_t *cnt, const V4<T> *snap, const V4<T> *aux,
-                                              int64_t i, const V4<T> &si, uint32_t pki, F &&f) {
+                                              int64_t i, const V4<T> &si, uint32_t pki, F &&f,
+                                              uint32_t sub = 0) {
     if constexpr (LIST) {
-        walk_list_aux<T, D>(d, cp, nbr, cnt, snap, aux, i, si, f);
+        walk_list_aux<T, D, L>(d, cp, nbr, cnt, snap, aux, i, si, f, sub);
         return false;
     } else {
         return walk<T, D>(d, cp, starts, snap, i, si, pki,
@@ -472,13 +476,13 @@ __device__ __forceinline__ bool neighbors_aux(const CaseDesc &d, const CasePhys<
 // neighbours of i from the list (LIST) or from the cell walk; PART_OTHER
 // restricts the list to the other fluid phase (the cell walk visits all and
 // the caller filters)
-template <bool LIST, typename T, int D, int PART = PART_ALL, typename F>
+template <bool LIST, typename T, int D, int PART = PART_ALL, int L = 1, typename F>
 __device__ __forceinline__ bool neighbors(const CaseDesc &d, const CasePhys<T> &cp,
                                           const uint32_t *starts, const uint32_t *nbr,
                                           const uint32_t *cnt, const V4<T> *snap, int64_t i,
-                                          const V4<T> &si, uint32_t pki, F &&f) {
+                                          const V4<T> &si, uint32_t pki, F &&f, uint32_t sub = 0) {
     if constexpr (LIST) {
-        walk_list<PART, T, D>(d, cp, nbr, cnt, snap, i, si, f);
+        walk_list<PART, T, D, L>(d, cp, nbr, cnt, snap, i, si, f, sub);
         return false;
     } else {
         return walk<T, D>(d, cp, starts, snap, i, si, pki, f);
@@ -548,6 +552,19 @@ __device__ __forceinline__ void walk_geo_aux(const CaseDesc &d, const uint32_t *
                                              const V4<T> *__restrict__ aux, int64_t i, F &&f) {
     walk_geo<PART_ALL, T>(d, nbr, cnt, lgeo, i,
                           [&](bool other, uint32_t j, const V4<T> &G) { f(other, j, G, ld4(aux + j)); });
+}
+
+// Sum over the L lanes that share one particle (L = 1, 2, 4; groups are
+// aligned within the warp).  The butterfly gives every lane of the group the
+// same value: each step adds two partial sums in an order-free way.
+template <int L, typename T> __device__ __forceinline__ T group_sum(T v) {
+    if constexpr (L > 1) {
+        const unsigned lane = threadIdx.x & 31u;
+        const unsigned mask = ((1u << L) - 1u) << (lane & ~(unsigned)(L - 1));
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+    }
+    return v;
 }
 
 // kernel radial derivative and unit vector of one pair
@@ -1057,10 +1074,10 @@ __device__ __forceinline__ void sweep_V(const CaseDesc &d, const CasePhys<T> &cp
 }
 
 // ---- A: colour gradient, Eq. 22 (only pairs of different fluids contribute)
-template <bool LIST, typename T, int D>
+template <bool LIST, typename T, int D, int L = 1>
 __device__ __forceinline__ void sweep_A(const CaseDesc &d, const CasePhys<T> &cp, int64_t i,
                                         const uint32_t *starts, const uint32_t *nbr, const uint32_t *cnt, const V4<T> *snap, const T *drho,
-                                        const V4<T> *lgeo, V4<T> *gradC) {
+                                        const V4<T> *lgeo, V4<T> *gradC, uint32_t sub = 0) {
     const V4<T> si = ld4(snap + i);
     const uint32_t pki = w_bits(si.w);
     const uint32_t ki = phase_of(pki);
@@ -1069,7 +1086,7 @@ __device__ __forceinline__ void sweep_A(const CaseDesc &d, const CasePhys<T> &cp
         const uint32_t other = ki ^ 1u;
         const T two_phi = cp.two_phi[ki];
         const T m_o = cp.mass[other], rho0_o = cp.rho0[other];
-        if constexpr (LIST && SPHST_LIST_GEO) {
+        if constexpr (LIST && SPHST_LIST_GEO && L == 1) {
             walk_geo<PART_OTHER, T>(d, nbr, cnt, lgeo, i, [&](bool, uint32_t j, const V4<T> &G) {
                 const T s = two_phi * G.w * div_fast(m_o, rho0_o + drho[j]);
                 g.x += s * G.x;
@@ -1077,7 +1094,7 @@ __device__ __forceinline__ void sweep_A(const CaseDesc &d, const CasePhys<T> &cp
                 if (D == 3) g.z += s * G.z;
             });
         } else
-        neighbors<LIST, T, D, PART_OTHER>(d, cp, starts, nbr, cnt, snap, i, si, pki,
+        neighbors<LIST, T, D, PART_OTHER, L>(d, cp, starts, nbr, cnt, snap, i, si, pki,
             [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
                 if (!LIST && phase_of(w_bits(sj.w)) != other) return;
                 const PairGeo<T> gg = geo(cp, r2);
@@ -1086,10 +1103,13 @@ __device__ __forceinline__ void sweep_A(const CaseDesc &d, const CasePhys<T> &cp
                 g.x += s * rx;
                 g.y += s * ry;
                 if (D == 3) g.z += s * rz;
-            });
+            }, sub);
+        g.x = group_sum<L>(g.x);
+        g.y = group_sum<L>(g.y);
+        if (D == 3) g.z = group_sum<L>(g.z);
         g.w = sqrt(g.x * g.x + g.y * g.y + g.z * g.z);
     }
-    gradC[i] = g;
+    if (sub == 0) gradC[i] = g;
 }
 
 // ---- B: pressure + surface tension + kick
@@ -1103,13 +1123,13 @@ __device__ __forceinline__ void sweep_A(const CaseDesc &d, const CasePhys<T> &cp
 //
 // PASS: 0 = pressure + surface in one walk (cell walk), 1 = pressure and the
 // stored surface sum (list), 2 = surface sum only (list, band particles).
-template <bool LIST, int PASS, typename T, int D>
+template <bool LIST, int PASS, typename T, int D, int L = 1>
 __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &cp, T dt,
                                           int64_t i, const uint32_t *starts, const uint32_t *nbr, const uint32_t *cnt,
                                           const uint8_t *band, const V4<T> *snap,
                                           const V4<T> *vel, const V4<T> *gradC,
                                           const V4<T> *acc_visc, V4<T> *acc_surf, V4<T> *vel_new,
-                                          const V4<T> *lgeo, uint32_t *phase_out) {
+                                          const V4<T> *lgeo, uint32_t *phase_out, uint32_t sub = 0) {
     const V4<T> si = ld4(snap + i);
     const uint32_t pki = w_bits(si.w);
     const uint32_t ki = phase_of(pki);
@@ -1233,7 +1253,7 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
         acc_surf[i] = V4<T>{asx, asy, asz, T(0)};
         return 0.0;
     } else if constexpr (PASS == 1) {
-        if constexpr (LIST && SPHST_LIST_GEO) {
+        if constexpr (LIST && SPHST_LIST_GEO && L == 1) {
             const T rho0_o = sel(ki ^ 1u, rho0_0, rho0_1), rho0_s = sel(ki, rho0_0, rho0_1);
             const T m_o = sel(ki ^ 1u, m_0, m_1), m_s = sel(ki, m_0, m_1);
             walk_geo_aux<T>(d, nbr, cnt, lgeo, vel, i, [&](bool other, uint32_t, const V4<T> &G, const V4<T> &vj) {
@@ -1242,7 +1262,14 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
                               other ? m_o : m_s, vj);
             });
         } else
-        neighbors_aux<LIST, T, D>(d, cp, starts, nbr, cnt, snap, vel, i, si, pki, pressure);
+        neighbors_aux<LIST, T, D, L>(d, cp, starts, nbr, cnt, snap, vel, i, si, pki, pressure, sub);
+        apx = group_sum<L>(apx);
+        apy = group_sum<L>(apy);
+        if (D == 3) apz = group_sum<L>(apz);
+        if (sub != 0) {               // the group's lane 0 kicks
+            *phase_out = PH_WALL;
+            return 0.0;
+        }
         if (surface_on && band[i]) {
             const V4<T> as = acc_surf[i];
             asx = as.x; asy = as.y; asz = as.z;
@@ -1266,11 +1293,11 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
 }
 
 // ---- C: continuity (Eq. 6) with v* (normal component -U*) + drift
-template <bool LIST, typename T, int D>
+template <bool LIST, typename T, int D, int L = 1>
 __device__ __forceinline__ void sweep_C(const CaseDesc &d, const CasePhys<T> &cp, T dt, int64_t i,
                                         const uint32_t *starts, const uint32_t *nbr, const uint32_t *cnt, const V4<T> *snap,
                                         const V4<T> *vel_new, T *drho,
-                                        V4<T> *vel, V4<T> *pos, const V4<T> *lgeo) {
+                                        V4<T> *vel, V4<T> *pos, const V4<T> *lgeo, uint32_t sub = 0) {
     const V4<T> si = ld4(snap + i);
     const uint32_t pki = w_bits(si.w);
     const uint32_t ki = phase_of(pki);
@@ -1301,7 +1328,7 @@ __device__ __forceinline__ void sweep_C(const CaseDesc &d, const CasePhys<T> &cp
         const T num = (rho_j * c0 * dve + (sp_i - sc0sq * drj)) * m_j;
         s += div_fast(num, c0 * (rho_i + rho_j) * rho_j) * dW;
     };
-    if constexpr (LIST && SPHST_LIST_GEO) {
+    if constexpr (LIST && SPHST_LIST_GEO && L == 1) {
         const T rho0_o = sel(ki ^ 1u, rho0_0, rho0_1), rho0_s = sel(ki, rho0_0, rho0_1);
         const T m_o = sel(ki ^ 1u, m_0, m_1), m_s = sel(ki, m_0, m_1);
         walk_geo_aux<T>(d, nbr, cnt, lgeo, vel_new, i, [&](bool other, uint32_t, const V4<T> &G, const V4<T> &vj) {
@@ -1311,7 +1338,7 @@ __device__ __forceinline__ void sweep_C(const CaseDesc &d, const CasePhys<T> &cp
             pair(dve, wall ? -G.w : G.w, wall, other ? rho0_o : rho0_s, other ? m_o : m_s, vj.w);
         });
     } else
-    neighbors_aux<LIST, T, D>(d, cp, starts, nbr, cnt, snap, vel_new, i, si, pki,
+    neighbors_aux<LIST, T, D, L>(d, cp, starts, nbr, cnt, snap, vel_new, i, si, pki,
         [&](uint32_t, const V4<T> &sj, const V4<T> &vj, T rx, T ry, T rz, T r2) {
             const PairGeo<T> g = kgeo(r2);
             const uint32_t kj = phase_of(w_bits(sj.w));
@@ -1319,7 +1346,9 @@ __device__ __forceinline__ void sweep_C(const CaseDesc &d, const CasePhys<T> &cp
             const T dvx = dvxy.x, dvy = dvxy.y, dvz = D == 3 ? vi.z - vj.z : T(0);
             pair((dvx * rx + dvy * ry + dvz * rz) * g.inv_r, g.dW, kj == PH_WALL, sel(kj, rho0_0, rho0_1),
                  sel(kj, m_0, m_1), vj.w);
-        });
+        }, sub);
+    s = group_sum<L>(s);
+    if (sub != 0) return;
     const T dr_new = dri + dt * (T(2) * rho_i * s);
     drho[i] = dr_new;
     V4<T> p = pos[i];
@@ -1510,14 +1539,23 @@ __global__ void SPH_SWEEP_BOUNDS k_sweep_V(SweepArgs a, const V4<T> *snap, const
                         &a.st[t.c].status);
 }
 
-template <typename T, int D, bool LIST>
+// Sweeps A, B and C take L lanes per particle (L = 1, 2, 4; list classes):
+// L blocks share one tile, block b takes its part b % L of blockDim / L
+// particles, and lane threadIdx % L of a particle's group walks every L-th
+// list entry.  local_index gives the particle's index within its tile.
+template <int L> __device__ __forceinline__ int local_index() {
+    return L == 1 ? (int)threadIdx.x : (int)((blockIdx.x % L) * (blockDim.x / L) + threadIdx.x / L);
+}
+
+template <typename T, int D, bool LIST, int L = 1>
 __global__ void SPH_SWEEPAS_BOUNDS k_sweep_A(SweepArgs a, const V4<T> *snap, const T *drho, const V4<T> *lgeo,
                                            V4<T> *gradC) {
-    const Tile t = a.tiles[a.tile0 + blockIdx.x];
-    if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
+    const Tile t = a.tiles[a.tile0 + blockIdx.x / L];
+    const int li = local_index<L>();
+    if (li >= t.n || !a.st[t.c].active) return;
     const CaseDesc &d = a.desc[t.c];
-    const int64_t i = t.begin + threadIdx.x;
-    sweep_A<LIST, T, D>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, lgeo, gradC);
+    const int64_t i = t.begin + li;
+    sweep_A<LIST, T, D, L>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, lgeo, gradC, threadIdx.x % L);
 }
 
 // surface sum of the band particles (list classes only), before B: one
@@ -1539,20 +1577,21 @@ __global__ void SPH_SWEEPAS_BOUNDS k_sweep_S(SweepArgs a, const uint64_t *blist,
                            acc_surf, nullptr, nullptr, &ph);
 }
 
-template <typename T, int D, bool LIST>
+template <typename T, int D, bool LIST, int L = 1>
 __global__ void SPH_SWEEPB_BOUNDS k_sweep_B(SweepArgs a, const uint8_t *band, const V4<T> *snap, const V4<T> *vel,
                                             const V4<T> *gradC, const V4<T> *acc_visc, V4<T> *acc_surf,
                                             V4<T> *vel_new, const V4<T> *lgeo) {
-    const Tile t = a.tiles[a.tile0 + blockIdx.x];
+    const Tile t = a.tiles[a.tile0 + blockIdx.x / L];
     if (!a.st[t.c].active) return;                 // uniform per block
     const CaseDesc &d = a.desc[t.c];
     double v2 = 0.0;
     uint32_t ph = PH_WALL;
-    if ((int)threadIdx.x < t.n) {
-        const int64_t i = t.begin + threadIdx.x;
+    const int li = local_index<L>();
+    if (li < t.n) {
+        const int64_t i = t.begin + li;
         const T dt = (T)a.st[t.c].dt;
-        v2 = sweep_B<LIST, LIST ? 1 : 0, T, D>(d, phys<T>(d), dt, i, a.starts, a.nbr, a.cnt, band, snap, vel,
-                                               gradC, acc_visc, acc_surf, vel_new, lgeo, &ph);
+        v2 = sweep_B<LIST, LIST ? 1 : 0, T, D, L>(d, phys<T>(d), dt, i, a.starts, a.nbr, a.cnt, band, snap, vel,
+                                                  gradC, acc_visc, acc_surf, vel_new, lgeo, &ph, threadIdx.x % L);
     }
     unsigned long long m0 = ph == 0 ? (unsigned long long)__double_as_longlong(v2) : 0ull;
     unsigned long long m1 = ph == 1 ? (unsigned long long)__double_as_longlong(v2) : 0ull;
@@ -1564,15 +1603,17 @@ __global__ void SPH_SWEEPB_BOUNDS k_sweep_B(SweepArgs a, const uint8_t *band, co
     }
 }
 
-template <typename T, int D, bool LIST>
+template <typename T, int D, bool LIST, int L = 1>
 __global__ void SPH_SWEEP_BOUNDS k_sweep_C(SweepArgs a, const V4<T> *snap, const V4<T> *vel_new, T *drho,
                                            V4<T> *vel, V4<T> *pos, const V4<T> *lgeo) {
-    const Tile t = a.tiles[a.tile0 + blockIdx.x];
-    if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
+    const Tile t = a.tiles[a.tile0 + blockIdx.x / L];
+    const int li = local_index<L>();
+    if (li >= t.n || !a.st[t.c].active) return;
     const CaseDesc &d = a.desc[t.c];
-    const int64_t i = t.begin + threadIdx.x;
+    const int64_t i = t.begin + li;
     const T dt = (T)a.st[t.c].dt;
-    sweep_C<LIST, T, D>(d, phys<T>(d), dt, i, a.starts, a.nbr, a.cnt, snap, vel_new, drho, vel, pos, lgeo);
+    sweep_C<LIST, T, D, L>(d, phys<T>(d), dt, i, a.starts, a.nbr, a.cnt, snap, vel_new, drho, vel, pos, lgeo,
+                           threadIdx.x % L);
 }
 
 // ---------------------------------------------------------- diagnostics

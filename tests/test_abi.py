@@ -30,11 +30,19 @@ def test_every_declared_symbol_is_exported():
     assert set(names) <= set(S.EXPORTS)
 
 
+def test_struct_layout_matches_the_binding():
+    sizes = [C.c_int64() for _ in range(3)]
+    assert S.load().sphst_struct_sizes(*[C.byref(v) for v in sizes]) == S.OK
+    assert [v.value for v in sizes] == [C.sizeof(S.CaseParams), C.sizeof(S.PhaseProps), C.sizeof(S.StepInfo)]
+
+
 def test_default_params_and_validation():
     p = S.default_params(dx=0.01)
     assert p.dim == 2 and p.precision == 32 and p.h_factor == 1.3 and p.tvf_alpha == 0.2
+    assert p.lanes == 1 and p.block == 128
     for bad in (dict(dx=0.0), dict(dx=0.01, c0=-1.0), dict(dx=0.01, gamma=-1.0),
-                dict(dx=0.01, block=48), dict(dx=0.01, limiter=7), dict(dx=0.01, grid_pad=0)):
+                dict(dx=0.01, block=48), dict(dx=0.01, limiter=7), dict(dx=0.01, grid_pad=0),
+                dict(dx=0.01, lanes=3), dict(dx=0.01, lanes=8), dict(dx=0.01, block=512)):
         with pytest.raises(S.SphstError) as e:
             S.create_case(S.default_params(**bad))
         assert e.value.code == S.ERR_INVALID_ARG

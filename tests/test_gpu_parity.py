@@ -227,6 +227,44 @@ def test_list_and_cell_walk_agree(dim, precision):
         assert np.abs(a - b).max() <= tol * scale, k
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("lanes", [2, 4])
+def test_lanes_per_particle_fp64_against_oracle(dim, lanes):
+    # L lanes split each particle's list (sweeps A, B, C): same pairs, sums
+    # in another order, so the oracle bar of one advection step holds
+    case = small(dim)
+    g, o, info, oinfo, pos0, kind = run_both(case, 64, 1, lanes=lanes)
+    assert info["n_sub"] == oinfo["n_sub"] > 5
+    for key in ("pos", "vel", "rho", "gradC", "acc_visc"):
+        assert rel_err(g, o, pos0, kind, key, case) <= 1e-12, key
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("lanes", [2, 4])
+def test_lanes_per_particle_fp32_one_substep(dim, lanes):
+    case = one_substep_case(dim)
+    g, o, info, oinfo, pos0, kind = run_both(case, 32, 1, lanes=lanes)
+    assert info["n_sub"] == oinfo["n_sub"] == 1
+    for key in ("pos", "vel", "rho", "gradC", "acc_visc"):
+        assert rel_err(g, o, pos0, kind, key, case) <= 1e-5, key
+
+
+@pytest.mark.parametrize("lanes", [2, 4])
+def test_lanes_per_particle_repeat_bitwise(lanes):
+    # the group sums run in a fixed order: two runs are identical, and a
+    # tile's last, partly filled block (ragged tail) is covered
+    case = small(3, n_side=11)
+    out = []
+    for _ in range(2):
+        h = gpu_case(case, 32, lanes=lanes, block=64)
+        S.step(h, 2)
+        out.append([S.read_fields(h, f, 3) for f in (S.FIELD_POS, S.FIELD_VEL, S.FIELD_RHO, S.FIELD_GRADC)])
+        S.destroy(h)
+    assert case.n % 64 != 0
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+
+
 def test_profiled_launch_counts():
     # one advection step of a two-phase list case: every per-substep kernel
     # (criterion, A, S, B, C) runs once per substep
