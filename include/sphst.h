@@ -139,7 +139,9 @@ typedef struct {
     double  period_lo[3];
     double  period_hi[3];
     int32_t lanes;          /* lanes per particle in the per-substep sweeps
-                               with the neighbour list: 1, 2 or 4.  With L > 1
+                               (colour gradient, pressure, continuity) with
+                               the neighbour list: 1, 2 or 4; the surface
+                               sweep over the interface band takes at least 2.  With L > 1
                                the L lanes of a particle split its list and
                                add their partial sums (fixed order, so runs
                                repeat bit for bit; results differ from L = 1

@@ -35,22 +35,22 @@ enum ArrayId { A_POS = 0, A_VEL, A_DRHO, A_ID, A_GRADC, A_ACCV };
         }                                                                              \
     }
 
-// SPH_CLASSES_L: the same for sweeps A, B and C, whose list classes run with
-// `lanes` lanes per particle (L blocks per tile).
-#define SPH_LANES(KERN, D, ...)                                                                   \
-    switch (lanes) {                                                                              \
+// SPH_CLASSES_L: the same for sweeps A, S, B and C, whose list classes run
+// with LN lanes per particle (L blocks per tile).
+#define SPH_LANES(KERN, D, LN, ...)                                                               \
+    switch (LN) {                                                                                 \
     case 2: KERN<T, D, true, 2><<<g_ * 2, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
     case 4: KERN<T, D, true, 4><<<g_ * 4, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
     default: KERN<T, D, true, 1><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;               \
     }
-#define SPH_CLASSES_L(NCLS, KERN, ...)                                                 \
+#define SPH_CLASSES_L(NCLS, KERN, LN, ...)                                             \
     for (int k_ = 0; k_ < (NCLS); ++k_) {                                              \
         if (!cls_n[k_]) continue;                                                      \
         const SweepArgs a_ = sweep_args(k_);                                           \
         const unsigned g_ = (unsigned)cls_n[k_];                                       \
         switch (k_) {                                                                  \
-        case 0: SPH_LANES(KERN, 3, __VA_ARGS__) break;                                 \
-        case 1: SPH_LANES(KERN, 2, __VA_ARGS__) break;                                 \
+        case 0: SPH_LANES(KERN, 3, LN, __VA_ARGS__) break;                             \
+        case 1: SPH_LANES(KERN, 2, LN, __VA_ARGS__) break;                             \
         case 2: KERN<T, 3, false><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;   \
         default: KERN<T, 2, false><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;  \
         }                                                                              \
@@ -294,6 +294,11 @@ template <typename T> struct EngineT : Engine {
         return SPHST_OK;
     }
 
+    // The surface sweep covers only the interface band, a few blocks per SM
+    // at most, so it takes at least SPHST_SURFACE_MIN_LANES lanes per band
+    // particle whatever `lanes` is (measured on the 3D drop: 93 -> 60 us with 2)
+    int surface_lanes() const { return std::max(lanes, (int)SPHST_SURFACE_MIN_LANES); }
+
     static int tile_class(const CaseDesc &d) { return (d.nbr_mode == 0 ? 0 : 2) + (d.dim == 3 ? 0 : 1); }
     SweepArgs sweep_args(int k) const { return SweepArgs{d_tiles, d_desc, d_state, starts, nbr, nbr_cnt, cls_b[k]}; }
     int n_classes(int upto) const {
@@ -333,10 +338,10 @@ template <typename T> struct EngineT : Engine {
 
     int launch_body(cudaGraphConditionalHandle h, int use_handle) {
         k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, h, use_handle);
-        SPH_CLASSES_L(4, k_sweep_A, snap, drho, lgeo, gradC);
-        SPH_CLASSES(2, k_sweep_S, band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
-        SPH_CLASSES_L(4, k_sweep_B, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo);
-        SPH_CLASSES_L(4, k_sweep_C, snap, vel_new, drho, vel, pos, lgeo);
+        SPH_CLASSES_L(4, k_sweep_A, lanes, snap, drho, lgeo, gradC);
+        SPH_CLASSES_L(2, k_sweep_S, surface_lanes(), band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
+        SPH_CLASSES_L(4, k_sweep_B, lanes, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo);
+        SPH_CLASSES_L(4, k_sweep_C, lanes, snap, vel_new, drho, vel, pos, lgeo);
         SPH_CK(cudaGetLastError());
         return SPHST_OK;
     }
@@ -465,12 +470,12 @@ template <typename T> struct EngineT : Engine {
         });
         for (;;) {
             timed(2, 1, [&] { k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, 0, 0); });
-            timed(3, ncls, [&] { SPH_CLASSES_L(4, k_sweep_A, snap, drho, lgeo, gradC); });
+            timed(3, ncls, [&] { SPH_CLASSES_L(4, k_sweep_A, lanes, snap, drho, lgeo, gradC); });
             timed(6, nlist, [&] {
-                SPH_CLASSES(2, k_sweep_S, band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
+                SPH_CLASSES_L(2, k_sweep_S, surface_lanes(), band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
             });
-            timed(4, ncls, [&] { SPH_CLASSES_L(4, k_sweep_B, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo); });
-            timed(5, ncls, [&] { SPH_CLASSES_L(4, k_sweep_C, snap, vel_new, drho, vel, pos, lgeo); });
+            timed(4, ncls, [&] { SPH_CLASSES_L(4, k_sweep_B, lanes, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo); });
+            timed(5, ncls, [&] { SPH_CLASSES_L(4, k_sweep_C, lanes, snap, vel_new, drho, vel, pos, lgeo); });
             if (rc) break;
             int flag = 0;
             cudaError_t e = cudaMemcpy(&flag, d_loop_flag, sizeof(int), cudaMemcpyDeviceToHost);

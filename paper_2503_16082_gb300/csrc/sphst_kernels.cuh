@@ -28,6 +28,7 @@
 //   SPHST_SWEEP_MINB   >0: minimum resident 256-thread blocks per SM for the
 //                      sweeps (caps registers per thread)
 //   SPHST_SWEEPB_MINB  the same for sweep B alone (default 4: 64 registers)
+//   SPHST_SURFACE_MIN_LANES  least lanes per band particle of sweep S (1, 2, 4)
 //   SPHST_SWEEPAS_MINB the same for sweeps A and S (default 4: with the
 //                      64-register room the compiler keeps more loads in
 //                      flight; measured: A 35 -> 28 us, S 93 -> 89 us on the
@@ -64,6 +65,9 @@
 #endif
 #ifndef SPHST_SWEEP_MINB
 #define SPHST_SWEEP_MINB 0
+#endif
+#ifndef SPHST_SURFACE_MIN_LANES
+#define SPHST_SURFACE_MIN_LANES 2
 #endif
 #ifndef SPHST_SWEEPAS_MINB
 #define SPHST_SWEEPAS_MINB 4
@@ -1249,8 +1253,11 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
 
     const bool surface_on = d.n_fluid_phases == 2;
     if constexpr (PASS == 2) {
-        if (surface_on) neighbors<LIST, T, D>(d, cp, starts, nbr, cnt, snap, i, si, pki, surface);
-        acc_surf[i] = V4<T>{asx, asy, asz, T(0)};
+        if (surface_on) neighbors<LIST, T, D, PART_ALL, L>(d, cp, starts, nbr, cnt, snap, i, si, pki, surface, sub);
+        asx = group_sum<L>(asx);
+        asy = group_sum<L>(asy);
+        if (D == 3) asz = group_sum<L>(asz);
+        if (sub == 0) acc_surf[i] = V4<T>{asx, asy, asz, T(0)};
         return 0.0;
     } else if constexpr (PASS == 1) {
         if constexpr (LIST && SPHST_LIST_GEO && L == 1) {
@@ -1543,6 +1550,7 @@ __global__ void SPH_SWEEP_BOUNDS k_sweep_V(SweepArgs a, const V4<T> *snap, const
 // L blocks share one tile, block b takes its part b % L of blockDim / L
 // particles, and lane threadIdx % L of a particle's group walks every L-th
 // list entry.  local_index gives the particle's index within its tile.
+// Sweep S does the same per entry of its band list.
 template <int L> __device__ __forceinline__ int local_index() {
     return L == 1 ? (int)threadIdx.x : (int)((blockIdx.x % L) * (blockDim.x / L) + threadIdx.x / L);
 }
@@ -1559,13 +1567,13 @@ __global__ void SPH_SWEEPAS_BOUNDS k_sweep_A(SweepArgs a, const V4<T> *snap, con
 }
 
 // surface sum of the band particles (list classes only), before B: one
-// thread per entry of the class's compacted band list, so warps are full of
-// band particles; threads past the list's length exit at once
-template <typename T, int D, bool LIST>
+// thread (L lanes) per entry of the class's compacted band list, so warps
+// are full of band particles; threads past the list's length exit at once
+template <typename T, int D, bool LIST, int L = 1>
 __global__ void SPH_SWEEPAS_BOUNDS k_sweep_S(SweepArgs a, const uint64_t *blist, const uint32_t *bcount,
                                            const uint8_t *band, const V4<T> *snap, const V4<T> *vel,
                                            const V4<T> *gradC, V4<T> *acc_surf) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L;
     if (k >= (int64_t)*bcount) return;
     const uint64_t e = blist[k];
     const int c = (int)(e >> 32);
@@ -1573,8 +1581,8 @@ __global__ void SPH_SWEEPAS_BOUNDS k_sweep_S(SweepArgs a, const uint64_t *blist,
     if (!a.st[c].active) return;
     const CaseDesc &d = a.desc[c];
     uint32_t ph;
-    sweep_B<LIST, 2, T, D>(d, phys<T>(d), T(0), i, a.starts, a.nbr, a.cnt, band, snap, vel, gradC, nullptr,
-                           acc_surf, nullptr, nullptr, &ph);
+    sweep_B<LIST, 2, T, D, L>(d, phys<T>(d), T(0), i, a.starts, a.nbr, a.cnt, band, snap, vel, gradC, nullptr,
+                              acc_surf, nullptr, nullptr, &ph, threadIdx.x % L);
 }
 
 template <typename T, int D, bool LIST, int L = 1>
