@@ -77,6 +77,20 @@ def test_staged_case_reads_back_and_rejects_third_fluid():
     assert S.load().sphst_destroy(None) == S.OK
 
 
+def test_case_without_fluid_cannot_step():
+    # an empty case, and one holding only walls, are rejected on the host
+    for walls in (False, True):
+        h = S.create_case(S.default_params(dx=0.1))
+        try:
+            if walls:
+                S.add_phase_particles(h, S.WALL, np.array([[0.05, 0.05], [0.15, 0.05]]))
+            info = S.step(h, 1, check=False)
+            assert info["rc"] == S.ERR_STATE
+            assert "no fluid" in S.last_error()
+        finally:
+            S.destroy(h)
+
+
 def test_batch_bookkeeping_on_host():
     b = S.batch_create(32)
     cases = [S.case_from_spec(sphcases.small_droplet(2, 10)) for _ in range(3)]
