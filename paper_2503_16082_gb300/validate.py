@@ -4,7 +4,7 @@
   python -m paper_2503_16082_gb300.validate oscillating_3d [--periods 1.5]
   python -m paper_2503_16082_gb300.validate impact_3d [--t-end 2]
   python -m paper_2503_16082_gb300.validate oscillating_2d [--ratio 1000] [--r-over-dp 12] [--xi 0]
-  python -m paper_2503_16082_gb300.validate shear_drop [--ca 0.1] [--t-end 20]
+  python -m paper_2503_16082_gb300.validate shear_drop [--ca 0.1] [--t-end 20] [--r-over-dp 12]
   python -m paper_2503_16082_gb300.validate impact_sweep [--res 20] [--u0 0.5 1 5 10 50]
 
 Each prints one JSON line.  laplace_2d: Young-Laplace jump (Eq. 37)
@@ -43,9 +43,19 @@ import paper_2503_16082_gb300 as S  # noqa: E402
 from paper_2503_16082_gb300 import observables as ob  # noqa: E402
 
 
+def launch(args) -> dict:
+    """Launch shape of the sweeps (speed only): block size and lanes per particle."""
+    kw = {}
+    if args.block:
+        kw["block"] = args.block
+    if args.lanes:
+        kw["lanes"] = args.lanes
+    return kw
+
+
 def laplace(args):
     case = sphcases.laplace_2d()
-    h = S.case_from_spec(case, precision=args.precision)
+    h = S.case_from_spec(case, precision=args.precision, **launch(args))
     phase = S.read_fields(h, S.FIELD_PHASE, 2)
     samples = []
     t0 = time.perf_counter()
@@ -78,7 +88,7 @@ def oscillating(args, dim):
         tau = ob.period_2d_drop(0.2, 1.0, 1.0) * (math.sqrt(2.0) if args.ratio == 1 else 1.0)
     if args.xi is not None:
         case.xi = args.xi
-    h = S.case_from_spec(case, precision=args.precision)
+    h = S.case_from_spec(case, precision=args.precision, **launch(args))
     phase = S.read_fields(h, S.FIELD_PHASE, dim)
     hk = case.h_factor * case.dx
     ts, an, stray = [], [], []
@@ -114,7 +124,7 @@ def oscillating(args, dim):
 
 def impact(args):
     case = sphcases.impact_3d()
-    h = S.case_from_spec(case, precision=args.precision)
+    h = S.case_from_spec(case, precision=args.precision, **launch(args))
     t0 = time.perf_counter()
     info = S.case_info(h)
     while info["t"] < args.t_end:
@@ -131,8 +141,8 @@ def impact(args):
 
 
 def shear(args):
-    case = sphcases.shear_drop_2d(args.ca, t_end=args.t_end)
-    h = S.case_from_spec(case, precision=args.precision)
+    case = sphcases.shear_drop_2d(args.ca, t_end=args.t_end, R_over_dp=args.r_over_dp)
+    h = S.case_from_spec(case, precision=args.precision, **launch(args))
     ts, ds = [], []
     t0 = time.perf_counter()
     info = S.case_info(h)
@@ -150,6 +160,7 @@ def shear(args):
     D = float(ds[tail].mean()) if len(ts) else float("nan")
     ref = ob.taylor_deformation(args.ca)
     return {"workload": "shear_drop_2d", "precision": args.precision, "Ca": args.ca, "Re": case.meta["Re"],
+            "R_over_dp": args.r_over_dp,
             "particles": case.n, "adv": info["n_adv"], "substeps": info["n_sub"], "t": info["t"],
             "status": info["status"], "D": D, "D_std_tail": float(ds[tail].std()) if len(ts) else None,
             "taylor": ref, "rel_error": (D - ref) / ref, "n_nonfinite": dg["n_nonfinite"],
@@ -161,7 +172,7 @@ def impact_sweep(args):
     out = []
     for U0 in args.u0:
         case = sphcases.impact_sweep_case(U0, args.res)
-        h = S.case_from_spec(case, precision=args.precision)
+        h = S.case_from_spec(case, precision=args.precision, **launch(args))
         t_end = case.t_end * args.t_frac
         t0 = time.perf_counter()
         info = S.case_info(h)
@@ -201,7 +212,10 @@ def main(argv=None):
     ap.add_argument("--periods", type=float, default=1.5)
     ap.add_argument("--every", type=int, default=5)
     ap.add_argument("--ratio", type=float, default=1000.0)
-    ap.add_argument("--r-over-dp", type=int, default=12, help="oscillating_2d: R / dp")
+    ap.add_argument("--r-over-dp", type=int, default=12, help="oscillating_2d, shear_drop: R / dp")
+    ap.add_argument("--block", type=int, default=0, help="threads per block of the sweeps (0: library default)")
+    ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="lanes per particle (0: library default); small 2D cases run faster with 4")
     ap.add_argument("--xi", type=float, default=None, help="penalty coefficient (default: from the density ratio)")
     ap.add_argument("--t-end", type=float, default=None, help="impact_3d: 2.0, shear_drop: 20.0")
     args = ap.parse_args(argv)
