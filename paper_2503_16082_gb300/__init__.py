@@ -204,12 +204,21 @@ def num_particles(case):
     return a.value, b.value
 
 
-def read_fields(case, field: int, dim: int) -> np.ndarray:
+def read_fields(case, field: int, dim: int, out: Optional[np.ndarray] = None) -> np.ndarray:
+    """FP64 field in insertion order, (n, dim) for vectors.  `out`, if given,
+    is a C-contiguous float64 array of at least n * width elements that
+    receives it (for example a view of pinned host memory, which the
+    device-to-host copy reads faster than pageable memory)."""
     n, _ = num_particles(case)
     w = dim if field in VECTOR_FIELDS else 1
-    out = np.empty(n * w, dtype=np.float64)
-    _check(load().sphst_read_fields(case, field, out.ctypes.data, out.size), "read_fields")
-    return out.reshape(n, w) if w > 1 else out
+    if out is None:
+        buf = np.empty(n * w, dtype=np.float64)
+    else:
+        if out.dtype != np.float64 or not out.flags["C_CONTIGUOUS"] or out.size < n * w:
+            raise ValueError("out must be a C-contiguous float64 array of at least n * width elements")
+        buf = out.reshape(-1)[: n * w]
+    _check(load().sphst_read_fields(case, field, buf.ctypes.data, buf.size), "read_fields")
+    return buf.reshape(n, w) if w > 1 else buf
 
 
 def destroy(case) -> None:

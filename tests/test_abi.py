@@ -59,6 +59,11 @@ def test_staged_case_reads_back_and_rejects_third_fluid():
         assert n == case.n and nf == case.n_fluid
         pos = S.read_fields(h, S.FIELD_POS, 2)
         assert np.array_equal(pos, case.flat()[0][:, :2])
+        buf = np.full(2 * case.n + 5, np.nan)             # a caller's buffer, larger than needed
+        got = S.read_fields(h, S.FIELD_POS, 2, out=buf)
+        assert np.array_equal(got, pos) and np.shares_memory(got, buf) and np.isnan(buf[-1])
+        with pytest.raises(ValueError):
+            S.read_fields(h, S.FIELD_POS, 2, out=np.zeros(case.n))
         ph = S.read_fields(h, S.FIELD_PHASE, 2)
         assert sorted(set(ph.tolist())) == [0.0, 1.0, 2.0]
         p = S.read_fields(h, S.FIELD_PRESSURE, 2)
