@@ -192,7 +192,7 @@ int64_t footprint(const sphst_case_params *P, int64_t n) {
     const int64_t kmax = P->nbr_mode == SPHST_NBR_LIST
                              ? (P->max_neighbors > 0 ? P->max_neighbors : (P->dim == 3 ? 128 : 48)) : 0;
     // V4 arrays, scalars, ints, list (+ its pair geometry), band + band list
-    const int64_t per = 9 * 4 * tsz + 2 * tsz + 4 * 4 + 4 * kmax + (SPHST_LIST_GEO ? 4 * tsz * kmax : 0) + 4 + 1 + 8;
+    const int64_t per = 9 * 4 * tsz + 2 * tsz + 6 * 4 + 4 * kmax + (SPHST_LIST_GEO ? 4 * tsz * kmax : 0) + 4 + 1 + 8;
     // cell table: cells ~ n / 2.6^d per axis padded to a power of two
     const double side = std::pow((double)std::max<int64_t>(n, 1), 1.0 / P->dim) / 2.6 + 2.0 * P->grid_pad + 2.0;
     int bits = 0;

@@ -36,18 +36,19 @@ enum ArrayId { A_POS = 0, A_VEL, A_DRHO, A_ID, A_GRADC, A_ACCV };
     }
 
 // SPH_CLASSES_L: the same for sweeps A, S, B and C, whose list classes run
-// with LN lanes per particle (L blocks per tile).
+// with LN lanes per particle (L blocks per tile); SPH_CLASSES_LF runs the
+// tiles over fluid ranks (sweeps B and C).
 #define SPH_LANES(KERN, D, LN, ...)                                                               \
     switch (LN) {                                                                                 \
     case 2: KERN<T, D, true, 2><<<g_ * 2, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
     case 4: KERN<T, D, true, 4><<<g_ * 4, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
     default: KERN<T, D, true, 1><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;               \
     }
-#define SPH_CLASSES_L(NCLS, KERN, LN, ...)                                             \
+#define SPH_CLASSES_LX(NCLS, KERN, LN, ARGS, CNT, ...)                                 \
     for (int k_ = 0; k_ < (NCLS); ++k_) {                                              \
-        if (!cls_n[k_]) continue;                                                      \
-        const SweepArgs a_ = sweep_args(k_);                                           \
-        const unsigned g_ = (unsigned)cls_n[k_];                                       \
+        if (!CNT[k_]) continue;                                                        \
+        const SweepArgs a_ = ARGS(k_);                                                 \
+        const unsigned g_ = (unsigned)CNT[k_];                                         \
         switch (k_) {                                                                  \
         case 0: SPH_LANES(KERN, 3, LN, __VA_ARGS__) break;                             \
         case 1: SPH_LANES(KERN, 2, LN, __VA_ARGS__) break;                             \
@@ -55,6 +56,8 @@ enum ArrayId { A_POS = 0, A_VEL, A_DRHO, A_ID, A_GRADC, A_ACCV };
         default: KERN<T, 2, false><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;  \
         }                                                                              \
     }
+#define SPH_CLASSES_L(NCLS, KERN, LN, ...) SPH_CLASSES_LX(NCLS, KERN, LN, sweep_args, cls_n, __VA_ARGS__)
+#define SPH_CLASSES_LF(NCLS, KERN, LN, ...) SPH_CLASSES_LX(NCLS, KERN, LN, fluid_args, cls_fn, __VA_ARGS__)
 
 template <typename T> struct EngineT : Engine {
     // particle arrays
@@ -62,6 +65,7 @@ template <typename T> struct EngineT : Engine {
     V4<T> *gradC = nullptr, *acc_visc = nullptr, *acc_surf = nullptr, *bmat = nullptr;
     T *drho = nullptr, *drho_old = nullptr;        // drho_old: rebuild scratch (sorted copy)
     uint32_t *id = nullptr, *key = nullptr, *rank = nullptr, *perm = nullptr;
+    uint32_t *fidx = nullptr, *fscan = nullptr;     // particle of each fluid rank; scan scratch
     // cell table + scan scratch
     uint32_t *starts = nullptr, *block_sums = nullptr;
     uint32_t *nbr = nullptr, *nbr_cnt = nullptr;   // neighbour lists (ELL per case) and counts
@@ -75,13 +79,15 @@ template <typename T> struct EngineT : Engine {
     // cases
     CaseDesc *d_desc = nullptr;
     CaseState *d_state = nullptr;
-    Tile *d_tiles = nullptr;
+    Tile *d_tiles = nullptr, *d_ftiles = nullptr;   // tiles over particles; over fluid ranks
     int *d_loop_flag = nullptr;
     double *d_read = nullptr;              // read-back buffer
     double *d_diag = nullptr;              // diagnostics partials + result
     void *arena = nullptr;
     int64_t n = 0, table_total = 0, n_tiles = 0, max_case_n = 0;
     int64_t cls_b[4] = {0, 0, 0, 0}, cls_n[4] = {0, 0, 0, 0};   // tile range of each class
+    int64_t cls_fb[4] = {0, 0, 0, 0}, cls_fn[4] = {0, 0, 0, 0}; // the same over fluid ranks
+    int64_t n_ftiles = 0;
     int ncases = 0, block = 128, lanes = 1;
     bool any_tvf = false;
     int loop_mode = SPHST_LOOP_GRAPH;
@@ -148,6 +154,7 @@ template <typename T> struct EngineT : Engine {
             n += r->n;
             table_total += d.table_size;
             n_tiles += (r->n + block - 1) / block;
+            n_ftiles += (r->n_fluid + block - 1) / block;
             max_case_n = std::max(max_case_n, r->n);
             any_tvf = any_tvf || d.tvf_on;
             if (d.nbr_mode == 0) {
@@ -167,7 +174,7 @@ template <typename T> struct EngineT : Engine {
             return SPHST_ERR_UNSUPPORTED;
         }
         // arena
-        const int64_t nb = (table_total + 1 + SCAN_ITEMS - 1) / SCAN_ITEMS;
+        const int64_t nb = std::max(table_total + 1, n + 1) / SCAN_ITEMS + 1;   // table or particle scan
         size_t off = 0;
         auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
         const size_t nn = (size_t)std::max<int64_t>(n, 1);
@@ -181,6 +188,8 @@ template <typename T> struct EngineT : Engine {
         size_t o_st = take((size_t)(table_total + 1) * 4), o_bs = take((size_t)nb * 4);
         size_t o_desc = take(sizeof(CaseDesc) * ncases), o_state = take(sizeof(CaseState) * ncases);
         size_t o_tiles = take(sizeof(Tile) * (size_t)std::max<int64_t>(n_tiles, 1));
+        size_t o_ftiles = take(sizeof(Tile) * (size_t)std::max<int64_t>(n_ftiles, 1));
+        size_t o_fidx = take(nn * 4), o_fscan = take((nn + 1) * 4);
         size_t o_flag = take(64);
         size_t o_read = take((size_t)std::max<int64_t>(max_case_n, 1) * 3 * sizeof(double));
         size_t o_nbr = take((size_t)std::max<int64_t>(nbr_total, 1) * 4), o_ncnt = take(nn * 4);
@@ -206,6 +215,8 @@ template <typename T> struct EngineT : Engine {
         starts = (uint32_t *)(b + o_st); block_sums = (uint32_t *)(b + o_bs);
         d_desc = (CaseDesc *)(b + o_desc); d_state = (CaseState *)(b + o_state);
         d_tiles = (Tile *)(b + o_tiles); d_loop_flag = (int *)(b + o_flag);
+        d_ftiles = (Tile *)(b + o_ftiles);
+        fidx = (uint32_t *)(b + o_fidx); fscan = (uint32_t *)(b + o_fscan);
         d_read = (double *)(b + o_read);
         nbr = (uint32_t *)(b + o_nbr);
         nbr_cnt = (uint32_t *)(b + o_ncnt);
@@ -233,6 +244,23 @@ template <typename T> struct EngineT : Engine {
         band_base[0] = 0;
         band_base[1] = np0;
         SPH_CK(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, stream));
+        // tiles over fluid ranks: case c's fluid particles hold the ranks
+        // after those of cases 0..c-1
+        std::vector<int64_t> fb(ncases + 1, 0);
+        for (int c = 0; c < ncases; ++c) fb[c + 1] = fb[c] + cases[c]->n_fluid;
+        std::vector<Tile> ftiles;
+        ftiles.reserve(n_ftiles);
+        for (int k = 0; k < 4; ++k) {
+            cls_fb[k] = (int64_t)ftiles.size();
+            for (int c = 0; c < ncases; ++c) {
+                if (tile_class(h_desc[c]) != k) continue;
+                for (int64_t s = fb[c]; s < fb[c + 1]; s += block)
+                    ftiles.push_back(Tile{c, (int32_t)std::min<int64_t>(block, fb[c + 1] - s), s});
+            }
+            cls_fn[k] = (int64_t)ftiles.size() - cls_fb[k];
+        }
+        if (!ftiles.empty())
+            SPH_CK(cudaMemcpyAsync(d_ftiles, ftiles.data(), sizeof(Tile) * ftiles.size(), cudaMemcpyHostToDevice, stream));
         SPH_CK(cudaMemcpyAsync(d_desc, h_desc.data(), sizeof(CaseDesc) * ncases, cudaMemcpyHostToDevice, stream));
         // fill each case
         for (int c = 0; c < ncases; ++c) {
@@ -301,6 +329,19 @@ template <typename T> struct EngineT : Engine {
 
     static int tile_class(const CaseDesc &d) { return (d.nbr_mode == 0 ? 0 : 2) + (d.dim == 3 ? 0 : 1); }
     SweepArgs sweep_args(int k) const { return SweepArgs{d_tiles, d_desc, d_state, starts, nbr, nbr_cnt, cls_b[k]}; }
+    SweepArgs fluid_args(int k) const {
+        return SweepArgs{d_ftiles, d_desc, d_state, starts, nbr, nbr_cnt, cls_fb[k], fidx};
+    }
+    // fluid ranks of the reordered particles (after the gather)
+    void launch_fluid_ranks() {
+        const int64_t np1 = n + 1;
+        const unsigned nbp = (unsigned)((np1 + SCAN_ITEMS - 1) / SCAN_ITEMS);
+        k_fluid_flag<T><<<(unsigned)((np1 + 255) / 256), 256, 0, stream>>>(n, snap, fscan);
+        k_scan_reduce<<<nbp, SCAN_T, 0, stream>>>(fscan, np1, block_sums);
+        k_scan_blocks<<<1, SCAN_T, 0, stream>>>(block_sums, nbp);
+        k_scan_apply<<<nbp, SCAN_T, 0, stream>>>(fscan, np1, block_sums);
+        k_fluid_scatter<T><<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(n, snap, fscan, fidx);
+    }
     int n_classes(int upto) const {
         int m = 0;
         for (int k = 0; k < upto; ++k) m += cls_n[k] > 0;
@@ -326,6 +367,7 @@ template <typename T> struct EngineT : Engine {
         k_cell_sort<<<(unsigned)((table_total + nthr - 1) / nthr), nthr, 0, stream>>>(table_total, starts, id, perm);
         k_gather<T><<<pgrid, nthr, 0, stream>>>(n, perm, pos, vel, drho, id, snap, vel_new, drho_old, rank);
         k_copy_back<T><<<pgrid, nthr, 0, stream>>>(n, snap, vel_new, drho_old, rank, pos, vel, drho, id);
+        launch_fluid_ranks();
         SPH_CLASSES(2, k_build_list, snap, nbr, nbr_cnt);
         if (SPHST_LIST_GEO) SPH_CLASSES(2, k_list_geo, snap, lgeo);
         SPH_CK(cudaMemsetAsync(band_count, 0, 2 * sizeof(uint32_t), stream));
@@ -340,8 +382,8 @@ template <typename T> struct EngineT : Engine {
         k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, h, use_handle);
         SPH_CLASSES_L(4, k_sweep_A, lanes, snap, drho, lgeo, gradC);
         SPH_CLASSES_L(2, k_sweep_S, surface_lanes(), band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
-        SPH_CLASSES_L(4, k_sweep_B, lanes, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo);
-        SPH_CLASSES_L(4, k_sweep_C, lanes, snap, vel_new, drho, vel, pos, lgeo);
+        SPH_CLASSES_LF(4, k_sweep_B, lanes, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo);
+        SPH_CLASSES_LF(4, k_sweep_C, lanes, snap, vel_new, drho, vel, pos, lgeo);
         SPH_CK(cudaGetLastError());
         return SPHST_OK;
     }
@@ -458,6 +500,7 @@ template <typename T> struct EngineT : Engine {
             k_gather<T><<<pgrid, nthr, 0, stream>>>(n, perm, pos, vel, drho, id, snap, vel_new, drho_old, rank);
             k_copy_back<T><<<pgrid, nthr, 0, stream>>>(n, snap, vel_new, drho_old, rank, pos, vel, drho, id);
         });
+        timed(0, 5, [&] { launch_fluid_ranks(); });
         timed(0, (SPHST_LIST_GEO ? 3 : 2) * nlist, [&] {
             SPH_CLASSES(2, k_build_list, snap, nbr, nbr_cnt);
             if (SPHST_LIST_GEO) SPH_CLASSES(2, k_list_geo, snap, lgeo);
@@ -474,8 +517,8 @@ template <typename T> struct EngineT : Engine {
             timed(6, nlist, [&] {
                 SPH_CLASSES_L(2, k_sweep_S, surface_lanes(), band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
             });
-            timed(4, ncls, [&] { SPH_CLASSES_L(4, k_sweep_B, lanes, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo); });
-            timed(5, ncls, [&] { SPH_CLASSES_L(4, k_sweep_C, lanes, snap, vel_new, drho, vel, pos, lgeo); });
+            timed(4, ncls, [&] { SPH_CLASSES_LF(4, k_sweep_B, lanes, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo); });
+            timed(5, ncls, [&] { SPH_CLASSES_LF(4, k_sweep_C, lanes, snap, vel_new, drho, vel, pos, lgeo); });
             if (rc) break;
             int flag = 0;
             cudaError_t e = cudaMemcpy(&flag, d_loop_flag, sizeof(int), cudaMemcpyDeviceToHost);

@@ -275,8 +275,9 @@ def test_profiled_launch_counts():
     S.destroy(h)
     for g in ("criterion", "sweep_A", "sweep_S", "sweep_B", "sweep_C"):
         assert prof[g][1] == n_sub, g
-    # keys, 3 scans, scatter, cell sort, gather, copy-back, list, band
-    assert prof["rebuild"][1] == 10
+    # keys, 3 scans, scatter, cell sort, gather, copy-back, fluid ranks (flag,
+    # 3 scans, scatter), list, band
+    assert prof["rebuild"][1] == 15
 
 
 @pytest.mark.parametrize("dim", [2, 3])
