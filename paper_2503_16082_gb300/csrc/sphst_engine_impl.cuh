@@ -21,12 +21,15 @@ enum ArrayId { A_POS = 0, A_VEL, A_DRHO, A_ID, A_GRADC, A_ACCV };
 
 // Tile classes: 0 = 3D list, 1 = 2D list, 2 = 3D cell walk, 3 = 2D cell walk.
 // SPH_CLASSES(NCLS, KERN, args...) launches KERN<T, D, LIST> over the tiles of
-// each non-empty class among the first NCLS (2: list classes only).
-#define SPH_CLASSES(NCLS, KERN, ...)                                                   \
+// each non-empty class among the first NCLS (2: list classes only);
+// SPH_CLASSES_F over the tiles of fluid ranks.
+#define SPH_CLASSES(NCLS, KERN, ...) SPH_CLASSES_X(NCLS, KERN, sweep_args, cls_n, __VA_ARGS__)
+#define SPH_CLASSES_F(NCLS, KERN, ...) SPH_CLASSES_X(NCLS, KERN, fluid_args, cls_fn, __VA_ARGS__)
+#define SPH_CLASSES_X(NCLS, KERN, ARGS, CNT, ...)                                      \
     for (int k_ = 0; k_ < (NCLS); ++k_) {                                              \
-        if (!cls_n[k_]) continue;                                                      \
-        const SweepArgs a_ = sweep_args(k_);                                           \
-        const unsigned g_ = (unsigned)cls_n[k_];                                       \
+        if (!CNT[k_]) continue;                                                        \
+        const SweepArgs a_ = ARGS(k_);                                                 \
+        const unsigned g_ = (unsigned)CNT[k_];                                         \
         switch (k_) {                                                                  \
         case 0: KERN<T, 3, true><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;    \
         case 1: KERN<T, 2, true><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;    \
@@ -372,8 +375,8 @@ template <typename T> struct EngineT : Engine {
         if (SPHST_LIST_GEO) SPH_CLASSES(2, k_list_geo, snap, lgeo);
         SPH_CK(cudaMemsetAsync(band_count, 0, 2 * sizeof(uint32_t), stream));
         SPH_CLASSES(2, k_band, snap, band, band_list + band_base[k_], band_count + k_);
-        if (any_tvf) SPH_CLASSES(4, k_sweep_M, snap, drho, bmat);
-        SPH_CLASSES(4, k_sweep_V, snap, drho, vel, bmat, acc_visc, pos);
+        if (any_tvf) SPH_CLASSES_F(4, k_sweep_M, snap, drho, bmat);
+        SPH_CLASSES_F(4, k_sweep_V, snap, drho, vel, bmat, acc_visc, pos);
         SPH_CK(cudaGetLastError());
         return SPHST_OK;
     }
@@ -508,8 +511,8 @@ template <typename T> struct EngineT : Engine {
             SPH_CLASSES(2, k_band, snap, band, band_list + band_base[k_], band_count + k_);
         });
         timed(1, any_tvf ? 2 * ncls : ncls, [&] {
-            if (any_tvf) SPH_CLASSES(4, k_sweep_M, snap, drho, bmat);
-            SPH_CLASSES(4, k_sweep_V, snap, drho, vel, bmat, acc_visc, pos);
+            if (any_tvf) SPH_CLASSES_F(4, k_sweep_M, snap, drho, bmat);
+            SPH_CLASSES_F(4, k_sweep_V, snap, drho, vel, bmat, acc_visc, pos);
         });
         for (;;) {
             timed(2, 1, [&] { k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, 0, 0); });

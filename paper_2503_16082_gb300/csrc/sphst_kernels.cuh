@@ -819,8 +819,8 @@ __global__ void k_copy_back(int64_t n, const V4<T> *pos_t, const V4<T> *vel_t, c
 
 // ---- fluid ranks: after the reorder, the sorted positions of the fluid
 // particles, walls left out (an exclusive scan of the fluid flags, then a
-// scatter).  Sweeps B and C run their tiles over these ranks, so no lane of
-// theirs idles on a wall particle (16% of the 3D drop, interleaved with the
+// scatter).  Sweeps M, V, B and C run their tiles over these ranks, so no
+// lane of theirs idles on a wall particle (16% of the 3D drop, interleaved with the
 // fluid near the walls by the Morton order).  Each case's fluid particles
 // take the ranks after the previous cases' ones, whose count is fixed.
 template <typename T>
@@ -1405,7 +1405,7 @@ struct SweepArgs {
 };
 
 // particle of tile position q: the position itself, or the fluid particle of
-// that rank
+// that rank (sweeps M, V, B and C)
 __device__ __forceinline__ int64_t particle_at(const SweepArgs &a, int64_t q) {
     return a.fidx ? (int64_t)a.fidx[q] : q;
 }
@@ -1560,7 +1560,7 @@ __global__ void SPH_SWEEP_BOUNDS k_sweep_M(SweepArgs a, const V4<T> *snap, const
     if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
     const CaseDesc &d = a.desc[t.c];
     if (!d.tvf_on) return;
-    const int64_t i = t.begin + threadIdx.x;
+    const int64_t i = particle_at(a, t.begin + threadIdx.x);
     sweep_M<LIST, T, D>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, bmat, &a.st[t.c].status);
 }
 
@@ -1570,7 +1570,7 @@ __global__ void SPH_SWEEP_BOUNDS k_sweep_V(SweepArgs a, const V4<T> *snap, const
     const Tile t = a.tiles[a.tile0 + blockIdx.x];
     if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
     const CaseDesc &d = a.desc[t.c];
-    const int64_t i = t.begin + threadIdx.x;
+    const int64_t i = particle_at(a, t.begin + threadIdx.x);
     sweep_V<LIST, T, D>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, vel, bmat, acc_visc, pos,
                         &a.st[t.c].status);
 }
