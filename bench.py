@@ -67,7 +67,8 @@ def recorded_traffic(summary: str, kernel: str):
     m = re.search(r"traffic_bytes_per_launch\[" + re.escape(kernel) + r"\]:\s*([0-9]+)", text)
     return int(m.group(1)) if m else None
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
-# algorithmic FP32 flops per neighbour pair of sweep B (derivation in the design doc):
+# algorithmic flops per neighbour pair, counted from the formulas (adds and
+# multiplies 1, fused multiply-adds 2, divisions and square roots 1):
 FP64_PEAK_TFLOPS = 1.25      # nominal FP64 (non-tensor) rate of a GB300
 FLOPS_PAIR_B = 59            # geometry + Riemann pressure, every pair (sweep B)
 FLOPS_PAIR_B_SURF = 110      # surface stress + penalty, pairs touching the interface (sweep S)
@@ -356,7 +357,7 @@ def run_reference(args, dist: Dist):
 
 # ------------------------------------------------------ batched and served
 def run_batch(args):
-    """Config 4: independent 2D/3D droplet cases advanced together in one
+    """The batched workload: independent 2D/3D droplet cases advanced together in one
     engine (one graph per advection step), against the same cases stepped
     one at a time through the single-case path."""
     import torch
@@ -415,7 +416,7 @@ def run_batch(args):
 
 
 def run_serve(args):
-    """Config 5: Poisson arrivals of droplet cases into the continuous-batching
+    """The served workload: Poisson arrivals of droplet cases into the continuous-batching
     server; p50/p99 time from submission to result."""
     import torch
 
