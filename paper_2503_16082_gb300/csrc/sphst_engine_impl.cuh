@@ -343,7 +343,7 @@ template <typename T> struct EngineT : Engine {
         k_scan_reduce<<<nbp, SCAN_T, 0, stream>>>(fscan, np1, block_sums);
         k_scan_blocks<<<1, SCAN_T, 0, stream>>>(block_sums, nbp);
         k_scan_apply<<<nbp, SCAN_T, 0, stream>>>(fscan, np1, block_sums);
-        k_fluid_scatter<T><<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(n, snap, fscan, fidx);
+        k_fluid_scatter<T><<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(n, snap, fscan, fidx, gradC, nbr_cnt);
     }
     int n_classes(int upto) const {
         int m = 0;
@@ -371,10 +371,10 @@ template <typename T> struct EngineT : Engine {
         k_gather<T><<<pgrid, nthr, 0, stream>>>(n, perm, pos, vel, drho, id, snap, vel_new, drho_old, rank);
         k_copy_back<T><<<pgrid, nthr, 0, stream>>>(n, snap, vel_new, drho_old, rank, pos, vel, drho, id);
         launch_fluid_ranks();
-        SPH_CLASSES(2, k_build_list, snap, nbr, nbr_cnt);
+        SPH_CLASSES_F(2, k_build_list, snap, nbr, nbr_cnt);
         if (SPHST_LIST_GEO) SPH_CLASSES(2, k_list_geo, snap, lgeo);
         SPH_CK(cudaMemsetAsync(band_count, 0, 2 * sizeof(uint32_t), stream));
-        SPH_CLASSES(2, k_band, snap, band, band_list + band_base[k_], band_count + k_);
+        SPH_CLASSES_F(2, k_band, snap, band, band_list + band_base[k_], band_count + k_);
         if (any_tvf) SPH_CLASSES_F(4, k_sweep_M, snap, drho, bmat);
         SPH_CLASSES_F(4, k_sweep_V, snap, drho, vel, bmat, acc_visc, pos);
         SPH_CK(cudaGetLastError());
@@ -383,7 +383,7 @@ template <typename T> struct EngineT : Engine {
 
     int launch_body(cudaGraphConditionalHandle h, int use_handle) {
         k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, h, use_handle);
-        SPH_CLASSES_L(4, k_sweep_A, lanes, snap, drho, lgeo, gradC);
+        SPH_CLASSES_LF(4, k_sweep_A, lanes, snap, drho, lgeo, gradC);
         SPH_CLASSES_L(2, k_sweep_S, surface_lanes(), band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
         SPH_CLASSES_LF(4, k_sweep_B, lanes, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo);
         SPH_CLASSES_LF(4, k_sweep_C, lanes, snap, vel_new, drho, vel, pos, lgeo);
@@ -505,10 +505,10 @@ template <typename T> struct EngineT : Engine {
         });
         timed(0, 5, [&] { launch_fluid_ranks(); });
         timed(0, (SPHST_LIST_GEO ? 3 : 2) * nlist, [&] {
-            SPH_CLASSES(2, k_build_list, snap, nbr, nbr_cnt);
+            SPH_CLASSES_F(2, k_build_list, snap, nbr, nbr_cnt);
             if (SPHST_LIST_GEO) SPH_CLASSES(2, k_list_geo, snap, lgeo);
             cudaMemsetAsync(band_count, 0, 2 * sizeof(uint32_t), stream);
-            SPH_CLASSES(2, k_band, snap, band, band_list + band_base[k_], band_count + k_);
+            SPH_CLASSES_F(2, k_band, snap, band, band_list + band_base[k_], band_count + k_);
         });
         timed(1, any_tvf ? 2 * ncls : ncls, [&] {
             if (any_tvf) SPH_CLASSES_F(4, k_sweep_M, snap, drho, bmat);
@@ -516,7 +516,7 @@ template <typename T> struct EngineT : Engine {
         });
         for (;;) {
             timed(2, 1, [&] { k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, 0, 0); });
-            timed(3, ncls, [&] { SPH_CLASSES_L(4, k_sweep_A, lanes, snap, drho, lgeo, gradC); });
+            timed(3, ncls, [&] { SPH_CLASSES_LF(4, k_sweep_A, lanes, snap, drho, lgeo, gradC); });
             timed(6, nlist, [&] {
                 SPH_CLASSES_L(2, k_sweep_S, surface_lanes(), band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
             });

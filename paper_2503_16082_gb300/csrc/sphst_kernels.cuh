@@ -310,18 +310,33 @@ __device__ __forceinline__ bool walk(const CaseDesc &d, const CasePhys<T> &cp,
     const int cx = cell_x<D>(pki), cy = cell_y<D>(pki), cz = cell_z<D>(pki);
     const uint32_t toff = (uint32_t)d.table_off;
     const T cs = cp.cs, R2 = cp.four_h2;
+    // Cells that lie wholly 2h or farther from s_i are skipped: per axis the
+    // gap from s_i to the near face of the cell at offset -1 / +1 (0 for the
+    // own column), shrunk by 1e-4 of the cell width so that offsets rounded
+    // onto a face stay covered; a skipped cell holds no pair with r < 2h, so
+    // the walk visits the same pairs (about 21 of the 27 cells in 3D)
+    const T margin = T(1e-4) * cs;
+    const auto gap2 = [&](T s, int o) {
+        T g = o < 0 ? s - margin : (o > 0 ? (cs - s) - margin : T(0));
+        g = g > T(0) ? g : T(0);
+        return g * g;
+    };
     bool coincident = false;
     for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz) {
         int nz = cz + oz;
         if (D == 3 && !wrap_cell(d, 2, nz)) continue;
+        const T gz2 = D == 3 ? gap2(si.z, oz) : T(0);
         const T sz = D == 3 ? sub_rn(si.z, mul_rn(T(oz), cs)) : T(0);
         for (int oy = -1; oy <= 1; ++oy) {
             int ny = cy + oy;
             if (!wrap_cell(d, 1, ny)) continue;
+            const T gyz2 = gz2 + gap2(si.y, oy);
+            if (gyz2 >= R2) continue;
             const T sy = sub_rn(si.y, mul_rn(T(oy), cs));
             for (int ox = -1; ox <= 1; ++ox) {
                 int nx = cx + ox;
                 if (!wrap_cell(d, 0, nx)) continue;
+                if (gyz2 + gap2(si.x, ox) >= R2) continue;
                 const T sx = sub_rn(si.x, mul_rn(T(ox), cs));
                 const uint32_t m = toff + morton<D>(nx, ny, nz);
                 const uint32_t b = __ldg(starts + m), e = __ldg(starts + m + 1);
@@ -819,8 +834,8 @@ __global__ void k_copy_back(int64_t n, const V4<T> *pos_t, const V4<T> *vel_t, c
 
 // ---- fluid ranks: after the reorder, the sorted positions of the fluid
 // particles, walls left out (an exclusive scan of the fluid flags, then a
-// scatter).  Sweeps M, V, B and C run their tiles over these ranks, so no
-// lane of theirs idles on a wall particle (16% of the 3D drop, interleaved with the
+// scatter).  The list build, the band and sweeps M, V, A, B and C run their
+// tiles over these ranks, so no lane of theirs idles on a wall particle (16% of the 3D drop, interleaved with the
 // fluid near the walls by the Morton order).  Each case's fluid particles
 // take the ranks after the previous cases' ones, whose count is fixed.
 template <typename T>
@@ -830,11 +845,19 @@ __global__ void k_fluid_flag(int64_t n, const V4<T> *snap, uint32_t *flag) {
     flag[i] = (i < n && phase_of(w_bits(snap[i].w)) != PH_WALL) ? 1u : 0u;
 }
 
+// Wall slots get their fixed values here, since no sweep visits them: a zero
+// colour gradient and an empty neighbour list.
 template <typename T>
-__global__ void k_fluid_scatter(int64_t n, const V4<T> *snap, const uint32_t *rank, uint32_t *fidx) {
+__global__ void k_fluid_scatter(int64_t n, const V4<T> *snap, const uint32_t *rank, uint32_t *fidx,
+                                V4<T> *gradC, uint32_t *cnt) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    if (phase_of(w_bits(snap[i].w)) != PH_WALL) fidx[rank[i]] = (uint32_t)i;
+    if (phase_of(w_bits(snap[i].w)) != PH_WALL) {
+        fidx[rank[i]] = (uint32_t)i;
+    } else {
+        gradC[i] = V4<T>{T(0), T(0), T(0), T(0)};
+        cnt[i] = 0u;
+    }
 }
 
 // ================================================================ time step
@@ -1405,7 +1428,7 @@ struct SweepArgs {
 };
 
 // particle of tile position q: the position itself, or the fluid particle of
-// that rank (sweeps M, V, B and C)
+// that rank (the list build, the band, sweeps M, V, A, B and C)
 __device__ __forceinline__ int64_t particle_at(const SweepArgs &a, int64_t q) {
     return a.fidx ? (int64_t)a.fidx[q] : q;
 }
@@ -1488,7 +1511,7 @@ __global__ void __launch_bounds__(256) k_band(SweepArgs a, const V4<T> *snap, ui
                                               uint64_t *blist, uint32_t *bcount) {
     const Tile t = a.tiles[a.tile0 + blockIdx.x];
     const bool live = (int)threadIdx.x < t.n && a.st[t.c].active;
-    const int64_t i = t.begin + threadIdx.x;
+    const int64_t i = live ? particle_at(a, t.begin + threadIdx.x) : 0;
     bool b = false;
     if (live) {
         const CaseDesc &d = a.desc[t.c];
@@ -1516,7 +1539,7 @@ __global__ void __launch_bounds__(256) k_build_list(SweepArgs a, const V4<T> *sn
     const Tile t = a.tiles[a.tile0 + blockIdx.x];
     if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
     const CaseDesc &d = a.desc[t.c];
-    const int64_t i = t.begin + threadIdx.x;
+    const int64_t i = particle_at(a, t.begin + threadIdx.x);
     build_list<T, D>(d, phys<T>(d), i, a.starts, snap, nbr, cnt, &a.st[t.c].status);
 }
 
@@ -1591,7 +1614,7 @@ __global__ void SPH_SWEEPAS_BOUNDS k_sweep_A(SweepArgs a, const V4<T> *snap, con
     const int li = local_index<L>();
     if (li >= t.n || !a.st[t.c].active) return;
     const CaseDesc &d = a.desc[t.c];
-    const int64_t i = t.begin + li;
+    const int64_t i = particle_at(a, t.begin + li);
     sweep_A<LIST, T, D, L>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, lgeo, gradC, threadIdx.x % L);
 }
 
