@@ -310,33 +310,18 @@ __device__ __forceinline__ bool walk(const CaseDesc &d, const CasePhys<T> &cp,
     const int cx = cell_x<D>(pki), cy = cell_y<D>(pki), cz = cell_z<D>(pki);
     const uint32_t toff = (uint32_t)d.table_off;
     const T cs = cp.cs, R2 = cp.four_h2;
-    // Cells that lie wholly 2h or farther from s_i are skipped: per axis the
-    // gap from s_i to the near face of the cell at offset -1 / +1 (0 for the
-    // own column), shrunk by 1e-4 of the cell width so that offsets rounded
-    // onto a face stay covered; a skipped cell holds no pair with r < 2h, so
-    // the walk visits the same pairs (about 21 of the 27 cells in 3D)
-    const T margin = T(1e-4) * cs;
-    const auto gap2 = [&](T s, int o) {
-        T g = o < 0 ? s - margin : (o > 0 ? (cs - s) - margin : T(0));
-        g = g > T(0) ? g : T(0);
-        return g * g;
-    };
     bool coincident = false;
     for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz) {
         int nz = cz + oz;
         if (D == 3 && !wrap_cell(d, 2, nz)) continue;
-        const T gz2 = D == 3 ? gap2(si.z, oz) : T(0);
         const T sz = D == 3 ? sub_rn(si.z, mul_rn(T(oz), cs)) : T(0);
         for (int oy = -1; oy <= 1; ++oy) {
             int ny = cy + oy;
             if (!wrap_cell(d, 1, ny)) continue;
-            const T gyz2 = gz2 + gap2(si.y, oy);
-            if (gyz2 >= R2) continue;
             const T sy = sub_rn(si.y, mul_rn(T(oy), cs));
             for (int ox = -1; ox <= 1; ++ox) {
                 int nx = cx + ox;
                 if (!wrap_cell(d, 0, nx)) continue;
-                if (gyz2 + gap2(si.x, ox) >= R2) continue;
                 const T sx = sub_rn(si.x, mul_rn(T(ox), cs));
                 const uint32_t m = toff + morton<D>(nx, ny, nz);
                 const uint32_t b = __ldg(starts + m), e = __ldg(starts + m + 1);
@@ -835,9 +820,10 @@ __global__ void k_copy_back(int64_t n, const V4<T> *pos_t, const V4<T> *vel_t, c
 // ---- fluid ranks: after the reorder, the sorted positions of the fluid
 // particles, walls left out (an exclusive scan of the fluid flags, then a
 // scatter).  The list build, the band and sweeps M, V, A, B and C run their
-// tiles over these ranks, so no lane of theirs idles on a wall particle (16% of the 3D drop, interleaved with the
-// fluid near the walls by the Morton order).  Each case's fluid particles
-// take the ranks after the previous cases' ones, whose count is fixed.
+// tiles over these ranks, so no lane of theirs idles on a wall particle (16%
+// of the 3D drop, interleaved with the fluid near the walls by the Morton
+// order).  Each case's fluid particles take the ranks after the previous
+// cases' ones, whose count is fixed.
 template <typename T>
 __global__ void k_fluid_flag(int64_t n, const V4<T> *snap, uint32_t *flag) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
