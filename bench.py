@@ -401,6 +401,21 @@ def run_batch(args):
         psecs += time.perf_counter() - t0
         punits += c.n_fluid * (S.case_info(h)["n_sub"] - s0)
         S.destroy(h)
+    # the oracle as it stands on a bounded sample of the same cases (one
+    # advection-step set-up + a few substeps each, about 10 s of host time)
+    cpu = None
+    if not args.no_cpu_baseline:
+        cu, cs, used, threads = 0.0, 0.0, 0, 0
+        for c in cases:
+            _, secs, threads, nsub = oracle_sample(c)
+            cu += c.n_fluid * nsub
+            cs += secs
+            used += 1
+            if cs > 10.0 or used >= 16:
+                break
+        cpu = {"value": round(cu / cs, 1), "unit": METRIC, "cores": threads, "kind": "oracle",
+               "sample": f"the batch's first {used} cases, each one advection-step set-up + "
+                         f"{SAMPLE_SUBSTEPS} acoustic substeps of the FP64 oracle, {cs:.1f} s"}
     line = {"metric": METRIC, "mode": "batch", "value": round(units / dt, 1), "unit": METRIC,
             "cases": len(cases), "particles": int(sum(c.n for c in cases)),
             "fluid_particles": int(sum(c.n_fluid for c in cases)), "steps": args.steps,
@@ -409,7 +424,7 @@ def run_batch(args):
             "failed_specs": [dict(dim=sp.dim, n=c.n, sigma=round(sp.sigma, 3), shape=sp.shape)
                              for sp, c, x in zip(specs, cases, statuses) if x][:8],
             "plain_single_case": {"value": round(punits / psecs, 1), "cases_sampled": k},
-            "speedup_vs_plain": round((units / dt) / (punits / psecs), 2),
+            "speedup_vs_plain": round((units / dt) / (punits / psecs), 2), "cpu_baseline": cpu,
             "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
             "config": {"workload": "batch_cases seed 20250320", "step": "one advection step of every case"}}
     print(json.dumps(line), flush=True)
