@@ -540,7 +540,7 @@ def main():
     dtype = "f32" if args.precision == 32 else "f64"
 
     if args.impl == "reference":
-        dist = Dist("gloo") if ws > 1 else Dist("gloo")
+        dist = Dist("gloo")                    # the oracle runs on the host: no NCCL needed
         res = run_reference(args, dist)
         dist.close()
         if res is None:
