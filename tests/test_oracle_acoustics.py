@@ -1,0 +1,107 @@
+"""Linear acoustics pins the oracle's pressure force (Eqs. 7-12), continuity
+(Eq. 6), equation of state and time integration together, against a closed
+form.  A small density wave rho = rho0 (1 + eps cos kx) at rest in a
+periodic lattice is a standing wave of angular frequency c k.  On a lattice
+with a fixed h / dx the discrete gradient of the scheme, sum_j V_j (.)
+grad_i W_ij, equals m times the true one for long waves, with
+m = -sum_j V_j x_ij^2 W'(r_ij) / r_ij (one lattice sum of the kernel), and
+both the momentum and the continuity equation carry it: the period tends to
+2 pi / (c0 k m) as the wave is resolved by more particles.  A factor lost or
+doubled in either equation, a wrong sound speed or a wrong update order moves
+it by percents or tens of percents."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+
+def fit_period(t, s, guess):
+    """Period of s ~ c + exp(-l t) (a cos wt + b sin wt): a scan over w near
+    2 pi / guess (l and a, b, c by least squares), then a simplex refinement."""
+    from scipy.optimize import minimize
+
+    t, s = np.asarray(t), np.asarray(s)
+
+    def resid(x):
+        w, lam = x
+        e = np.exp(-lam * t)
+        A = np.stack([np.ones_like(t), e * np.cos(w * t), e * np.sin(w * t)], axis=1)
+        return float(((A @ np.linalg.lstsq(A, s, rcond=None)[0] - s) ** 2).sum())
+
+    w0 = 2.0 * math.pi / guess
+    best = min(((resid((w, l)), (w, l)) for w in np.linspace(0.5 * w0, 1.5 * w0, 201)
+                for l in np.linspace(0.0, 0.5 * w0, 11)), key=lambda z: z[0])
+    x = minimize(resid, np.array(best[1]), method="Nelder-Mead",
+                 options={"xatol": 1e-9 * w0, "fatol": 1e-16, "maxiter": 2000}).x
+    return 2.0 * math.pi / x[0]
+
+
+def wendland_dW(dim, h, r):
+    """W'(r) of the Wendland C2 kernel (normalised; alpha_2 = 7/(4 pi h^2),
+    alpha_3 = 21/(16 pi h^3))."""
+    a = 7.0 / (4.0 * math.pi * h * h) if dim == 2 else 21.0 / (16.0 * math.pi * h ** 3)
+    q = r / h
+    return -5.0 * a * q * (1.0 - q / 2.0) ** 3 / h if q < 2.0 else 0.0
+
+
+def lattice_gradient_factor(dim, h_over_dx=1.3):
+    m = 0.0
+    for off in itertools.product(range(-3, 4), repeat=dim):
+        r = math.sqrt(sum(o * o for o in off))
+        if 0.0 < r < 2.0 * h_over_dx:
+            m -= off[0] * off[0] / r * wendland_dW(dim, h_over_dx, r)
+    return m
+
+
+def standing_wave_period(dim, nx, n_side=8, eps=1e-3, c0=10.0, n_adv=40):
+    dx = 1.0 / nx
+    axes = [(np.arange(nx) + 0.5) * dx] + [(np.arange(n_side) + 0.5) * dx] * (dim - 1)
+    grid = np.meshgrid(*axes, indexing="ij")
+    pos = np.zeros((grid[0].size, 3))
+    for a in range(dim):
+        pos[:, a] = grid[a].ravel()
+    k = 2.0 * math.pi
+    rho = 1.0 + eps * np.cos(k * pos[:, 0])
+    vel = np.zeros_like(pos)
+    kind = np.zeros(len(pos), dtype=np.int32)
+    hi = (1.0, n_side * dx, n_side * dx if dim == 3 else 0.0)
+    # the viscosity only sets the advection step (Eq. 16: 0.1 rho h^2 / eta),
+    # so that about 20 samples fall in one period
+    eta = 0.03 * (32.0 / nx) ** 2
+    P = oracle.make_params(dim, dx, 1.3 * dx, c0, 0.0, rho0=(1.0, 1.0), eta=(eta, eta), n=len(pos),
+                           periodic=(1 << dim) - 1, box_lo=(0.0, 0.0, 0.0), box_hi=hi)
+    ts, amp, t = [0.0], [eps], 0.0
+    for _ in range(n_adv):
+        pos, vel, rho, info, _, _ = oracle.run(P, pos, vel, rho, kind, 1)
+        assert info["status"] == 0
+        t += info["t"]
+        ts.append(t)
+        amp.append(2.0 * np.mean((rho - 1.0) * np.cos(k * pos[:, 0])))
+    exact = 1.0 / c0                              # 2 pi / (c0 k) with k = 2 pi
+    return fit_period(ts, amp, exact) / exact
+
+
+def test_lattice_gradient_factor_is_near_one():
+    # a sanity bound on the lattice sum itself: the continuous integral of
+    # x^2 W'(r)/r gives exactly 1
+    assert lattice_gradient_factor(2) == pytest.approx(0.9739, abs=2e-4)
+    assert lattice_gradient_factor(3) == pytest.approx(0.9789, abs=2e-4)
+
+
+def test_standing_wave_period_2d():
+    want = 1.0 / lattice_gradient_factor(2)          # 1.0268
+    got64 = standing_wave_period(2, 64)
+    got32 = standing_wave_period(2, 32)
+    assert got64 == pytest.approx(want, rel=2e-3)
+    # and the error shrinks with resolution towards that limit
+    assert abs(got64 - want) < abs(got32 - want)
+    assert abs(got32 - 1.0) > 0.02                  # far from the continuum speed: m matters
+
+
+@pytest.mark.slow
+def test_standing_wave_period_3d():
+    want = 1.0 / lattice_gradient_factor(3)          # 1.0216
+    assert standing_wave_period(3, 48) == pytest.approx(want, rel=3e-3)

@@ -7,7 +7,8 @@ The mistakes: a wrong kernel normalisation or derivative sign, a flipped
 pressure force, the neighbour's stress dropped from Eq. 26, the colour
 weight phi_i replaced by phi_j (Eq. 22), an arithmetic instead of a
 harmonic pair viscosity (Eq. 13), the pressure difference of U* (Eq. 9)
-reversed, the density update reversed (Eq. 6).  An unmodified copy passes
+reversed, the density update reversed (Eq. 6), the factor 2 of Eq. 6 dropped
+(only the acoustic standing wave catches that one).  An unmodified copy passes
 the same harness."""
 import os
 import subprocess
@@ -19,7 +20,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "sph_oracle.c")
 PINS = ["test_oracle_kernel.py", "test_oracle_neighbors.py", "test_oracle_riemann.py",
         "test_oracle_invariants.py", "test_oracle_dynamics.py", "test_oracle_periodic.py",
-        "test_oracle_reading_flags.py", "test_oracle_weights.py", "test_golden.py"]
+        "test_oracle_reading_flags.py", "test_oracle_weights.py", "test_oracle_acoustics.py", "test_golden.py"]
 
 MUTANTS = {
     "kernel normalisation": ("return dim == 2 ? 7.0 / (4.0 * ORA_PI * h * h)",
@@ -37,6 +38,7 @@ MUTANTS = {
     "U* pressure difference reversed": ("return (zl * L.U + zr * R.U + L.p - R.p) / (zl + zr);",
                                         "return (zl * L.U + zr * R.U - L.p + R.p) / (zl + zr);"),
     "density update reversed": ("rho[i] += dt * drho[i];", "rho[i] -= dt * drho[i];"),
+    "continuity factor 2 dropped": ("            s *= 2.0 * rho_i;", "            s *= rho_i;"),
 }
 
 
