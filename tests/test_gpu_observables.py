@@ -161,3 +161,45 @@ def test_impact_at_highest_reynolds_and_weber_stays_finite():
     assert info["status"] == 0 and dg["n_nonfinite"] == 0
     # the drop has hit the wall and spread beyond its initial radius
     assert np.sqrt(((pos[ph == 0, :2] - 4.0) ** 2).sum(1)).max() > 0.6
+
+
+def lattice_gradient_factor_2d(h_over_dx=1.3):
+    # m = -sum_j V_j x_ij^2 W'(r_ij) / r_ij over the lattice (Wendland C2)
+    a = 7.0 / (4.0 * math.pi * h_over_dx ** 2)
+    m = 0.0
+    for i in range(-3, 4):
+        for j in range(-3, 4):
+            r = math.hypot(i, j)
+            q = r / h_over_dx
+            if 0.0 < r and q < 2.0:
+                m += i * i / r * 5.0 * a * q * (1.0 - q / 2.0) ** 3 / h_over_dx
+    return m
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_standing_sound_wave_period(precision):
+    # a small density wave at rest in a periodic lattice: the period of the
+    # standing wave is 2 pi / (c0 k m), m the lattice factor of the discrete
+    # gradient, to O((k h)^2) (0.1% at 64 particles per wavelength)
+    nx, ny, eps, c0 = 64, 8, 1e-3, 10.0
+    dx = 1.0 / nx
+    pos = sphcases.lattice([0.0, 0.0], [1.0, ny * dx], dx)
+    k = 2.0 * math.pi
+    rho = 1.0 + eps * np.cos(k * pos[:, 0])
+    eta = 0.03 * (32.0 / nx) ** 2                   # sets the advection step only (Eq. 16)
+    case = sphcases.Case(name="sound", dim=2, lo=[0.0, 0.0], hi=[1.0, ny * dx], dx=dx, gamma=0.0, c0=c0,
+                         h_factor=1.3, xi=-1.0, periodic=3,
+                         phases=[sphcases.Phase("fluid", pos, rho0=1.0, eta=eta, rho=rho)])
+    h = S.case_from_spec(case, precision=precision)
+    ts, amp = [0.0], [eps]
+    try:
+        for _ in range(40):
+            info = S.step(h, 1)
+            p = S.read_fields(h, S.FIELD_POS, 2)
+            r = S.read_fields(h, S.FIELD_RHO, 2)
+            ts.append(info["t"])
+            amp.append(2.0 * np.mean((r - 1.0) * np.cos(k * p[:, 0])))
+    finally:
+        S.destroy(h)
+    ratio = ob.fit_period(ts, amp, 1.0 / c0) * c0
+    assert ratio == pytest.approx(1.0 / lattice_gradient_factor_2d(), rel=3e-3)
