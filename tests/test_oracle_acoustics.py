@@ -8,7 +8,13 @@ m = -sum_j V_j x_ij^2 W'(r_ij) / r_ij (one lattice sum of the kernel), and
 both the momentum and the continuity equation carry it: the period tends to
 2 pi / (c0 k m) as the wave is resolved by more particles.  A factor lost or
 doubled in either equation, a wrong sound speed or a wrong update order moves
-it by percents or tens of percents."""
+it by percents or tens of percents.
+
+Between two walls (periodic across them) the lowest mode cos(pi x / L) has
+the period 2 L / (c0 m) when the walls reflect sound as rigid boundaries at
+the box's faces: this pins the wall reading of the pressure and continuity
+terms (mirror state, wall volume dp^d, v* = v_w), which the paper leaves
+open."""
 import itertools
 import math
 
@@ -16,6 +22,7 @@ import numpy as np
 import pytest
 
 import oracle
+import sphcases
 
 
 def fit_period(t, s, guess):
@@ -105,3 +112,35 @@ def test_standing_wave_period_2d():
 def test_standing_wave_period_3d():
     want = 1.0 / lattice_gradient_factor(3)          # 1.0216
     assert standing_wave_period(3, 48) == pytest.approx(want, rel=3e-3)
+
+
+def box_mode_period(nx, n_side=8, eps=1e-3, c0=10.0, n_adv=60):
+    dx = 1.0 / nx
+    lo, hi = [0.0, 0.0], [1.0, n_side * dx]
+    p = sphcases.lattice(lo, hi, dx)
+    k = math.pi
+    eta = 0.03 * (32.0 / nx) ** 2
+    case = sphcases.Case(name="box_mode", dim=2, lo=lo, hi=hi, dx=dx, gamma=0.0, c0=c0, h_factor=1.3,
+                         xi=-1.0, periodic=2,
+                         phases=[sphcases.Phase("fluid", p, rho0=1.0, eta=eta, rho=1.0 + eps * np.cos(k * p[:, 0])),
+                                 sphcases.Phase("wall", sphcases.wall_shell(lo, hi, dx, sides=[0]))])
+    pos, vel, rho, kind = case.flat()
+    P = oracle.params_for_case(case)
+    fl = kind < 2
+    ts, amp, t = [0.0], [eps], 0.0
+    for _ in range(n_adv):
+        pos, vel, rho, info, _, _ = oracle.run(P, pos, vel, rho, kind, 1)
+        assert info["status"] == 0
+        t += info["t"]
+        ts.append(t)
+        amp.append(2.0 * np.mean((rho[fl] - 1.0) * np.cos(k * pos[fl, 0])))
+    exact = 2.0 / c0                              # 2 L / c0 with L = 1
+    return fit_period(ts, amp, exact) / exact
+
+
+def test_box_mode_between_walls():
+    want = 1.0 / lattice_gradient_factor(2)
+    got64 = box_mode_period(64)
+    got32 = box_mode_period(32)
+    assert got64 == pytest.approx(want, rel=1e-3)     # measured 1.02704 against 1.02678
+    assert abs(got64 - want) < abs(got32 - want)

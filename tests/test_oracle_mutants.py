@@ -8,7 +8,8 @@ pressure force, the neighbour's stress dropped from Eq. 26, the colour
 weight phi_i replaced by phi_j (Eq. 22), an arithmetic instead of a
 harmonic pair viscosity (Eq. 13), the pressure difference of U* (Eq. 9)
 reversed, the density update reversed (Eq. 6), the factor 2 of Eq. 6 dropped
-(only the acoustic standing wave catches that one).  An unmodified copy passes
+(only the acoustic standing wave catches that one), the wall's mirror
+pressure dropped, the wall volume doubled.  An unmodified copy passes
 the same harness."""
 import os
 import subprocess
@@ -39,6 +40,10 @@ MUTANTS = {
                                         "return (zl * L.U + zr * R.U - L.p + R.p) / (zl + zr);"),
     "density update reversed": ("rho[i] += dt * drho[i];", "rho[i] -= dt * drho[i];"),
     "continuity factor 2 dropped": ("            s *= 2.0 * rho_i;", "            s *= rho_i;"),
+    "wall mirror pressure dropped": ("R.p = p_i; R.c = c0;\n                    pbar = pair_pbar(rho_i, p_i, rho_i, p_i);",
+                                     "R.p = 0.0; R.c = c0;\n                    pbar = pair_pbar(rho_i, p_i, rho_i, 0.0);"),
+    "wall volume doubled": ("return P->dim == 2 ? P->dx * P->dx : P->dx * P->dx * P->dx;",
+                            "return P->dim == 2 ? 2.0 * P->dx * P->dx : 2.0 * P->dx * P->dx * P->dx;"),
 }
 
 
