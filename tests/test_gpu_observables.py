@@ -203,3 +203,33 @@ def test_standing_sound_wave_period(precision):
         S.destroy(h)
     ratio = ob.fit_period(ts, amp, 1.0 / c0) * c0
     assert ratio == pytest.approx(1.0 / lattice_gradient_factor_2d(), rel=3e-3)
+
+
+def test_box_mode_between_walls_period():
+    # the lowest acoustic mode between two walls (periodic across them) has
+    # the rigid-wall period 2 L / (c0 m) on the GPU as in the oracle
+    nx, ny, eps, c0 = 64, 8, 1e-3, 10.0
+    dx = 1.0 / nx
+    lo, hi = [0.0, 0.0], [1.0, ny * dx]
+    pos = sphcases.lattice(lo, hi, dx)
+    k = math.pi
+    eta = 0.03 * (32.0 / nx) ** 2
+    case = sphcases.Case(name="box_mode", dim=2, lo=lo, hi=hi, dx=dx, gamma=0.0, c0=c0, h_factor=1.3,
+                         xi=-1.0, periodic=2,
+                         phases=[sphcases.Phase("fluid", pos, rho0=1.0, eta=eta, rho=1.0 + eps * np.cos(k * pos[:, 0])),
+                                 sphcases.Phase("wall", sphcases.wall_shell(lo, hi, dx, sides=[0]))])
+    h = S.case_from_spec(case, precision=64)
+    ph = S.read_fields(h, S.FIELD_PHASE, 2)
+    fl = ph == 0
+    ts, amp = [0.0], [eps]
+    try:
+        for _ in range(60):
+            info = S.step(h, 1)
+            p = S.read_fields(h, S.FIELD_POS, 2)
+            r = S.read_fields(h, S.FIELD_RHO, 2)
+            ts.append(info["t"])
+            amp.append(2.0 * np.mean((r[fl] - 1.0) * np.cos(k * p[fl, 0])))
+    finally:
+        S.destroy(h)
+    ratio = ob.fit_period(ts, amp, 2.0 / c0) * c0 / 2.0
+    assert ratio == pytest.approx(1.0 / lattice_gradient_factor_2d(), rel=1e-3)
