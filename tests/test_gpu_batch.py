@@ -23,8 +23,8 @@ def specs():
     return out
 
 
-def alone(spec, n_adv, precision=32):
-    h = S.case_from_spec(spec, precision=precision)
+def alone(spec, n_adv, precision=32, **kw):
+    h = S.case_from_spec(spec, precision=precision, **kw)
     S.step(h, n_adv)
     res = [S.read_fields(h, f, spec.dim) for f in FIELDS], S.case_info(h)
     S.destroy(h)
@@ -35,12 +35,14 @@ def fields_of(h, spec):
     return [S.read_fields(h, f, spec.dim) for f in FIELDS]
 
 
-@pytest.mark.parametrize("precision", [32, 64])
-def test_batch_equals_alone(precision):
+@pytest.mark.parametrize("precision,lanes", [(32, 1), (64, 1), (32, 4)])
+def test_batch_equals_alone(precision, lanes):
+    # with L lanes per particle too: each particle's partial sums and their
+    # reduction are the same alone and in the batch
     sp = specs()
-    ref = [alone(s, 2, precision) for s in sp]
+    ref = [alone(s, 2, precision, lanes=lanes) for s in sp]
     b = S.batch_create(precision)
-    hs = [S.case_from_spec(s, precision=precision) for s in sp]
+    hs = [S.case_from_spec(s, precision=precision, lanes=lanes) for s in sp]
     for h in hs:
         S.batch_add(b, h)
     S.batch_step(b, 1)
