@@ -1151,8 +1151,10 @@ __device__ __forceinline__ void sweep_A(const CaseDesc &d, const CasePhys<T> &cp
 // interface band (band[i]: i or one of its neighbours has neighbours of the
 // other fluid; elsewhere grad C = 0 for i and all its neighbours and every
 // surface term is zero).  B then runs the pressure sum over all neighbours and
-// adds the stored surface sum.  Both sums keep their order, so the result
-// equals the single pass of the cell walk term by term.
+// adds the stored surface sum.  The terms are those of the single pass of
+// the cell walk; the list's order (other-phase neighbours first) and the
+// surface sweep's lanes add them in another order, so the two agree to
+// rounding.
 //
 // PASS: 0 = pressure + surface in one walk (cell walk), 1 = pressure and the
 // stored surface sum (list), 2 = surface sum only (list, band particles).
