@@ -6,8 +6,9 @@
 // order canonical, a gather of the particle arrays, the neighbour list of the
 // frozen configuration and the interface band.
 //
-// Pair sweeps (gather-only: every thread owns one particle and sums over its
-// neighbours, so there are no atomics on particle data):
+// Pair sweeps (gather-only: every particle's sum is owned by one thread, or by
+// a group of 2-4 lanes that split its list and add their parts in a fixed
+// order, so there are no atomics on particle data):
 //   M  correction matrix B_i (Eq. 15)                     once per advection step
 //   V  viscous acceleration (Eq. 13) + transport shift (Eq. 14)  once per advection step
 //   A  colour gradient (Eq. 22)                           every acoustic substep
@@ -16,7 +17,9 @@
 //   B  pressure (Eqs. 7-12) (+ the surface terms with the cell walk) + kick
 //                                                         every substep
 //   C  continuity (Eq. 6) + drift                         every substep
-// Time-step control (Eqs. 16-18) runs in FP64 in one-thread-per-case kernels.
+// The list build, the band and M, V, A, B, C run over the fluid particles
+// only (their ranks after each reorder).  Time-step control (Eqs. 16-18)
+// runs in FP64 in one-thread-per-case kernels.
 #pragma once
 
 #include <cuda_runtime.h>
