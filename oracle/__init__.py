@@ -9,8 +9,9 @@ this module only builds it with gcc and marshals numpy arrays through ctypes.
 the pin-strength test uses it to load copies with planted mistakes.
 
 Parity unpinned (see the header of ``sph_oracle.c``): the magnitude of the
-penalty force, the wall model and the integrator are fixed only by agreement
-with the CUDA path and the integral observables.
+penalty force and the dissipative part of the wall reading are fixed only by
+agreement with the CUDA path and the integral observables; the integrator
+and the wall's mirror pressure and volume are pinned by acoustic modes.
 """
 from __future__ import annotations
 

@@ -59,7 +59,10 @@
  *
  * Parity unpinned (no closed form or invariant fixes them; only agreement
  * with the CUDA path and the integral observables check them): the magnitude
- * of the penalty force, the wall model, the integrator.
+ * of the penalty force, and the dissipative part of the wall reading (the
+ * mirrored normal velocity in the limiter term).  The integrator and the
+ * wall reading's mirror pressure and volume are pinned in the linear regime
+ * by acoustic modes (a standing wave, and the lowest mode between walls).
  */
 #include <math.h>
 #include <stdint.h>
