@@ -8,10 +8,11 @@ this module only builds it with gcc and marshals numpy arrays through ctypes.
 ``SPH_ORACLE_LIB`` may name a separately built library of the same source;
 the pin-strength test uses it to load copies with planted mistakes.
 
-Parity unpinned (see the header of ``sph_oracle.c``): the magnitude of the
-penalty force and the dissipative part of the wall reading are fixed only by
-agreement with the CUDA path and the integral observables; the integrator
-and the wall's mirror pressure and volume are pinned by acoustic modes.
+Parity unpinned (see the header of ``sph_oracle.c``): the same-phase penalty
+term away from special cases and the dissipative part of the wall reading
+are fixed only by agreement with the CUDA path and the integral observables;
+the integrator and the wall's mirror pressure and volume are pinned by
+acoustic modes, the cross-phase penalty by an isolated pair.
 """
 from __future__ import annotations
 

@@ -59,10 +59,12 @@
  *
  * Parity unpinned (no closed form or invariant fixes them; only agreement
  * with the CUDA path and the integral observables check them): the magnitude
- * of the penalty force, and the dissipative part of the wall reading (the
- * mirrored normal velocity in the limiter term).  The integrator and the
- * wall reading's mirror pressure and volume are pinned in the linear regime
- * by acoustic modes (a standing wave, and the lowest mode between walls).
+ * of the same-phase penalty term away from special cases, and the
+ * dissipative part of the wall reading (the mirrored normal velocity in the
+ * limiter term).  The integrator and the wall reading's mirror pressure and
+ * volume are pinned in the linear regime by acoustic modes (a standing wave,
+ * and the lowest mode between walls); the cross-phase penalty by the closed
+ * form of an isolated pair.
  */
 #include <math.h>
 #include <stdint.h>

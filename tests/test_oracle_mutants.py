@@ -9,7 +9,8 @@ weight phi_i replaced by phi_j (Eq. 22), an arithmetic instead of a
 harmonic pair viscosity (Eq. 13), the pressure difference of U* (Eq. 9)
 reversed, the density update reversed (Eq. 6), the factor 2 of Eq. 6 dropped
 (only the acoustic standing wave catches that one), the wall's mirror
-pressure dropped, the wall volume doubled.  An unmodified copy passes
+pressure dropped, the wall volume doubled, the cross-phase penalty weight
+4 phi_i phi_j halved (Eq. 33).  An unmodified copy passes
 the same harness."""
 import os
 import subprocess
@@ -21,7 +22,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "sph_oracle.c")
 PINS = ["test_oracle_kernel.py", "test_oracle_neighbors.py", "test_oracle_riemann.py",
         "test_oracle_invariants.py", "test_oracle_dynamics.py", "test_oracle_periodic.py",
-        "test_oracle_reading_flags.py", "test_oracle_weights.py", "test_oracle_acoustics.py", "test_golden.py"]
+        "test_oracle_reading_flags.py", "test_oracle_weights.py", "test_oracle_acoustics.py", "test_oracle_penalty_pair.py",
+        "test_golden.py"]
 
 MUTANTS = {
     "kernel normalisation": ("return dim == 2 ? 7.0 / (4.0 * ORA_PI * h * h)",
@@ -42,6 +44,7 @@ MUTANTS = {
     "continuity factor 2 dropped": ("            s *= 2.0 * rho_i;", "            s *= rho_i;"),
     "wall mirror pressure dropped": ("R.p = p_i; R.c = c0;\n                    pbar = pair_pbar(rho_i, p_i, rho_i, p_i);",
                                      "R.p = 0.0; R.c = c0;\n                    pbar = pair_pbar(rho_i, p_i, rho_i, 0.0);"),
+    "cross-phase penalty weight halved": ("- 4.0 * phi_i * phi_j * pen;", "- 2.0 * phi_i * phi_j * pen;"),
     "wall volume doubled": ("return P->dim == 2 ? P->dx * P->dx : P->dx * P->dx * P->dx;",
                             "return P->dim == 2 ? 2.0 * P->dx * P->dx : 2.0 * P->dx * P->dx * P->dx;"),
 }
