@@ -141,3 +141,35 @@ def test_coincident_particles_are_reported():
     assert info["rc"] == S.ERR_COINCIDENT
     assert S.case_info(h)["status"] == S.ERR_COINCIDENT
     S.destroy(h)
+
+
+def test_isolated_cross_phase_pair_first_substep():
+    # two particles of different fluids at rest, viscous enough that one
+    # advection step is one substep: v after it is dt times the penalty
+    # acceleration of the hand-reduced Eqs. 22-33,
+    # a_i = -(4 phi_i phi_j xi gamma / (rho_i r)) (1 - |W'| V r) W' V e_ij
+    import math
+    dx, rho_a, rho_b, gamma, r = 0.1, 10.0, 1.0, 1.0, 0.1
+    h = 1.3 * dx
+    case = sphcases.Case(name="pair", dim=2, lo=[0.0, 0.0], hi=[1.0, 1.0], dx=dx, gamma=gamma, c0=10.0,
+                         h_factor=1.3, xi=-1.0,
+                         phases=[sphcases.Phase("fluid", np.array([[0.5, 0.5]]), rho0=rho_a, eta=50.0),
+                                 sphcases.Phase("fluid", np.array([[0.5 + r, 0.5]]), rho0=rho_b, eta=5.0)])
+    h_ = S.case_from_spec(case, precision=64)
+    try:
+        info = S.step(h_, 1)
+        vel = S.read_fields(h_, S.FIELD_VEL, 2)
+    finally:
+        S.destroy(h_)
+    assert info["n_sub"] == 1
+    a = 7.0 / (4.0 * math.pi * h * h)
+    q = r / h
+    dW = -5.0 * a * q * (1.0 - q / 2.0) ** 3 / h
+    xi = 1.3 * math.log10(rho_a / rho_b) + 0.6
+    phi_i, phi_j, V = rho_a / (rho_a + rho_b), rho_b / (rho_a + rho_b), dx * dx
+    coef = -4.0 * phi_i * phi_j * xi * gamma / r * (1.0 - abs(dW) * V * r)
+    want_i = info["t"] * coef * dW * V / rho_a * -1.0          # x component; e_ij = (-1, 0)
+    want_j = info["t"] * coef * dW * V / rho_b
+    assert vel[0, 0] == pytest.approx(want_i, rel=1e-12)
+    assert vel[1, 0] == pytest.approx(want_j, rel=1e-12)
+    assert abs(vel[0, 1]) < 1e-15 and abs(vel[1, 1]) < 1e-15
