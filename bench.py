@@ -159,12 +159,20 @@ def dist_env():
 
 
 class Dist:
-    def __init__(self, backend: str):
+    """Replica bookkeeping over torch.distributed.  A rank that dies or never
+    arrives turns the others' next barrier or reduction into an error after
+    `timeout_s` (SPHST_BENCH_PG_TIMEOUT_S, default 600 s) instead of a hang."""
+
+    def __init__(self, backend: str, timeout_s: float = None):
         self.ws, self.rank, self.local = dist_env()
         self.pg = None
         if self.ws > 1:
+            import datetime
+
             import torch.distributed as dist
-            dist.init_process_group(backend)
+            if timeout_s is None:
+                timeout_s = float(os.environ.get("SPHST_BENCH_PG_TIMEOUT_S", "600"))
+            dist.init_process_group(backend, timeout=datetime.timedelta(seconds=timeout_s))
             self.pg = dist
 
     def barrier(self):
