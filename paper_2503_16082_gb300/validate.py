@@ -1,6 +1,7 @@
 """Run the paper-shaped workloads on the GPU and report their observables.
 
   python -m paper_2503_16082_gb300.validate laplace_2d [--precision 64] [--adv 500]
+  python -m paper_2503_16082_gb300.validate laplace_3d [--ratio3d 1] [--dx3d 0.05]
   python -m paper_2503_16082_gb300.validate oscillating_3d [--periods 1.5]
   python -m paper_2503_16082_gb300.validate impact_3d [--t-end 2]
   python -m paper_2503_16082_gb300.validate oscillating_2d [--ratio 1000] [--r-over-dp 12] [--xi 0]
@@ -53,10 +54,10 @@ def launch(args) -> dict:
     return kw
 
 
-def laplace(args):
-    case = sphcases.laplace_2d()
+def laplace(args, dim=2):
+    case = sphcases.laplace_2d() if dim == 2 else sphcases.laplace_3d(ratio=args.ratio3d, dx=args.dx3d)
     h = S.case_from_spec(case, precision=args.precision, **launch(args))
-    phase = S.read_fields(h, S.FIELD_PHASE, 2)
+    phase = S.read_fields(h, S.FIELD_PHASE, dim)
     samples = []
     t0 = time.perf_counter()
     every = 10
@@ -65,16 +66,17 @@ def laplace(args):
         if info["rc"]:
             break
         if k >= 0.8 * args.adv:
-            dp, R = ob.laplace_jump(S.read_fields(h, S.FIELD_POS, 2), S.read_fields(h, S.FIELD_PRESSURE, 2),
+            dp, R = ob.laplace_jump(S.read_fields(h, S.FIELD_POS, dim), S.read_fields(h, S.FIELD_PRESSURE, dim),
                                     phase, case.dx, case.h_factor * case.dx)
-            samples.append(dp * R / case.gamma)
+            samples.append(dp * R / ((dim - 1) * case.gamma))     # Eq. 37: (d - 1) gamma / R
     wall = time.perf_counter() - t0
-    vmax = float(np.abs(S.read_fields(h, S.FIELD_VEL, 2)).max())
+    vmax = float(np.abs(S.read_fields(h, S.FIELD_VEL, dim)).max())
     S.destroy(h)
-    return {"workload": "laplace_2d", "precision": args.precision, "adv": info["n_adv"],
+    return {"workload": f"laplace_{dim}d", "precision": args.precision, "adv": info["n_adv"],
+            **({"ratio": args.ratio3d, "dx": case.dx, "particles": case.n} if dim == 3 else {}),
             "substeps": info["n_sub"], "t": info["t"], "status": info["status"],
-            "dp_R_over_gamma_mean": float(np.mean(samples)) if samples else None,
-            "dp_R_over_gamma_std": float(np.std(samples)) if samples else None,
+            "dp_R_over_dm1_gamma_mean": float(np.mean(samples)) if samples else None,
+            "dp_R_over_dm1_gamma_std": float(np.std(samples)) if samples else None,
             "exact": 1.0, "vmax_end": vmax, "wall_s": round(wall, 2)}
 
 
@@ -200,7 +202,7 @@ def impact_sweep(args):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("workload", choices=["laplace_2d", "oscillating_3d", "oscillating_2d", "impact_3d", "shear_drop",
+    ap.add_argument("workload", choices=["laplace_2d", "laplace_3d", "oscillating_3d", "oscillating_2d", "impact_3d", "shear_drop",
                                          "impact_sweep"])
     ap.add_argument("--res", type=int, default=20, help="impact_sweep: d / dp")
     ap.add_argument("--u0", type=float, nargs="+", default=[0.5, 1.0, 5.0, 10.0, 50.0])
@@ -213,6 +215,8 @@ def main(argv=None):
     ap.add_argument("--every", type=int, default=5)
     ap.add_argument("--ratio", type=float, default=1000.0)
     ap.add_argument("--r-over-dp", type=int, default=12, help="oscillating_2d, shear_drop: R / dp")
+    ap.add_argument("--ratio3d", type=float, default=1.0, help="laplace_3d: density ratio (1 or 1000)")
+    ap.add_argument("--dx3d", type=float, default=0.05, help="laplace_3d: particle spacing (R = 0.5)")
     ap.add_argument("--block", type=int, default=0, help="threads per block of the sweeps (0: library default)")
     ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4],
                     help="lanes per particle (0: library default); small 2D cases run faster with 4")
@@ -225,6 +229,8 @@ def main(argv=None):
         args.precision = 64 if args.workload in ("laplace_2d", "oscillating_2d", "shear_drop") else 32
     if args.workload == "laplace_2d":
         out = laplace(args)
+    elif args.workload == "laplace_3d":
+        out = laplace(args, 3)
     elif args.workload == "oscillating_3d":
         out = oscillating(args, 3)
     elif args.workload == "oscillating_2d":

@@ -299,6 +299,19 @@ def laplace_2d(dx: float = 0.025, R: float = 0.5, box: float = 2.0) -> Case:
                         shape="circle", sigma=1.0)
 
 
+def laplace_3d(dx: float = 0.05, R: float = 0.5, box: float = 2.0, ratio: float = 1.0,
+               eta: float = 0.05) -> Case:
+    """Static spherical droplet, the 3D form of the Laplace check: R = 0.5 in
+    a 2x2x2 box, drop density 1 and outer density 1/ratio, viscosities eta
+    and eta/ratio (ratio 1: the paper's viscous regime of its 2D checks),
+    sigma 1; the jump is 2 sigma / R."""
+    c = [box / 2] * 3
+    case = droplet_case("laplace_3d", 3, [0, 0, 0], [box, box, box], dx, c, R, shape="circle",
+                        rho_l=1.0, rho_g=1.0 / ratio, mu_l=eta, mu_g=eta / ratio, sigma=1.0)
+    case.cfl_ac = 0.4
+    return case
+
+
 def oscillating_3d(dx: float = 0.02, R: float = 0.5, box: float = 2.0,
                    amp: float = 0.05) -> Case:
     """3D droplet with a mode-2 perturbation r < R(1 + 0.05 P2(cos theta)) in a
