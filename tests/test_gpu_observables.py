@@ -233,3 +233,22 @@ def test_box_mode_between_walls_period():
         S.destroy(h)
     ratio = ob.fit_period(ts, amp, 2.0 / c0) * c0 / 2.0
     assert ratio == pytest.approx(1.0 / lattice_gradient_factor_2d(), rel=1e-3)
+
+
+def test_laplace_jump_3d_static_drop():
+    # the 3D form of Eq. 37: dp = 2 gamma / R for a spherical drop (ratio 1,
+    # the paper's viscous regime), R = 15 dp; measured 0.959 at t = 3.75
+    case = sphcases.laplace_3d(dx=0.5 / 15.0)
+    h = S.case_from_spec(case, precision=32)
+    phase = S.read_fields(h, S.FIELD_PHASE, 3)
+    samples = []
+    try:
+        for k in range(0, 1000, 50):
+            S.step(h, 50)
+            if k >= 800:
+                dp, R = ob.laplace_jump(S.read_fields(h, S.FIELD_POS, 3), S.read_fields(h, S.FIELD_PRESSURE, 3),
+                                        phase, case.dx, case.h_factor * case.dx)
+                samples.append(dp * R / (2.0 * case.gamma))
+    finally:
+        S.destroy(h)
+    assert 0.85 < np.mean(samples) < 1.15
