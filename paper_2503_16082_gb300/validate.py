@@ -82,8 +82,13 @@ def laplace(args, dim=2):
 
 def oscillating(args, dim):
     if dim == 3:
-        case = sphcases.oscillating_3d()
-        R, rho_in, rho_out = 0.5, 1000.0, 1.0
+        if args.ratio == 1000.0:
+            rho_in, rho_out = 1000.0, 1.0
+            case = sphcases.oscillating_3d()
+        else:      # drop density 1, viscosity 0.01 (light damping), outer fluid rho/ratio, eta/ratio
+            rho_in, rho_out = 1.0, 1.0 / args.ratio
+            case = sphcases.oscillating_3d(rho_l=rho_in, rho_g=rho_out, mu_l=0.01, mu_g=0.01 / args.ratio)
+        R = 0.5
         tau = ob.period_lamb_3d(R, rho_in, rho_out, case.gamma)
     else:
         case = sphcases.oscillating_2d(ratio=args.ratio, R_over_dp=args.r_over_dp)
@@ -114,7 +119,7 @@ def oscillating(args, dim):
     cr = [ts[k - 1] + (ts[k] - ts[k - 1]) * (-s[k - 1]) / (s[k] - s[k - 1])
           for k in range(1, len(s)) if np.sign(s[k]) != np.sign(s[k - 1]) and s[k] != s[k - 1]]
     period = ob.fit_period(ts, an, tau) if len(ts) > 10 else float("nan")
-    return {"workload": f"oscillating_{dim}d", "precision": args.precision, "ratio": args.ratio if dim == 2 else 1000,
+    return {"workload": f"oscillating_{dim}d", "precision": args.precision, "ratio": args.ratio,
             "adv": info["n_adv"], "substeps": info["n_sub"], "t": info["t"], "status": info["status"],
             "zero_crossings": [round(c, 4) for c in cr], "period": period, "theory": tau,
             "rel_error": (period - tau) / tau if period == period else None,

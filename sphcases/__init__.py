@@ -313,17 +313,19 @@ def laplace_3d(dx: float = 0.05, R: float = 0.5, box: float = 2.0, ratio: float 
 
 
 def oscillating_3d(dx: float = 0.02, R: float = 0.5, box: float = 2.0,
-                   amp: float = 0.05) -> Case:
+                   amp: float = 0.05, rho_l: float = 1000.0, rho_g: float = 1.0,
+                   mu_l: float = 0.1, mu_g: float = 0.001) -> Case:
     """3D droplet with a mode-2 perturbation r < R(1 + 0.05 P2(cos theta)) in a
     2x2x2 box, dx = R/25 (1e6 fluid particles), rho 1000/1, mu 0.1/0.001,
-    sigma 1, at rest."""
+    sigma 1, at rest (other densities and viscosities on request)."""
     c = [box / 2] * 3
-    rho_l, rho_g, sigma = 1000.0, 1.0, 1.0
+    sigma = 1.0
     # linear (Lamb) n = 2 frequency for a drop inside a second fluid
     w2 = 24.0 * sigma / (R ** 3 * (3 * rho_l + 2 * rho_g))
     tau = 2 * math.pi / math.sqrt(w2)
     case = droplet_case("oscillating_3d", 3, [0] * 3, [box] * 3, dx, c, R,
-                        shape="mode2", amp=amp, sigma=sigma, t_end=3 * tau)
+                        shape="mode2", amp=amp, sigma=sigma, t_end=3 * tau,
+                        rho_l=rho_l, rho_g=rho_g, mu_l=mu_l, mu_g=mu_g)
     # the gas surface-tension term binds the acoustic step at c0 dt / h = 0.38
     # with the printed factor, at the edge of the 3D interface stability limit
     case.cfl_ac = 0.4
