@@ -12,7 +12,8 @@ Parity unpinned (see the header of ``sph_oracle.c``): the same-phase penalty
 term away from special cases and the dissipative part of the wall reading
 are fixed only by agreement with the CUDA path and the integral observables;
 the integrator and the wall's mirror pressure and volume are pinned by
-acoustic modes, the cross-phase penalty by an isolated pair.
+acoustic modes, v* = v_w at a wall by the water hammer, the cross-phase
+penalty by an isolated pair.
 """
 from __future__ import annotations
 

@@ -63,7 +63,8 @@
  * dissipative part of the wall reading (the mirrored normal velocity in the
  * limiter term).  The integrator and the wall reading's mirror pressure and
  * volume are pinned in the linear regime by acoustic modes (a standing wave,
- * and the lowest mode between walls); the cross-phase penalty by the closed
+ * and the lowest mode between walls), v* = v_w at a wall by the water hammer
+ * (p = rho c0 U behind the front); the cross-phase penalty by the closed
  * form of an isolated pair.
  */
 #include <math.h>

@@ -12,9 +12,10 @@ it by percents or tens of percents.
 
 Between two walls (periodic across them) the lowest mode cos(pi x / L) has
 the period 2 L / (c0 m) when the walls reflect sound as rigid boundaries at
-the box's faces: this pins the wall reading of the pressure and continuity
-terms (mirror state, wall volume dp^d, v* = v_w), which the paper leaves
-open."""
+the box's faces, and a fluid hitting a wall at U stops behind a front of
+pressure rho c0 U (the water hammer): these pin the wall reading of the
+pressure and continuity terms (mirror state, wall volume dp^d, v* = v_w),
+which the paper leaves open."""
 import itertools
 import math
 
@@ -144,3 +145,43 @@ def test_box_mode_between_walls():
     got32 = box_mode_period(32)
     assert got64 == pytest.approx(want, rel=1e-3)     # measured 1.02704 against 1.02678
     assert abs(got64 - want) < abs(got32 - want)
+
+
+def water_hammer(nx=128, n_side=8, U=0.05, c0=10.0, front=0.4):
+    """Fluid moving at -U along x between two walls (periodic across y): the
+    left wall stops it behind a compression front, the right wall leaves a
+    rarefaction behind.  Linear acoustics gives p = +rho c0 U and u = 0 behind
+    the first front and p = -rho c0 U behind the second, whatever the wave
+    speed (the lattice factor m cancels between the two equations)."""
+    dx = 1.0 / nx
+    lo, hi = [0.0, 0.0], [1.0, n_side * dx]
+    p = sphcases.lattice(lo, hi, dx)
+    v = np.zeros_like(p)
+    v[:, 0] = -U
+    case = sphcases.Case(name="water_hammer", dim=2, lo=lo, hi=hi, dx=dx, gamma=0.0, c0=c0, h_factor=1.3,
+                         xi=-1.0, periodic=2,
+                         phases=[sphcases.Phase("fluid", p, rho0=1.0, eta=1e-3, vel=v),
+                                 sphcases.Phase("wall", sphcases.wall_shell(lo, hi, dx, sides=[0]))])
+    pos, vel, rho, kind = case.flat()
+    P = oracle.params_for_case(case)
+    t = 0.0
+    while t < front / c0:
+        pos, vel, rho, info, _, _ = oracle.run(P, pos, vel, rho, kind, 1)
+        assert info["status"] == 0
+        t += info["t"]
+    fl = kind < 2
+    x, pr, u = pos[fl, 0], c0 ** 2 * (rho[fl] - 1.0), vel[fl, 0]
+    d, edge = c0 * t, 4 * 1.3 * dx
+    near = (x > edge) & (x < 0.7 * d)
+    far = (x < 1.0 - edge) & (x > 1.0 - 0.7 * d)
+    return pr[near].mean() / (c0 * U), pr[far].mean() / (c0 * U), u[near].mean() / U
+
+
+def test_water_hammer_at_a_wall():
+    # pins the wall reading where a fluid hits it: the mirror pressure and
+    # v* = v_w in the continuity equation (R16); measured +0.9993 / -0.953
+    # at 128 particles per length, +1.0010 / -0.996 at 256
+    p_near, p_far, u_near = water_hammer()
+    assert p_near == pytest.approx(1.0, abs=0.01)
+    assert p_far == pytest.approx(-1.0, abs=0.07)
+    assert abs(u_near) < 0.01                         # the wall has stopped the fluid

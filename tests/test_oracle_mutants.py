@@ -9,7 +9,8 @@ weight phi_i replaced by phi_j (Eq. 22), an arithmetic instead of a
 harmonic pair viscosity (Eq. 13), the pressure difference of U* (Eq. 9)
 reversed, the density update reversed (Eq. 6), the factor 2 of Eq. 6 dropped
 (only the acoustic standing wave catches that one), the wall's mirror
-pressure dropped, the wall volume doubled, the cross-phase penalty weight
+pressure dropped, the wall volume doubled, v* = v_i instead of the wall's
+velocity in the continuity equation, the cross-phase penalty weight
 4 phi_i phi_j halved (Eq. 33).  An unmodified copy passes
 the same harness."""
 import os
@@ -45,6 +46,8 @@ MUTANTS = {
     "wall mirror pressure dropped": ("R.p = p_i; R.c = c0;\n                    pbar = pair_pbar(rho_i, p_i, rho_i, p_i);",
                                      "R.p = 0.0; R.c = c0;\n                    pbar = pair_pbar(rho_i, p_i, rho_i, 0.0);"),
     "cross-phase penalty weight halved": ("- 4.0 * phi_i * phi_j * pen;", "- 2.0 * phi_i * phi_j * pen;"),
+    "wall v* = v_i in continuity": ("                    for (int d = 0; d < dim; ++d) vs[d] = vj[d];",
+                                    "                    for (int d = 0; d < dim; ++d) vs[d] = vi[d];"),
     "wall volume doubled": ("return P->dim == 2 ? P->dx * P->dx : P->dx * P->dx * P->dx;",
                             "return P->dim == 2 ? 2.0 * P->dx * P->dx : 2.0 * P->dx * P->dx * P->dx;"),
 }
