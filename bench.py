@@ -72,6 +72,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # 152 SMs x 128 FP32 lanes 
 FP64_PEAK_TFLOPS = 1.25      # nominal FP64 (non-tensor) rate of a GB300
 FLOPS_PAIR_B = 59            # geometry + Riemann pressure, every pair (sweep B)
 FLOPS_PAIR_B_SURF = 110      # surface stress + penalty, pairs touching the interface (sweep S)
+L2_BYTES = 129 * 10**6       # L2 of a GB300; a case smaller than twice this is flushed between timed steps
 
 
 def workload(name: str):
@@ -225,18 +226,36 @@ def run_ours(args, dist: Dist):
     S.set_stream(h, stream.cuda_stream)
     S.step(h, args.warmup)                       # engine set-up, graph capture, warm-up
     info0 = S.case_info(h)
+    # a case whose state fits in L2 is evicted before each timed advection
+    # step by writing a buffer twice the L2 size, outside the events
+    state_bytes = S.footprint_bytes(S.params_from_spec(spec, args.precision, nbr_mode=nbr_mode, **extra), spec.n)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda") if state_bytes < 2 * L2_BYTES else None
+    l2_note = (f"inputs larger than L2 ({state_bytes / 1e6:.0f} MB of case state on the device vs 129 MB L2)"
+               if flush is None else
+               f"L2 flushed before each timed step (case state {state_bytes / 1e6:.1f} MB; a 258 MB buffer "
+               f"written between steps, outside the timed events)")
 
     clocks = ClockSampler(dist.local)
     clocks.start()
     dist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    S.step(h, args.steps)
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    if flush is None:
+        ev0.record(stream)
+        S.step(h, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+    else:
+        ms = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1)
+            ev0.record(stream)
+            S.step(h, 1)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms += ev0.elapsed_time(ev1)
     dist.barrier()
-    ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     info1 = S.case_info(h)
     n_sub = info1["n_sub"] - info0["n_sub"]
@@ -322,7 +341,7 @@ def run_ours(args, dist: Dist):
     return {
         "value": value, "ms_per_step": tmax * 1e3 / args.steps, "units": total_units,
         "n_sub": n_sub, "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clk, "kernel_ms": kernel_ms, "n_fluid": n_fluid, "n_total": spec.n,
+        "clocks": clk, "kernel_ms": kernel_ms, "n_fluid": n_fluid, "n_total": spec.n, "l2": l2_note,
     }
 
 
@@ -379,6 +398,8 @@ def run_batch(args):
     # capacity of 128 neighbours; the batch uses 192
     hs = [S.case_from_spec(c, precision=args.precision, max_neighbors=192 if c.dim == 3 else 0)
           for c in cases]
+    state_bytes = sum(S.footprint_bytes(S.params_from_spec(c, args.precision, max_neighbors=192 if c.dim == 3 else 0),
+                                        c.n) for c in cases)
     b = S.batch_create(args.precision)
     for h in hs:
         S.batch_add(b, h)
@@ -434,7 +455,8 @@ def run_batch(args):
             "plain_single_case": {"value": round(punits / psecs, 1), "cases_sampled": k},
             "speedup_vs_plain": round((units / dt) / (punits / psecs), 2), "cpu_baseline": cpu,
             "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
-            "config": {"workload": "batch_cases seed 20250320", "step": "one advection step of every case"}}
+            "config": {"workload": "batch_cases seed 20250320", "step": "one advection step of every case",
+                       "l2": f"inputs larger than L2 ({state_bytes / 1e9:.1f} GB of case state vs 129 MB L2)"}}
     print(json.dumps(line), flush=True)
 
 
@@ -542,7 +564,7 @@ def main():
     ws, rank, local = dist_env()
     config = {"workload": args.workload, "particles": None, "fluid_particles": None,
               "step": "one advection step (rebuild + all acoustic substeps)",
-              "l2": "inputs larger than L2 (~170 MB FP32 working set vs 129 MB L2)",
+              "l2": None,
               "parallelism": f"replicas x{max(ws, 1)}", "neighbours": args.nbr,
               "block": args.block or 128, "lanes": args.lanes or 1}
     dtype = "f32" if args.precision == 32 else "f64"
@@ -554,7 +576,8 @@ def main():
         if res is None:
             return
         spec_n = workload(args.workload)
-        config.update(particles=spec_n.n, fluid_particles=spec_n.n_fluid)
+        config.update(particles=spec_n.n, fluid_particles=spec_n.n_fluid,
+                      l2="not applicable: the oracle runs on the host cores")
         line = {"impl": "reference", "metric": METRIC, "value": round(res["value"], 1),
                 "unit": METRIC, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(res["ms_per_step"], 1), "higher_is_better": True,
@@ -569,7 +592,7 @@ def main():
 
     dist = Dist("nccl")
     res = run_ours(args, dist)
-    config.update(particles=res["n_total"], fluid_particles=res["n_fluid"],
+    config.update(particles=res["n_total"], fluid_particles=res["n_fluid"], l2=res["l2"],
                   substeps_per_step=round(res["n_sub"] / args.steps, 2))
     cpu = None
     if rank == 0 and ws <= 1 and not args.no_cpu_baseline:

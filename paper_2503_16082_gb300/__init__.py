@@ -335,10 +335,10 @@ def footprint_bytes(params: CaseParams, n: int) -> int:
 # --------------------------------------------------------------------------
 # convenience: a whole problem statement from a seeded case description
 # --------------------------------------------------------------------------
-def case_from_spec(spec, precision: int = 32, **params):
-    """Create and fill a case from a ``sphcases.Case``-like object (fields
-    dim, dx, h_factor, c0, gamma, xi and phases with kind/pos/rho0/eta/vel/
-    rho/wall_vel).  Returns the handle."""
+def params_from_spec(spec, precision: int = 32, **params) -> CaseParams:
+    """The case parameters of a ``sphcases.Case``-like object (fields dim,
+    dx, h_factor, c0, gamma, xi, optional periodic and cfl_ac), with
+    ``params`` overriding fields of the result."""
     p = default_params(dim=spec.dim, precision=precision, dx=spec.dx, h_factor=spec.h_factor,
                        c0=spec.c0, gamma=spec.gamma, xi=spec.xi,
                        cfl_ac=getattr(spec, "cfl_ac", 0.6))
@@ -348,7 +348,14 @@ def case_from_spec(spec, precision: int = 32, **params):
             p.period_lo[a], p.period_hi[a] = spec.lo[a], spec.hi[a]
     for k, v in params.items():
         setattr(p, k, v)
-    h = create_case(p)
+    return p
+
+
+def case_from_spec(spec, precision: int = 32, **params):
+    """Create and fill a case from a ``sphcases.Case``-like object (the
+    fields of ``params_from_spec`` and phases with kind/pos/rho0/eta/vel/
+    rho/wall_vel).  Returns the handle."""
+    h = create_case(params_from_spec(spec, precision, **params))
     try:
         for ph in spec.phases:
             if ph.kind == "fluid":
