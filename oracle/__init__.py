@@ -9,11 +9,11 @@ this module only builds it with gcc and marshals numpy arrays through ctypes.
 the pin-strength test uses it to load copies with planted mistakes.
 
 Parity unpinned (see the header of ``sph_oracle.c``): the same-phase penalty
-term away from special cases and the dissipative part of the wall reading
-are fixed only by agreement with the CUDA path and the integral observables;
-the integrator and the wall's mirror pressure and volume are pinned by
-acoustic modes, v* = v_w at a wall by the water hammer, the cross-phase
-penalty by an isolated pair.
+term away from special cases is fixed only by agreement with the CUDA path
+and the integral observables; the integrator and the wall's mirror pressure
+and volume are pinned by acoustic modes, v* = v_w at a wall by the water
+hammer, the wall's dissipative term by a fluid particle beside one wall
+particle, the cross-phase penalty by an isolated pair.
 """
 from __future__ import annotations
 

@@ -57,15 +57,15 @@
  *               with the viscous force and added to the positions once per
  *               advection step.
  *
- * Parity unpinned (no closed form or invariant fixes them; only agreement
- * with the CUDA path and the integral observables check them): the magnitude
- * of the same-phase penalty term away from special cases, and the
- * dissipative part of the wall reading (the mirrored normal velocity in the
- * limiter term).  The integrator and the wall reading's mirror pressure and
- * volume are pinned in the linear regime by acoustic modes (a standing wave,
- * and the lowest mode between walls), v* = v_w at a wall by the water hammer
- * (p = rho c0 U behind the front); the cross-phase penalty by the closed
- * form of an isolated pair.
+ * Parity unpinned (no closed form or invariant fixes it; only agreement
+ * with the CUDA path and the integral observables check it): the magnitude
+ * of the same-phase penalty term away from special cases.  The integrator
+ * and the wall reading's mirror pressure and volume are pinned in the
+ * linear regime by acoustic modes (a standing wave, and the lowest mode
+ * between walls), v* = v_w at a wall by the water hammer (p = rho c0 U
+ * behind the front), the wall's dissipative term (mirrored normal velocity,
+ * limiter) by the closed form of a fluid particle beside one wall particle;
+ * the cross-phase penalty by the closed form of an isolated pair.
  */
 #include <math.h>
 #include <stdint.h>

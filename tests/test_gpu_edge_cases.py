@@ -173,3 +173,45 @@ def test_isolated_cross_phase_pair_first_substep():
     assert vel[0, 0] == pytest.approx(want_i, rel=1e-12)
     assert vel[1, 0] == pytest.approx(want_j, rel=1e-12)
     assert abs(vel[0, 1]) < 1e-15 and abs(vel[1, 1]) < 1e-15
+
+
+@pytest.mark.parametrize("u,a,rho_eps", [(0.7, 0.2, 0.01), (3.0, 0.0, 0.0)])
+def test_fluid_particle_beside_a_wall_particle_first_substep(u, a, rho_eps):
+    # one fluid particle and one wall particle, viscous enough that one
+    # advection step is one substep: v after it is v0 + dt (a_p + a_v) of
+    # the hand-reduced wall reading (mirror state U_R = 2 U_w - U_L, Eq. 11's
+    # limiter at beta = 0.3 and clipped at 1, Eq. 13 with eta_i and v_i - v_w),
+    # and rho after it follows Eq. 6 with v* = v_w and the kicked velocity
+    import math
+    dx, c0, rho0, eta, r = 0.1, 10.0, 1.0, 50.0, 0.09
+    h = 1.3 * dx
+    w, b = 0.25, -0.15
+    case = sphcases.Case(name="wall_pair", dim=2, lo=[0.0, 0.0], hi=[1.0, 1.0], dx=dx, gamma=1.0, c0=c0,
+                         h_factor=1.3, xi=-1.0,
+                         phases=[sphcases.Phase("fluid", np.array([[0.5, 0.5]]), rho0=rho0, eta=eta,
+                                                vel=np.array([[u, w]]), rho=np.array([rho0 * (1.0 + rho_eps)])),
+                                 sphcases.Phase("wall", np.array([[0.5 + r, 0.5]]), wall_vel=(a, b, 0.0))])
+    h_ = S.case_from_spec(case, precision=64)
+    try:
+        info = S.step(h_, 1)
+        vel = S.read_fields(h_, S.FIELD_VEL, 2)
+        rho = S.read_fields(h_, S.FIELD_RHO, 2)
+    finally:
+        S.destroy(h_)
+    assert info["n_sub"] == 1
+    dt = info["t"]
+    q = r / h
+    dW = -5.0 * 7.0 / (4.0 * math.pi * h * h) * q * (1.0 - q / 2.0) ** 3 / h
+    V = dx * dx
+    rho_i = rho0 * (1.0 + rho_eps)
+    dU = 2.0 * (u - a)
+    beta = min(3.0 * max(dU / c0, 0.0), 1.0)
+    Ps = c0 * c0 * (rho_i - rho0) + beta * rho_i * c0 * dU / 2.0
+    e = np.array([-1.0, 0.0])
+    vij = np.array([u - a, w - b])
+    acc = -(2.0 / rho_i) * Ps * dW * e * V + (2.0 / rho_i) * eta * vij / r * dW * V
+    v1 = np.array([u, w]) + dt * acc
+    assert vel[0] == pytest.approx(v1, rel=1e-12)
+    assert np.array_equal(vel[1], [a, b])                      # the wall keeps its velocity
+    drho = 2.0 * rho_i * float((v1 - np.array([a, b])) @ e) * dW * V
+    assert rho[0] - rho_i == pytest.approx(dt * drho, rel=1e-10)

@@ -10,7 +10,8 @@ harmonic pair viscosity (Eq. 13), the pressure difference of U* (Eq. 9)
 reversed, the density update reversed (Eq. 6), the factor 2 of Eq. 6 dropped
 (only the acoustic standing wave catches that one), the wall's mirror
 pressure dropped, the wall volume doubled, v* = v_i instead of the wall's
-velocity in the continuity equation, the cross-phase penalty weight
+velocity in the continuity equation, the wall's normal velocity not
+mirrored in the Riemann state, the cross-phase penalty weight
 4 phi_i phi_j halved (Eq. 33).  An unmodified copy passes
 the same harness."""
 import os
@@ -24,6 +25,7 @@ SRC = os.path.join(ROOT, "oracle", "sph_oracle.c")
 PINS = ["test_oracle_kernel.py", "test_oracle_neighbors.py", "test_oracle_riemann.py",
         "test_oracle_invariants.py", "test_oracle_dynamics.py", "test_oracle_periodic.py",
         "test_oracle_reading_flags.py", "test_oracle_weights.py", "test_oracle_acoustics.py", "test_oracle_penalty_pair.py",
+        "test_oracle_wall_pair.py",
         "test_golden.py"]
 
 MUTANTS = {
@@ -48,6 +50,7 @@ MUTANTS = {
     "cross-phase penalty weight halved": ("- 4.0 * phi_i * phi_j * pen;", "- 2.0 * phi_i * phi_j * pen;"),
     "wall v* = v_i in continuity": ("                    for (int d = 0; d < dim; ++d) vs[d] = vj[d];",
                                     "                    for (int d = 0; d < dim; ++d) vs[d] = vi[d];"),
+    "wall velocity not mirrored": ("R.U = 2.0 * Uw - L.U;", "R.U = Uw;"),
     "wall volume doubled": ("return P->dim == 2 ? P->dx * P->dx : P->dx * P->dx * P->dx;",
                             "return P->dim == 2 ? 2.0 * P->dx * P->dx : 2.0 * P->dx * P->dx * P->dx;"),
 }
