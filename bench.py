@@ -97,7 +97,8 @@ class ClockSampler:
         self.gpu = gpu
         self.proc = None
         self.first = 0
-        self.path = tempfile.mktemp(suffix=".csv")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
 
     def _lines(self) -> int:
         try:
