@@ -124,6 +124,7 @@ def oscillating(args, dim):
             "zero_crossings": [round(c, 4) for c in cr], "period": period, "theory": tau,
             "rel_error": (period - tau) / tau if period == period else None,
             "anisotropy_amplitude": float(np.abs(s).max()) if len(s) else None,
+            "series": [[round(ts[k], 5), float(an[k])] for k in range(0, len(ts), max(1, len(ts) // 200))],
             **({"R_over_dp": args.r_over_dp, "xi": case.xi, "stray_end": stray[-1], "stray_max": max(stray)}
                if dim == 2 else {}),
             "wall_s": round(wall, 2)}
