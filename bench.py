@@ -541,7 +541,7 @@ def main():
     ap.add_argument("--nbr", default="list", choices=["list", "cells"],
                     help="neighbour source of the sweeps (list built per advection step, or cell walk)")
     ap.add_argument("--block", type=int, default=0, help="particles per tile / threads per block (0: library default)")
-    ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4],
+    ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4, 8],
                     help="lanes per particle in sweeps A, B, C with the list (0: library default, 1)")
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"],
                     help="single: the headline line; batch / serve: the batched and served workloads")

@@ -140,14 +140,15 @@ typedef struct {
     double  period_hi[3];
     int32_t lanes;          /* lanes per particle in the per-substep sweeps
                                (colour gradient, pressure, continuity) with
-                               the neighbour list: 1, 2 or 4; the surface
+                               the neighbour list: 1, 2, 4 or 8; the surface
                                sweep over the interface band takes at least 2.  With L > 1
                                the L lanes of a particle split its list and
                                add their partial sums (fixed order, so runs
                                repeat bit for bit; results differ from L = 1
                                by the rounding of the reordered sum).  More
                                lanes spread small cases over more of the GPU.
-                               Speed only; a batch uses its first case's     */
+                               Speed only; a batch uses its first case's
+                               value.                                        */
     int32_t pad2_;
 } sphst_case_params;
 

@@ -29,7 +29,7 @@ import time
 from typing import Callable, Dict, Iterable, Optional, Sequence, Tuple
 
 BLOCKS = (32, 64, 128, 256)
-LANES = (1, 2, 4)
+LANES = (1, 2, 4, 8)
 
 
 def bucket_key(dim: int, precision: int, n: int) -> str:

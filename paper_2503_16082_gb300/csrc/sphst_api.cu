@@ -297,8 +297,8 @@ int sphst_create_case(const sphst_case_params *params, sphst_case *out) {
         return SPHST_ERR_INVALID_ARG;
     }
     if (P.grid_pad < 1 || P.grid_pad > 64 || P.block < 32 || P.block > 256 || P.block % 32 ||
-        (P.lanes != 1 && P.lanes != 2 && P.lanes != 4)) {
-        set_error("grid_pad must be 1..64, block a multiple of 32 in 32..256 and lanes 1, 2 or 4");
+        (P.lanes != 1 && P.lanes != 2 && P.lanes != 4 && P.lanes != 8)) {
+        set_error("grid_pad must be 1..64, block a multiple of 32 in 32..256 and lanes 1, 2, 4 or 8");
         return SPHST_ERR_INVALID_ARG;
     }
     if (P.periodic < 0 || P.periodic >= (1 << P.dim)) {

@@ -45,6 +45,7 @@ enum ArrayId { A_POS = 0, A_VEL, A_DRHO, A_ID, A_GRADC, A_ACCV };
     switch (LN) {                                                                                 \
     case 2: KERN<T, D, true, 2><<<g_ * 2, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
     case 4: KERN<T, D, true, 4><<<g_ * 4, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
+    case 8: KERN<T, D, true, 8><<<g_ * 8, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
     default: KERN<T, D, true, 1><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;               \
     }
 #define SPH_CLASSES_LX(NCLS, KERN, LN, ARGS, CNT, ...)                                 \

@@ -561,7 +561,7 @@ __device__ __forceinline__ void walk_geo_aux(const CaseDesc &d, const uint32_t *
                           [&](bool other, uint32_t j, const V4<T> &G) { f(other, j, G, ld4(aux + j)); });
 }
 
-// Sum over the L lanes that share one particle (L = 1, 2, 4; groups are
+// Sum over the L lanes that share one particle (L = 1, 2, 4, 8; groups are
 // aligned within the warp).  The butterfly gives every lane of the group the
 // same value: each step adds two partial sums in an order-free way.
 template <int L, typename T> __device__ __forceinline__ T group_sum(T v) {
@@ -1589,7 +1589,7 @@ __global__ void SPH_SWEEP_BOUNDS k_sweep_V(SweepArgs a, const V4<T> *snap, const
                         &a.st[t.c].status);
 }
 
-// Sweeps A, B and C take L lanes per particle (L = 1, 2, 4; list classes):
+// Sweeps A, B and C take L lanes per particle (L = 1, 2, 4, 8; list classes):
 // L blocks share one tile, block b takes its part b % L of blockDim / L
 // particles, and lane threadIdx % L of a particle's group walks every L-th
 // list entry.  local_index gives the particle's index within its tile.

@@ -224,7 +224,7 @@ def main(argv=None):
     ap.add_argument("--ratio3d", type=float, default=1.0, help="laplace_3d: density ratio (1 or 1000)")
     ap.add_argument("--dx3d", type=float, default=0.05, help="laplace_3d: particle spacing (R = 0.5)")
     ap.add_argument("--block", type=int, default=0, help="threads per block of the sweeps (0: library default)")
-    ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4],
+    ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4, 8],
                     help="lanes per particle (0: library default); small 2D cases run faster with 4")
     ap.add_argument("--xi", type=float, default=None, help="penalty coefficient (default: from the density ratio)")
     ap.add_argument("--t-end", type=float, default=None, help="impact_3d: 2.0, shear_drop: 20.0")

@@ -2,8 +2,10 @@
 has for them: one fluid phase (every surface term vanishes), fluid at rest
 (stays at rest; the substep count follows the clipping of Eqs. 16-18), a
 lone particle (no neighbours: it drifts at its velocity), a handful of
-particles split over four lanes each in 32-thread blocks (a ragged,
-mostly empty tile), and coincident particles (reported, not divided by)."""
+particles split over four or eight lanes each in 32-thread blocks (a
+ragged, mostly empty tile), coincident particles (reported, not divided
+by), and the closed forms of an isolated cross-phase pair and of a fluid
+particle beside a wall particle."""
 import numpy as np
 import pytest
 
@@ -109,10 +111,10 @@ def test_lone_particle_drifts_at_its_velocity(precision):
     assert np.abs(pos - (0.5 + v * info["t"])).max() <= tol * np.abs(v * info["t"]).max()
 
 
-@pytest.mark.parametrize("lanes", [1, 4])
+@pytest.mark.parametrize("lanes", [1, 4, 8])
 def test_handful_of_particles_ragged_tile(lanes):
-    # nine fluid particles of two phases in 32-thread blocks split over four
-    # lanes each: one tile, mostly empty, every lane group ragged
+    # nine fluid particles of two phases in 32-thread blocks split over
+    # L lanes each: one tile, mostly empty, every lane group ragged
     rng = np.random.default_rng(9)
     dx = 0.05
     base = np.array([[0.5, 0.5]]) + dx * np.array([[i, j] for i in range(3) for j in range(3)])

@@ -228,7 +228,7 @@ def test_list_and_cell_walk_agree(dim, precision):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
-@pytest.mark.parametrize("lanes", [2, 4])
+@pytest.mark.parametrize("lanes", [2, 4, 8])
 def test_lanes_per_particle_fp64_against_oracle(dim, lanes):
     # L lanes split each particle's list (sweeps A, B, C): same pairs, sums
     # in another order, so the oracle bar of one advection step holds
@@ -240,7 +240,7 @@ def test_lanes_per_particle_fp64_against_oracle(dim, lanes):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
-@pytest.mark.parametrize("lanes", [2, 4])
+@pytest.mark.parametrize("lanes", [2, 4, 8])
 def test_lanes_per_particle_fp32_one_substep(dim, lanes):
     case = one_substep_case(dim)
     g, o, info, oinfo, pos0, kind = run_both(case, 32, 1, lanes=lanes)
@@ -249,7 +249,7 @@ def test_lanes_per_particle_fp32_one_substep(dim, lanes):
         assert rel_err(g, o, pos0, kind, key, case) <= 1e-5, key
 
 
-@pytest.mark.parametrize("lanes", [2, 4])
+@pytest.mark.parametrize("lanes", [2, 4, 8])
 def test_lanes_per_particle_repeat_bitwise(lanes):
     # the group sums run in a fixed order: two runs are identical, and a
     # tile's last, partly filled block (ragged tail) is covered
