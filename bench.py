@@ -223,6 +223,8 @@ def run_ours(args, dist: Dist):
     extra = {"block": args.block} if args.block else {}
     if args.lanes:
         extra["lanes"] = args.lanes
+    if args.loop == "host":                      # every kernel a launch of its own (profilers see them)
+        extra["loop_mode"] = S.LOOP_HOST
     h = S.case_from_spec(spec, precision=args.precision, nbr_mode=nbr_mode, **extra)
     S.set_stream(h, stream.cuda_stream)
     S.step(h, args.warmup)                       # engine set-up, graph capture, warm-up
@@ -541,6 +543,9 @@ def main():
     ap.add_argument("--nbr", default="list", choices=["list", "cells"],
                     help="neighbour source of the sweeps (list built per advection step, or cell walk)")
     ap.add_argument("--block", type=int, default=0, help="particles per tile / threads per block (0: library default)")
+    ap.add_argument("--loop", default="graph", choices=["graph", "host"],
+                    help="graph: one CUDA graph per advection step (the default, timed); host: the same kernels "
+                         "launched one by one with a host check per substep, for profilers")
     ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4, 8],
                     help="lanes per particle in sweeps A, B, C with the list (0: library default, 1)")
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"],
@@ -567,7 +572,7 @@ def main():
               "step": "one advection step (rebuild + all acoustic substeps)",
               "l2": None,
               "parallelism": f"replicas x{max(ws, 1)}", "neighbours": args.nbr,
-              "block": args.block or 128, "lanes": args.lanes or 1}
+              "block": args.block or 128, "lanes": args.lanes or 1, "loop": args.loop}
     dtype = "f32" if args.precision == 32 else "f64"
 
     if args.impl == "reference":
