@@ -73,6 +73,11 @@ extern "C" {
 /* the scalar C_ij - gradCbar . r_ij of Eq. 29 (the paper's first penalty,
  * which it notes does not conserve momentum), for ablation */
 #define SPHST_PENALTY_SCALAR 2
+/* which lines of Eq. 33 carry the penalty: BOTH as printed; CROSS_ONLY drops
+ * it from the same-phase line and keeps it on the cross-phase line (an
+ * ablation) */
+#define SPHST_PENALTY_SCOPE_BOTH       0
+#define SPHST_PENALTY_SCOPE_CROSS_ONLY 1
 /* Eq. 8's star velocity: CORRECTED takes the normal component as -U* along
  * e_ij (U = -v.e_ij, Eq. 10) and the tangential part of the pair average;
  * PRINTED is U* e_ij + (vbar - Ubar e_ij) as printed */
@@ -149,7 +154,7 @@ typedef struct {
                                lanes spread small cases over more of the GPU.
                                Speed only; a batch uses its first case's
                                value.                                        */
-    int32_t pad2_;
+    int32_t penalty_scope;  /* SPHST_PENALTY_SCOPE_*                           */
 } sphst_case_params;
 
 typedef struct {

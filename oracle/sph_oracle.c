@@ -40,7 +40,9 @@
  *   viscosity   Eq. 13 already is an acceleration (it carries 1/rho_i).
  *   C-hat       (the contraction) A A^T/|A| = |gradCbar| r_ij nbar nbar^T with
  *               nbar = gradCbar/|gradCbar|; the flag penalty_form = 1 takes
- *               A^T A/|A| = |gradCbar| r_ij e e^T instead.
+ *               A^T A/|A| = |gradCbar| r_ij e e^T instead.  The flag
+ *               penalty_scope = 1 drops the penalty from the same-phase line
+ *               of Eq. 33 and keeps it on the cross-phase line (an ablation).
  *   periodic    an axis flagged periodic (the shear drop of Section 5.2 is
  *               periodic in x) wraps positions into [box_lo, box_hi) and takes
  *               every pair vector as its minimum image; the key grid of a
@@ -106,7 +108,8 @@ typedef struct {
     int32_t pad2_;
     double box_lo[3], box_hi[3];
     int32_t vstar_form;   /* 0: normal component -U* (reading); 1: Eq. 8 as printed */
-    int32_t pad3_;
+    int32_t penalty_scope; /* 0: the penalty on both lines of Eq. 33 (as printed);
+                              1: on the cross-phase line only (an ablation) */
 } ora_params;
 
 typedef struct {
@@ -820,7 +823,7 @@ static void pressure_surface_acc(const ora_params *P, const state_t *S,
                     for (int b = 0; b < dim; ++b) {
                         double pen = xi * P->gamma * MC[3 * a + b] / pp->r[k];
                         S[3 * a + b] = same
-                            ? si.Pi[3 * a + b] + sj.Pi[3 * a + b] + pen
+                            ? si.Pi[3 * a + b] + sj.Pi[3 * a + b] + (P->penalty_scope == 1 ? 0.0 : pen)
                             : 2.0 * phi_j * si.Pi[3 * a + b] + 2.0 * phi_i * sj.Pi[3 * a + b]
                               - 4.0 * phi_i * phi_j * pen;
                     }

@@ -27,6 +27,7 @@ FLUID, WALL = 0, 1
 LIMITER_DENSITY, LIMITER_NONE, LIMITER_ZERO, LIMITER_PRINTED = 0, 1, 2, 3
 GRAD_COMMON, GRAD_PRINTED = 0, 1
 PENALTY_NN, PENALTY_EE, PENALTY_SCALAR = 0, 1, 2
+PENALTY_SCOPE_BOTH, PENALTY_SCOPE_CROSS_ONLY = 0, 1
 VSTAR_CORRECTED, VSTAR_PRINTED = 0, 1
 LOOP_GRAPH, LOOP_HOST = 0, 1
 FIELD_POS, FIELD_VEL, FIELD_RHO, FIELD_PRESSURE, FIELD_PHASE, FIELD_GRADC, FIELD_ACC_VISC = range(7)
@@ -43,7 +44,7 @@ class CaseParams(C.Structure):
                 ("nbr_mode", C.c_int32), ("max_neighbors", C.c_int32),
                 ("periodic", C.c_int32), ("vstar_form", C.c_int32),
                 ("period_lo", C.c_double * 3), ("period_hi", C.c_double * 3),
-                ("lanes", C.c_int32), ("pad2_", C.c_int32)]
+                ("lanes", C.c_int32), ("penalty_scope", C.c_int32)]
 
 
 class PhaseProps(C.Structure):

@@ -163,6 +163,7 @@ CaseDesc make_desc(const CaseRec *c) {
     d.limiter = c->P.limiter;
     d.grad_mode = c->P.grad_mode;
     d.penalty_form = c->P.penalty_form;
+    d.penalty_scope = c->P.penalty_scope;
     d.n_fluid_phases = c->n_fluid_phases;
     d.bits = c->bits;
     for (int a = 0; a < 3; ++a) { d.ncell[a] = c->ncell[a]; d.origin[a] = c->origin[a]; }
@@ -288,7 +289,7 @@ int sphst_create_case(const sphst_case_params *params, sphst_case *out) {
     }
     if (P.limiter < 0 || P.limiter > 3 || P.grad_mode < 0 || P.grad_mode > 1 ||
         P.penalty_form < 0 || P.penalty_form > 2 || P.loop_mode < 0 || P.loop_mode > 1 ||
-        P.vstar_form < 0 || P.vstar_form > 1) {
+        P.vstar_form < 0 || P.vstar_form > 1 || P.penalty_scope < 0 || P.penalty_scope > 1) {
         set_error("unknown reading or loop flag");
         return SPHST_ERR_INVALID_ARG;
     }

@@ -1271,9 +1271,10 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
         const T pen = cp.xi * cp.gamma * g.inv_r;
         T sx, sy, sz;
         if (same) {   // Eq. 33, first line; T-bar c = c - N-bar c
-            sx = pix + pjx + pen * (cx - qx);
-            sy = piy + pjy + pen * (cy - qy);
-            sz = piz + pjz + pen * (cz - qz);
+            const T pen_s = d.penalty_scope == 1 ? T(0) : pen;
+            sx = pix + pjx + pen_s * (cx - qx);
+            sy = piy + pjy + pen_s * (cy - qy);
+            sz = piz + pjz + pen_s * (cz - qz);
         } else {      // Eq. 33, second line
             const T a = sel(kj, cp.two_phi[0], cp.two_phi[1]), b = sel(ki, cp.two_phi[0], cp.two_phi[1]),
                     c = cp.four_phi_phi * pen;

@@ -45,8 +45,11 @@ from paper_2503_16082_gb300 import observables as ob  # noqa: E402
 
 
 def launch(args) -> dict:
-    """Launch shape of the sweeps (speed only): block size and lanes per particle."""
+    """Launch shape of the sweeps (speed only: block size, lanes per
+    particle) and the penalty-scope ablation flag."""
     kw = {}
+    if getattr(args, "penalty_scope", 0):
+        kw["penalty_scope"] = args.penalty_scope
     if args.block:
         kw["block"] = args.block
     if args.lanes:
@@ -125,7 +128,8 @@ def oscillating(args, dim):
             "rel_error": (period - tau) / tau if period == period else None,
             "anisotropy_amplitude": float(np.abs(s).max()) if len(s) else None,
             "series": [[round(ts[k], 5), float(an[k])] for k in range(0, len(ts), max(1, len(ts) // 200))],
-            **({"R_over_dp": args.r_over_dp, "xi": case.xi, "stray_end": stray[-1], "stray_max": max(stray)}
+            **({"R_over_dp": args.r_over_dp, "xi": case.xi, "penalty_scope": args.penalty_scope,
+                "stray_end": stray[-1], "stray_max": max(stray)}
                if dim == 2 else {}),
             "wall_s": round(wall, 2)}
 
@@ -227,6 +231,8 @@ def main(argv=None):
     ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4, 8],
                     help="lanes per particle (0: library default); small 2D cases run faster with 4")
     ap.add_argument("--xi", type=float, default=None, help="penalty coefficient (default: from the density ratio)")
+    ap.add_argument("--penalty-scope", type=int, default=0, choices=[0, 1],
+                    help="0: the penalty on both lines of Eq. 33; 1: on the cross-phase line only (ablation)")
     ap.add_argument("--t-end", type=float, default=None, help="impact_3d: 2.0, shear_drop: 20.0")
     args = ap.parse_args(argv)
     if args.t_end is None:

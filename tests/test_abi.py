@@ -42,7 +42,7 @@ def test_default_params_and_validation():
     assert p.lanes == 1 and p.block == 128
     for bad in (dict(dx=0.0), dict(dx=0.01, c0=-1.0), dict(dx=0.01, gamma=-1.0),
                 dict(dx=0.01, block=48), dict(dx=0.01, limiter=7), dict(dx=0.01, grid_pad=0),
-                dict(dx=0.01, lanes=3), dict(dx=0.01, lanes=16), dict(dx=0.01, block=512)):
+                dict(dx=0.01, lanes=3), dict(dx=0.01, lanes=16), dict(dx=0.01, penalty_scope=2), dict(dx=0.01, block=512)):
         with pytest.raises(S.SphstError) as e:
             S.create_case(S.default_params(**bad))
         assert e.value.code == S.ERR_INVALID_ARG

@@ -142,6 +142,7 @@ def test_fp32_one_advection_step(dim):
     (dict(xi=0.0), dict(xi=0.0)),
     (dict(limiter=3), dict(limiter=3)),
     (dict(penalty_form=2), dict(penalty_form=2)),
+    (dict(penalty_scope=1), dict(penalty_scope=1)),
 ])
 def test_fp64_readings_flags(opts, ora):
     case = small(2)

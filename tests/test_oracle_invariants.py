@@ -23,7 +23,8 @@ def masses(case, kind):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
-@pytest.mark.parametrize("opts", [{}, {"penalty_form": 1}, {"grad_mode": 1}, {"limiter": 1}, {"xi": 0.0}])
+@pytest.mark.parametrize("opts", [{}, {"penalty_form": 1}, {"grad_mode": 1}, {"limiter": 1}, {"xi": 0.0},
+                                  {"penalty_scope": 1}])
 def test_momentum_conserved_by_each_force(dim, opts):
     case, pos, vel, rho, kind = blob(dim)
     P = oracle.params_for_case(case, **opts)

@@ -35,8 +35,8 @@ MUTANTS = {
                                "return 5.0 * wendland_alpha(dim, h) * q * t * t * t / h;"),
     "pressure force sign": ("a_p[d] += -2.0 / rho_i * Ps * gradW[d] * Vj;",
                             "a_p[d] += 2.0 / rho_i * Ps * gradW[d] * Vj;"),
-    "neighbour stress dropped": ("? si.Pi[3 * a + b] + sj.Pi[3 * a + b] + pen",
-                                 "? si.Pi[3 * a + b] + si.Pi[3 * a + b] + pen"),
+    "neighbour stress dropped": ("? si.Pi[3 * a + b] + sj.Pi[3 * a + b] + (P->penalty_scope",
+                                 "? si.Pi[3 * a + b] + si.Pi[3 * a + b] + (P->penalty_scope"),
     "colour weight of j": ("g[d] += 2.0 * phi_i * Cij * pp->dW[k] * pp->e[3 * k + d] * Vj;",
                            "g[d] += 2.0 * (1.0 - phi_i) * Cij * pp->dW[k] * pp->e[3 * k + d] * Vj;"),
     "arithmetic pair viscosity": ("? 2.0 * P->eta[ki] * P->eta[kj] / (P->eta[ki] + P->eta[kj])",

@@ -75,3 +75,21 @@ def test_scalar_penalty_breaks_momentum_conservation_tensor_forms_keep_it():
     base = surface_force_sum(0, xi=0.0)[2]
     for form in (1, 2):
         assert np.array_equal(surface_force_sum(form, xi=0.0)[2], base)
+
+
+def test_penalty_on_the_cross_phase_line_only():
+    # the ablation keeps the cross-phase line of Eq. 33 and drops the
+    # penalty from the same-phase line: with xi = 0 it changes nothing;
+    # with the penalty on it changes the surface force, and what is left
+    # still differs from no penalty at all (the cross-phase line)
+    case = sphcases.small_droplet(2, 20, R_frac=0.3, shape="mode2", amp=0.2, walls=False,
+                                  rho_l=10.0, rho_g=1.0, seed=3, jitter=0.2)
+    pos, vel, rho, kind = case.flat()
+    f0 = oracle.forces(oracle.params_for_case(case, xi=0.0), pos, vel, rho, kind)["a_s"]
+    f1 = oracle.forces(oracle.params_for_case(case, xi=0.0, penalty_scope=1), pos, vel, rho, kind)["a_s"]
+    assert np.array_equal(f0, f1)
+    on = oracle.forces(oracle.params_for_case(case), pos, vel, rho, kind)["a_s"]
+    cross = oracle.forces(oracle.params_for_case(case, penalty_scope=1), pos, vel, rho, kind)["a_s"]
+    nopen = oracle.forces(oracle.params_for_case(case, xi=0.0), pos, vel, rho, kind)["a_s"]
+    assert np.abs(cross - on).max() > 1e-6 * np.abs(on).max()          # the same-phase line carried a penalty
+    assert np.abs(cross - nopen).max() > 1e-6 * np.abs(on).max()       # and the cross-phase line still does
