@@ -54,9 +54,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(summary: str, kernel: str):
-    """DRAM bytes per launch of `kernel` from a profiles/ summary, or None if
-    the summary is missing or was taken on other kernel sources."""
+def recorded_traffic(summary: str, kernel: str, key: str = "traffic_bytes_per_launch"):
+    """DRAM bytes (or another recorded per-launch count, `key`) of `kernel`
+    from a profiles/ summary, or None if the summary is missing or was taken
+    on other kernel sources."""
     path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
@@ -64,7 +65,7 @@ def recorded_traffic(summary: str, kernel: str):
     m = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
     if not m or m.group(1) != kernel_source_hash():
         return None
-    m = re.search(r"traffic_bytes_per_launch\[" + re.escape(kernel) + r"\]:\s*([0-9]+)", text)
+    m = re.search(re.escape(key) + r"\[" + re.escape(kernel) + r"\]:\s*([0-9]+)", text)
     return int(m.group(1)) if m else None
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 # algorithmic flops per neighbour pair, counted from the formulas (adds and
@@ -302,6 +303,16 @@ def run_ours(args, dist: Dist):
                                 else "nominal FP64 rate of a GB300"),
                 "flops_per_launch": flops, "pairs": pairs, "pairs_surface": pairs_surf,
                 "avg_launch_ms": round(b_avg * 1e3, 4)}
+    # the issue roof beside the ALU one: warp instructions of one launch (ncu,
+    # recorded with the traffic) over its live duration, against one warp
+    # instruction per scheduler per cycle (152 SMs x 4 x 2.07 GHz)
+    insts = (recorded_traffic(f"sweeps_{args.workload}_f{args.precision}_{args.nbr}.md", "k_sweep_B",
+                              "warp_instructions_per_launch") if f32 and not surf_in_b else None)
+    if insts:
+        issue_peak = 152 * 4 * 2.07e9
+        roofline["issue"] = {"warp_instructions": insts, "achieved": round(insts / b_avg / 1e12, 4),
+                             "peak": round(issue_peak / 1e12, 4), "unit": "T warp-instructions/s",
+                             "frac": round(insts / b_avg / issue_peak, 4)}
     try:                                   # measured FMA roof beside the derived one
         roofline["peak_measured_fma"] = round(S.fma_peak(args.precision)["tflops"], 2)
         roofline["frac_of_measured_fma"] = round(achieved / roofline["peak_measured_fma"], 4)
