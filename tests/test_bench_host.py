@@ -1,0 +1,39 @@
+"""Host logic of bench.py: per-launch counters recorded in a profile summary
+are read only while the summary's source hash equals the kernel sources'
+hash, and each counter by its own key."""
+import os
+
+import bench
+
+
+def test_recorded_counters_follow_the_source_hash(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    here = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for f in bench.KERNEL_SOURCES:                       # the real kernel sources, copied
+        dst = tmp_path / f
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        dst.write_bytes(open(os.path.join(here, f), "rb").read())
+    h = bench.kernel_source_hash()
+    (prof / "s.md").write_text(f"source_sha256: {h}\n"
+                               "traffic_bytes_per_launch[k_sweep_B]: 1234\n"
+                               "warp_instructions_per_launch[k_sweep_B]: 99\n")
+    assert bench.recorded_traffic("s.md", "k_sweep_B") == 1234
+    assert bench.recorded_traffic("s.md", "k_sweep_B", "warp_instructions_per_launch") == 99
+    assert bench.recorded_traffic("s.md", "k_sweep_C") is None
+    assert bench.recorded_traffic("missing.md", "k_sweep_B") is None
+    # a changed kernel source invalidates every recorded counter
+    src = tmp_path / bench.KERNEL_SOURCES[0]
+    src.write_bytes(src.read_bytes() + b"\n// changed\n")
+    assert bench.kernel_source_hash() != h
+    assert bench.recorded_traffic("s.md", "k_sweep_B") is None
+
+
+def test_committed_profile_matches_the_sources():
+    # the committed summary carries the counters the bench line reports
+    got = bench.recorded_traffic("sweeps_oscillating_3d_f32_list.md", "k_sweep_B")
+    assert got is not None and got > 0
+    assert bench.recorded_traffic("sweeps_oscillating_3d_f32_list.md", "k_sweep_B",
+                                  "warp_instructions_per_launch") > 0
+
