@@ -28,6 +28,9 @@ LIMITER_DENSITY, LIMITER_NONE, LIMITER_ZERO, LIMITER_PRINTED = 0, 1, 2, 3
 GRAD_COMMON, GRAD_PRINTED = 0, 1
 PENALTY_NN, PENALTY_EE, PENALTY_SCALAR = 0, 1, 2
 PENALTY_SCOPE_BOTH, PENALTY_SCOPE_CROSS_ONLY = 0, 1
+# one engine with neighbour lists holds at most 2^26 particles (a list entry
+# is j << 6 | cell code in 32 bits; sphst_batch_step rejects more)
+MAX_LIST_ENGINE_PARTICLES = 1 << 26
 VSTAR_CORRECTED, VSTAR_PRINTED = 0, 1
 LOOP_GRAPH, LOOP_HOST = 0, 1
 FIELD_POS, FIELD_VEL, FIELD_RHO, FIELD_PRESSURE, FIELD_PHASE, FIELD_GRADC, FIELD_ACC_VISC = range(7)

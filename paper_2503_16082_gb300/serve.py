@@ -7,7 +7,7 @@ scheduling round:
    back, the case leaves the batch and is released);
 2. admits queued requests, first come first served, while their device
    footprint (``sphst_footprint_bytes``) fits the memory budget next to the
-   resident members;
+   resident members and the engine's particle limit holds;
 3. advances every member by one advection step with one ``sphst_batch_step``
    (all members share one launch sequence; each keeps its own time steps).
 
@@ -27,7 +27,7 @@ from typing import Deque, Dict, List, Optional, Sequence
 
 import numpy as np
 
-from . import (FIELD_POS, FIELD_RHO, FIELD_VEL, OK, SphstError, batch_add, batch_create,
+from . import (FIELD_POS, FIELD_RHO, FIELD_VEL, MAX_LIST_ENGINE_PARTICLES, OK, SphstError, batch_add, batch_create,
                batch_destroy, batch_remove, batch_step, case_from_spec, case_info, default_params,
                destroy, footprint_bytes, read_fields)
 
@@ -68,13 +68,18 @@ class _Request:
 
 
 class Server:
-    """Admission by device-memory budget, one shared batch, FIFO queue."""
+    """Admission by device-memory budget and particle count, one shared
+    batch, FIFO queue.  An error in the background loop fails every queued
+    and resident request with it and stops the loop."""
 
     def __init__(self, precision: int = 32, budget_bytes: float = 150e9,
                  fields: Sequence[int] = (FIELD_POS, FIELD_VEL, FIELD_RHO),
-                 max_members: int = 4096):
+                 max_members: int = 4096, max_particles: int = MAX_LIST_ENGINE_PARTICLES):
         self.precision = precision
         self.budget = float(budget_bytes)
+        self.max_particles = int(max_particles)
+        self.resident_particles = 0
+        self.error: Optional[BaseException] = None
         self.fields = tuple(fields)
         self.max_members = max_members
         self.batch = batch_create(precision)
@@ -111,6 +116,13 @@ class Server:
             if r.footprint > self.budget:
                 fut.set_exception(SphstError(-8, f"request needs {r.footprint} B, budget {self.budget:.0f} B"))
                 return fut
+            if spec.n > self.max_particles:
+                fut.set_exception(SphstError(-1, f"request has {spec.n} particles, an engine holds "
+                                                 f"{self.max_particles}"))
+                return fut
+            if self.error is not None:
+                fut.set_exception(self.error)
+                return fut
             self.next_id += 1
             self.queue.append(r)
         return fut
@@ -136,6 +148,7 @@ class Server:
             batch_remove(self.batch, r.handle)
             destroy(r.handle)
             self.resident_bytes -= r.footprint
+            self.resident_particles -= r.spec.n
             res = Result(fields, info, r.submitted, r.admitted, now)
             self.results.append(res)
             r.future.set_result(res)
@@ -145,7 +158,8 @@ class Server:
         admitted = 0
         with self.lock:
             while (self.queue and len(self.members) < self.max_members
-                   and self.resident_bytes + self.queue[0].footprint <= self.budget):
+                   and self.resident_bytes + self.queue[0].footprint <= self.budget
+                   and self.resident_particles + self.queue[0].spec.n <= self.max_particles):
                 r = self.queue.popleft()
                 try:
                     r.handle = case_from_spec(r.spec, precision=self.precision, **r.params)
@@ -155,6 +169,7 @@ class Server:
                     continue
                 r.admitted = now
                 self.resident_bytes += r.footprint
+                self.resident_particles += r.spec.n
                 self.members.append(r)
                 admitted += 1
         return admitted
@@ -192,12 +207,25 @@ class Server:
     # ------------------------------------------------------- background loop
     def start(self) -> None:
         def loop():
-            while not self._stop.is_set():
-                if self.step() == 0:
-                    self._retire(time.perf_counter())
-                    time.sleep(0.0005)
+            try:
+                while not self._stop.is_set():
+                    if self.step() == 0:
+                        self._retire(time.perf_counter())
+                        time.sleep(0.0005)
+            except BaseException as e:      # noqa: BLE001 - handed to every waiting caller
+                self.fail_all(e)
         self._thread = threading.Thread(target=loop, daemon=True)
         self._thread.start()
+
+    def fail_all(self, e: BaseException) -> None:
+        """Record `e` and fail every queued and resident request with it."""
+        with self.lock:
+            self.error = e
+            pending = list(self.queue) + list(self.members)
+            self.queue.clear()
+        for r in pending:
+            if not r.future.done():
+                r.future.set_exception(e)
 
     def stop(self) -> None:
         self._stop.set()

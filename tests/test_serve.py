@@ -22,6 +22,32 @@ def test_oversized_request_rejected_on_host():
     S.batch_destroy(srv.batch)
 
 
+def test_particle_limit_of_one_engine_on_host():
+    # an engine with neighbour lists holds at most 2^26 particles: a request
+    # above the server's limit is rejected, and admission keeps the sum of
+    # the residents' particles under it
+    spec = sphcases.small_droplet(2, 16)
+    srv = serve.Server(budget_bytes=1e12, max_particles=spec.n - 1)
+    with pytest.raises(S.SphstError):
+        srv.submit(spec, n_adv=1).result(timeout=1)
+    assert serve.Server.__init__.__defaults__[-1] == S.MAX_LIST_ENGINE_PARTICLES == 1 << 26
+    S.batch_destroy(srv.batch)
+
+
+def test_loop_error_fails_every_waiting_request():
+    srv = serve.Server(budget_bytes=1e12)
+    futs = [srv.submit(sphcases.small_droplet(2, 12), n_adv=1) for _ in range(3)]
+    err = S.SphstError(-5, "device lost")
+    srv.fail_all(err)
+    for f in futs:
+        with pytest.raises(S.SphstError):
+            f.result(timeout=1)
+    with pytest.raises(S.SphstError):                 # later requests fail at once
+        srv.submit(sphcases.small_droplet(2, 12), n_adv=1).result(timeout=1)
+    assert not srv.queue
+    S.batch_destroy(srv.batch)
+
+
 def test_footprint_orders_requests():
     srv = serve.Server(budget_bytes=1e12)
     small = srv.footprint(sphcases.small_droplet(2, 12))
