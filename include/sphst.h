@@ -270,20 +270,28 @@ int sphst_profile_step(sphst_case c, double *kernel_ms, int64_t *launches);
  * pool owns every allocation, or a real-time caller that must not allocate
  * after start-up).  It computes what one rebuild computes for the particle
  * order: for n particles at pos_dev (DEVICE pointer, n x 3 doubles, the
- * unused coordinate of 2D ignored) on the grid (origin3, cell_size, ncell3
+ * unused coordinate of 2D ignored) on the grid (origin3, cell_size, ncell3;
+ * origin3 and ncell3 are HOST arrays of 3 entries, the third ignored in 2D,
  * as returned by sphst_debug_grid), keys_dev[k] receives the Morton code of
  * the k-th particle in canonical order and order_dev[k] its index in pos_dev
- * (the order sorts by (Morton code, index)).  keys_dev and order_dev are
- * DEVICE buffers of n entries owned by the caller; cuda_stream (a
- * cudaStream_t as void*, NULL for the default stream) runs the kernels and
- * is synchronised before return.  All intermediate data live in a fixed
- * device array of the library (about 8 MB per GPU, kept until exit): at most
- * 524,288 particles and 2^20 Morton cells (2^(dim*bits) with 2^bits >= the
- * largest ncell); larger inputs return INVALID_ARG.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress), so
- * make the first call on each device before any stream capture.  Calls that
- * overlap on the GPU share the array and race.  Errors: INVALID_ARG, DOMAIN
- * (a particle outside the grid; it is clamped to the nearest cell), CUDA. */
+ * (the order sorts by (Morton code, index)).  The grid is non-periodic: a
+ * position outside it (also one on the far end of a periodic axis, which
+ * the rebuild itself would wrap) is clamped into the nearest cell and
+ * reported as DOMAIN.  keys_dev and order_dev are DEVICE buffers of n
+ * entries owned by the caller; cuda_stream (a cudaStream_t as void*, NULL
+ * for the default stream) runs the kernels, and the call ends by copying a
+ * status word to the host and synchronising that stream.  All intermediate
+ * data live in a fixed device
+ * array of the library (about 10.5 MB per GPU, kept until exit): at most
+ * 524,288 particles, at most 2^10 (3D) or 2^15 (2D) cells per axis, 2^20
+ * Morton cells (2^(dim*bits) with 2^bits >= the largest ncell), and 256
+ * particles in any one cell; larger inputs return INVALID_ARG (for a crowded
+ * cell the outputs are left unwritten).  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress), so make the first
+ * call on each device before any stream capture.  Calls that overlap on the
+ * GPU share the array and race.  Errors: INVALID_ARG, DOMAIN (a
+ * particle outside the grid; it is clamped to the nearest cell and the
+ * outputs hold that clamped order), CUDA. */
 int sphst_cell_order_noalloc(int32_t dim, int64_t n, const double *pos_dev,
                              const double *origin3, double cell_size, const int32_t *ncell3,
                              uint64_t *keys_dev, int64_t *order_dev, void *cuda_stream);
@@ -350,6 +358,13 @@ int sphst_diagnose(sphst_case c, const double *center, double r_in, double r_out
  * duration.  It is the arithmetic roof of the pair sweeps.  Errors:
  * INVALID_ARG, CUDA. */
 int sphst_fma_peak(int32_t precision, double *tflops, double *kernel_ms);
+
+/* Properties of the current GPU that the arithmetic and issue roofs of the
+ * pair sweeps are derived from: the number of SMs, the peak SM clock in kHz
+ * as the device reports it, and (optional) the compute capability.  No
+ * device memory is touched.  Errors: INVALID_ARG, CUDA (no device). */
+int sphst_device_info(int32_t *sm_count, int32_t *max_sm_clock_khz, int32_t *cc_major,
+                      int32_t *cc_minor);
 
 /* Device bytes one case of n particles needs (particle arrays, cell table,
  * scratch), for admission control.  Errors: INVALID_ARG. */

@@ -112,6 +112,8 @@ EXPORTS = {
     "sphst_footprint_bytes": (C.c_int, [C.POINTER(CaseParams), C.c_int64, C.POINTER(C.c_int64)]),
     "sphst_diagnose": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.POINTER(Diagnostics)]),
     "sphst_fma_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "sphst_device_info": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_int32)]),
     "sphst_struct_sizes": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
 }
 
@@ -270,6 +272,14 @@ def fma_peak(precision: int = 32) -> dict:
     return {"tflops": tf.value, "kernel_ms": ms.value}
 
 
+def device_info() -> dict:
+    """SM count, peak SM clock and compute capability of the current GPU
+    (sphst_device_info)."""
+    v = [C.c_int32(0) for _ in range(4)]
+    _check(load().sphst_device_info(*[C.byref(x) for x in v]), "device_info")
+    return {"sm_count": v[0].value, "max_sm_clock_khz": v[1].value, "cc": (v[2].value, v[3].value)}
+
+
 PROFILE_GROUPS = ("rebuild", "setup", "criterion", "sweep_A", "sweep_B", "sweep_C", "sweep_S")
 
 
@@ -291,9 +301,15 @@ def cell_order_noalloc(dim: int, n: int, pos_dev_ptr: int, origin, cell_size: fl
     """Canonical cell order of n particles already on the device, computed
     without any device allocation (all buffers are the caller's; the
     library's fixed scratch array holds the intermediates).  Arguments are
-    raw device pointers, e.g. ``tensor.data_ptr()``."""
-    origin = np.ascontiguousarray(origin, dtype=np.float64)
-    ncell = np.ascontiguousarray(ncell, dtype=np.int32)
+    raw device pointers, e.g. ``tensor.data_ptr()``; origin and ncell have
+    `dim` or 3 entries (a 2D grid is padded to 3)."""
+    def three(v, dtype, pad):
+        v = np.asarray(v, dtype=dtype).reshape(-1)
+        if len(v) not in (dim, 3):
+            raise ValueError(f"origin and ncell need {dim} or 3 entries, got {len(v)}")
+        return np.ascontiguousarray(np.concatenate([v, np.full(3 - len(v), pad, dtype=dtype)]))
+    origin = three(origin, np.float64, 0.0)
+    ncell = three(ncell, np.int32, 1)
     _check(load().sphst_cell_order_noalloc(dim, n, C.c_void_p(pos_dev_ptr), origin.ctypes.data,
                                            cell_size, ncell.ctypes.data, C.c_void_p(keys_dev_ptr),
                                            C.c_void_p(order_dev_ptr), C.c_void_p(cuda_stream)),
