@@ -76,3 +76,22 @@ extern "C" int sphst_fma_peak(int32_t precision, double *tflops, double *kernel_
     }
     return precision == 32 ? sphst::fma_peak<float>(tflops, kernel_ms) : sphst::fma_peak<double>(tflops, kernel_ms);
 }
+
+extern "C" int sphst_device_info(int32_t *sm_count, int32_t *max_sm_clock_khz, int32_t *cc_major,
+                                 int32_t *cc_minor) {
+    if (!sm_count || !max_sm_clock_khz) {
+        sphst::set_error("sm_count and max_sm_clock_khz must be non-NULL");
+        return SPHST_ERR_INVALID_ARG;
+    }
+    int dev = 0, v[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaGetDevice(&dev);
+    const cudaDeviceAttr attrs[4] = {cudaDevAttrMultiProcessorCount, cudaDevAttrClockRate,
+                                     cudaDevAttrComputeCapabilityMajor, cudaDevAttrComputeCapabilityMinor};
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaDeviceGetAttribute(&v[k], attrs[k], dev);
+    if (e != cudaSuccess) return sphst::cuda_fail(e, "device attribute query");
+    *sm_count = v[0];
+    *max_sm_clock_khz = v[1];
+    if (cc_major) *cc_major = v[2];
+    if (cc_minor) *cc_minor = v[3];
+    return SPHST_OK;
+}

@@ -30,6 +30,11 @@ def test_every_declared_symbol_is_exported():
     assert set(names) <= set(S.EXPORTS)
 
 
+def test_device_info_validates_on_the_host():
+    # NULL outputs are rejected before any device call
+    assert S.load().sphst_device_info(None, None, None, None) == S.ERR_INVALID_ARG
+
+
 def test_struct_layout_matches_the_binding():
     sizes = [C.c_int64() for _ in range(3)]
     assert S.load().sphst_struct_sizes(*[C.byref(v) for v in sizes]) == S.OK
