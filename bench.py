@@ -67,13 +67,30 @@ def recorded_traffic(summary: str, kernel: str, key: str = "traffic_bytes_per_la
         return None
     m = re.search(re.escape(key) + r"\[" + re.escape(kernel) + r"\]:\s*([0-9]+)", text)
     return int(m.group(1)) if m else None
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+# FP32 lanes per SM of compute capability 10.x (GB300): the arithmetic roof
+# is SMs x lanes x 2 flop (FMA) x peak SM clock, with the SM count and clock
+# read from the device (sphst_device_info)
+FP32_LANES_PER_SM = 128
+ISSUE_PER_SM = 4             # warp schedulers per SM: one warp instruction each per cycle
 # algorithmic flops per neighbour pair, counted from the formulas (adds and
 # multiplies 1, fused multiply-adds 2, divisions and square roots 1):
 FP64_PEAK_TFLOPS = 1.25      # nominal FP64 (non-tensor) rate of a GB300
 FLOPS_PAIR_B = 59            # geometry + Riemann pressure, every pair (sweep B)
 FLOPS_PAIR_B_SURF = 110      # surface stress + penalty, pairs touching the interface (sweep S)
 L2_BYTES = 129 * 10**6       # L2 of a GB300; a case smaller than twice this is flushed between timed steps
+
+
+def device_roofs():
+    """FP32 arithmetic roof (TFLOP/s) and warp-instruction issue roof
+    (instructions/s) of the current GPU, from its SM count and peak SM
+    clock as the device reports them."""
+    import paper_2503_16082_gb300 as S
+
+    info = S.device_info()
+    sm, ghz = info["sm_count"], info["max_sm_clock_khz"] / 1e6
+    return {"sm_count": sm, "max_sm_clock_mhz": round(ghz * 1e3, 1), "cc": list(info["cc"]),
+            "fp32_tflops": sm * FP32_LANES_PER_SM * 2 * ghz * 1e9 / 1e12,
+            "issue_per_s": sm * ISSUE_PER_SM * ghz * 1e9}
 
 
 def workload(name: str):
@@ -291,7 +308,8 @@ def run_ours(args, dist: Dist):
     flops = FLOPS_PAIR_B * pairs + (FLOPS_PAIR_B_SURF * pairs_surf if surf_in_b else 0)
     achieved = flops / b_avg / 1e12
     f32 = args.precision == 32
-    peak = FP32_PEAK_TFLOPS if f32 else FP64_PEAK_TFLOPS
+    roofs = device_roofs()
+    peak = roofs["fp32_tflops"] if f32 else FP64_PEAK_TFLOPS
     roofline = {"bound": "alu",
                 "kernel": f"k_sweep_B<{'float' if f32 else 'double'}, {spec.dim}, {'false' if surf_in_b else 'true'}>",
                 "achieved": round(achieved, 3),
@@ -299,17 +317,19 @@ def run_ours(args, dist: Dist):
                 "frac": round(achieved / peak, 4),
                 "traffic": (recorded_traffic(f"sweeps_{args.workload}_f{args.precision}_{args.nbr}.md", "k_sweep_B")
                             if f32 and not surf_in_b else None),
-                "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if f32
+                "peak_source": (f"derived from the device: {roofs['sm_count']} SMs x {FP32_LANES_PER_SM} FP32 "
+                                f"lanes x 2 flop x {roofs['max_sm_clock_mhz']:.0f} MHz (peak SM clock)" if f32
                                 else "nominal FP64 rate of a GB300"),
+                "device": {k: roofs[k] for k in ("sm_count", "max_sm_clock_mhz", "cc")},
                 "flops_per_launch": flops, "pairs": pairs, "pairs_surface": pairs_surf,
                 "avg_launch_ms": round(b_avg * 1e3, 4)}
     # the issue roof beside the ALU one: warp instructions of one launch (ncu,
     # recorded with the traffic) over its live duration, against one warp
-    # instruction per scheduler per cycle (152 SMs x 4 x 2.07 GHz)
+    # instruction per scheduler per cycle (SMs x 4 x peak SM clock)
     insts = (recorded_traffic(f"sweeps_{args.workload}_f{args.precision}_{args.nbr}.md", "k_sweep_B",
                               "warp_instructions_per_launch") if f32 and not surf_in_b else None)
     if insts:
-        issue_peak = 152 * 4 * 2.07e9
+        issue_peak = roofs["issue_per_s"]
         roofline["issue"] = {"warp_instructions": insts, "achieved": round(insts / b_avg / 1e12, 4),
                              "peak": round(issue_peak / 1e12, 4), "unit": "T warp-instructions/s",
                              "frac": round(insts / b_avg / issue_peak, 4)}
@@ -361,137 +381,222 @@ def run_ours(args, dist: Dist):
 
 # ------------------------------------------------------ CPU oracle sample
 SAMPLE_SUBSTEPS = 4
+# acoustic substeps per advection step of each workload, as the GPU measures
+# them over the bench's timed steps (the default 20 after 5 warm-up steps):
+# the reference arm rates the oracle at this many substeps per advection
+# step, since it cannot afford whole advection steps of the full case
+SUBSTEPS_PER_STEP = {"oscillating_3d": 37.75, "laplace_2d": 25.2, "impact_3d": 3.0}
 
 
-def oracle_sample(spec, substeps: int = SAMPLE_SUBSTEPS):
-    """Time the oracle as it stands on the full workload: one advection
-    step's set-up (neighbour search, viscous force, transport shift) plus
-    `substeps` acoustic substeps.  Returns (particle-substeps/s, seconds, threads)."""
+_ALL_THREADS = []
+
+
+def oracle_time(spec, substeps: int, threads: int = 0):
+    """Seconds the oracle as it stands takes for one advection step's set-up
+    (neighbour search, correction matrix, viscous force, transport shift)
+    plus `substeps` acoustic substeps of the full workload; (seconds,
+    substeps run, threads used).  threads = 0: all host threads (the OpenMP
+    default seen at the first call; a thread count set for one run stays
+    set in the process, so it is always passed explicitly)."""
     import oracle
 
+    if not _ALL_THREADS:
+        _ALL_THREADS.append(oracle.max_threads())
+    threads = threads or _ALL_THREADS[0]
     pos, vel, rho, kind = spec.flat()
-    P = oracle.params_for_case(spec, max_substeps=substeps)
+    P = oracle.params_for_case(spec, max_substeps=substeps, n_threads=threads)
     t0 = time.perf_counter()
     _, _, _, info, _, _ = oracle.run(P, pos, vel, rho, kind, 1)
-    dt = time.perf_counter() - t0
-    return spec.n_fluid * info["n_sub"] / dt, dt, oracle.max_threads(), info["n_sub"]
+    return time.perf_counter() - t0, info["n_sub"], threads
+
+
+def oracle_split(spec, k: int = SAMPLE_SUBSTEPS):
+    """The oracle's set-up and per-substep costs, from one run with one
+    substep and one with k: per substep = (t_k - t_1) / (k - 1), set-up =
+    t_1 - per substep."""
+    t1, n1, threads = oracle_time(spec, 1)
+    tk, nk, _ = oracle_time(spec, k)
+    per_sub = max(tk - t1, 0.0) / max(nk - n1, 1)
+    return {"setup_s": max(t1 - per_sub, 0.0), "substep_s": per_sub, "threads": threads,
+            "seconds": t1 + tk, "runs": f"set-up + {n1} and set-up + {nk} substeps"}
+
+
+def oracle_rate(spec, split, substeps_per_step: float) -> float:
+    """particle-substeps/s of whole advection steps of `substeps_per_step`
+    substeps, from the measured set-up and per-substep costs."""
+    return spec.n_fluid * substeps_per_step / (split["setup_s"] + substeps_per_step * split["substep_s"])
+
+
+def cpu_baseline(spec, substeps_per_step: float, one_thread: bool = True):
+    """The oracle on the host cores, rated at the GPU's own substeps per
+    advection step; with one_thread, also set-up + 1 substep on one thread
+    (the all-core rate divided by the measured speed-up of that run)."""
+    sp = oracle_split(spec)
+    rate = oracle_rate(spec, sp, substeps_per_step)
+    out = {"value": round(rate, 1), "unit": METRIC, "cores": sp["threads"], "kind": "oracle",
+           "setup_s": round(sp["setup_s"], 3), "substep_s": round(sp["substep_s"], 4),
+           "substeps_per_step": substeps_per_step,
+           "sample": (f"full {spec.name} ({spec.n} particles): {sp['runs']} of the FP64 oracle "
+                      f"({sp['seconds']:.1f} s); rated as whole advection steps of {substeps_per_step} "
+                      f"substeps = set-up + that many substeps")}
+    if one_thread:
+        t1, _, _ = oracle_time(spec, 1, threads=1)
+        speedup = t1 / (sp["setup_s"] + sp["substep_s"])
+        out["one_thread"] = {"value": round(rate / speedup, 1), "setup_plus_1_substep_s": round(t1, 2),
+                             "speedup_all_cores": round(speedup, 2),
+                             "method": "set-up + 1 substep timed on 1 thread; the all-core rate divided by "
+                                       "that run's speed-up"}
+    return out
 
 
 def run_reference(args, dist: Dist):
+    """The oracle, timed as it stands: every timed step runs set-up + 1
+    substep and set-up + SAMPLE_SUBSTEPS substeps, and the value rates the
+    summed set-up and per-substep costs at the workload's substeps per
+    advection step."""
     if dist.rank != 0:
         return None
     spec = workload(args.workload)
     for _ in range(args.warmup):
-        oracle_sample(spec, 1)
-    units = 0.0
-    secs = 0.0
+        oracle_time(spec, 1)
+    setup = sub = secs = 0.0
     threads = 0
     for _ in range(args.steps):
-        rate, dt, threads, nsub = oracle_sample(spec)
-        units += spec.n_fluid * nsub
-        secs += dt
-    value = units / secs
-    return {"value": value, "ms_per_step": secs * 1e3 / max(args.steps, 1), "threads": threads,
-            "sample": f"full {args.workload} ({spec.n} particles): per step one advection-step "
-                      f"set-up + {SAMPLE_SUBSTEPS} acoustic substeps of the FP64 oracle"}
+        sp = oracle_split(spec)
+        setup += sp["setup_s"]
+        sub += sp["substep_s"]
+        secs += sp["seconds"]
+        threads = sp["threads"]
+    n = max(args.steps, 1)
+    split = {"setup_s": setup / n, "substep_s": sub / n}
+    S_sub = SUBSTEPS_PER_STEP.get(args.workload, float(SAMPLE_SUBSTEPS))
+    value = oracle_rate(spec, split, S_sub)
+    return {"value": value, "ms_per_step": (split["setup_s"] + S_sub * split["substep_s"]) * 1e3,
+            "threads": threads, "substeps_per_step": S_sub, "measured_s": secs,
+            "setup_s": split["setup_s"], "substep_s": split["substep_s"],
+            "sample": f"full {args.workload} ({spec.n} particles): per timed step set-up + 1 and set-up + "
+                      f"{SAMPLE_SUBSTEPS} acoustic substeps of the FP64 oracle; value and ms_per_step rate "
+                      f"whole advection steps of {S_sub} substeps (set-up + {S_sub} x per-substep cost)"}
 
 
 # ------------------------------------------------------ batched and served
-def run_batch(args):
-    """The batched workload: independent 2D/3D droplet cases advanced together in one
-    engine (one graph per advection step), against the same cases stepped
-    one at a time through the single-case path."""
+def batch_measure(precision: int = 32, n_cases: int = 512, steps: int = 20, warmup: int = 3,
+                  plain_sample: int = 32, cpu: bool = True, cpu_cases: int = 16):
+    """The batched workload: independent 2D/3D droplet cases advanced
+    together in one engine (one graph per advection step), against the same
+    cases stepped one at a time through the single-case path.  Each case's
+    arithmetic is the same alone and in the batch (bitwise, tested), so the
+    two paths reach every observable with the same error.  Host-timed
+    around each synchronising step call."""
     import torch
 
     import paper_2503_16082_gb300 as S
 
     torch.cuda.set_device(0)
-    specs = sphcases.batch_cases(args.cases)
+    specs = sphcases.batch_cases(n_cases)
     cases = [sp.build() for sp in specs]
     # coarse 3D drops with strong tension cluster beyond the default list
     # capacity of 128 neighbours; the batch uses 192
-    hs = [S.case_from_spec(c, precision=args.precision, max_neighbors=192 if c.dim == 3 else 0)
-          for c in cases]
-    state_bytes = sum(S.footprint_bytes(S.params_from_spec(c, args.precision, max_neighbors=192 if c.dim == 3 else 0),
-                                        c.n) for c in cases)
-    b = S.batch_create(args.precision)
+    kw = [dict(max_neighbors=192 if c.dim == 3 else 0) for c in cases]
+    hs = [S.case_from_spec(c, precision=precision, **k) for c, k in zip(cases, kw)]
+    state_bytes = sum(S.footprint_bytes(S.params_from_spec(c, precision, **k), c.n) for c, k in zip(cases, kw))
+    b = S.batch_create(precision)
     for h in hs:
         S.batch_add(b, h)
-    S.batch_step(b, args.warmup)
+    S.batch_step(b, warmup)
     sub0 = [S.case_info(h)["n_sub"] for h in hs]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    S.batch_step(b, args.steps)
+    S.batch_step(b, steps)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    units = sum(c.n_fluid * (S.case_info(h)["n_sub"] - s0) for c, h, s0 in zip(cases, hs, sub0))
+    subs = [S.case_info(h)["n_sub"] - s0 for h, s0 in zip(hs, sub0)]
+    units = sum(c.n_fluid * n for c, n in zip(cases, subs))
     statuses = [S.case_info(h)["status"] for h in hs]
     for h in hs:
         S.batch_remove(b, h)
         S.destroy(h)
     S.batch_destroy(b)
     # the single-case path on a sample of the same cases
-    k = min(args.plain_sample, len(cases))
+    k = min(plain_sample, len(cases))
     punits, psecs = 0, 0.0
-    for c in cases[:k]:
-        h = S.case_from_spec(c, precision=args.precision, max_neighbors=192 if c.dim == 3 else 0)
-        S.step(h, args.warmup)
+    for c, kk in zip(cases[:k], kw[:k]):
+        h = S.case_from_spec(c, precision=precision, **kk)
+        S.step(h, warmup)
         s0 = S.case_info(h)["n_sub"]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        S.step(h, args.steps)
+        S.step(h, steps)
         torch.cuda.synchronize()
         psecs += time.perf_counter() - t0
         punits += c.n_fluid * (S.case_info(h)["n_sub"] - s0)
         S.destroy(h)
-    # the oracle as it stands on a bounded sample of the same cases (one
-    # advection-step set-up + a few substeps each, about 10 s of host time)
-    cpu = None
-    if not args.no_cpu_baseline:
-        cu, cs, used, threads = 0.0, 0.0, 0, 0
-        for c in cases:
-            _, secs, threads, nsub = oracle_sample(c)
-            cu += c.n_fluid * nsub
-            cs += secs
+    # the oracle as it stands on the first cases: set-up and per-substep
+    # costs measured per case, rated at that case's substeps per advection
+    # step on the GPU (about 10 s of host time)
+    cpu_line = None
+    if cpu:
+        cu = cs = spent = 0.0
+        used, threads = 0, 0
+        for c, n, x in zip(cases, subs, statuses):
+            if x or n == 0:
+                continue
+            sp = oracle_split(c)
+            per_step = n / steps
+            cu += c.n_fluid * per_step
+            cs += sp["setup_s"] + per_step * sp["substep_s"]
+            spent += sp["seconds"]
+            threads = sp["threads"]
             used += 1
-            if cs > 10.0 or used >= 16:
+            if spent > 10.0 or used >= cpu_cases:
                 break
-        cpu = {"value": round(cu / cs, 1), "unit": METRIC, "cores": threads, "kind": "oracle",
-               "sample": f"the batch's first {used} cases, each one advection-step set-up + "
-                         f"{SAMPLE_SUBSTEPS} acoustic substeps of the FP64 oracle, {cs:.1f} s"}
-    line = {"metric": METRIC, "mode": "batch", "value": round(units / dt, 1), "unit": METRIC,
+        cpu_line = {"value": round(cu / cs, 1) if cs > 0 else None, "unit": METRIC, "cores": threads,
+                    "kind": "oracle",
+                    "sample": f"the batch's first {used} healthy cases: set-up + 1 and set-up + {SAMPLE_SUBSTEPS} "
+                              f"substeps of the FP64 oracle each ({spent:.1f} s), rated at each case's substeps "
+                              f"per advection step on the GPU"}
+    return {"metric": METRIC, "value": round(units / dt, 1), "unit": METRIC,
             "cases": len(cases), "particles": int(sum(c.n for c in cases)),
-            "fluid_particles": int(sum(c.n_fluid for c in cases)), "steps": args.steps,
-            "warmup": args.warmup, "seconds": round(dt, 3), "failed_cases": int(sum(1 for x in statuses if x)),
+            "fluid_particles": int(sum(c.n_fluid for c in cases)), "steps": steps,
+            "warmup": warmup, "seconds": round(dt, 3), "failed_cases": int(sum(1 for x in statuses if x)),
             "failed_status": {str(x): int(sum(1 for y in statuses if y == x)) for x in set(statuses) if x},
-            "failed_specs": [dict(dim=sp.dim, n=c.n, sigma=round(sp.sigma, 3), shape=sp.shape)
-                             for sp, c, x in zip(specs, cases, statuses) if x][:8],
+            "failed_specs": [dict(index=sp.index, dim=sp.dim, n=c.n, sigma=round(sp.sigma, 3), shape=sp.shape,
+                                  status=x) for sp, c, x in zip(specs, cases, statuses) if x][:8],
             "plain_single_case": {"value": round(punits / psecs, 1), "cases_sampled": k},
-            "speedup_vs_plain": round((units / dt) / (punits / psecs), 2), "cpu_baseline": cpu,
-            "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
-            "config": {"workload": "batch_cases seed 20250320", "step": "one advection step of every case",
+            "speedup_vs_plain": round((units / dt) / (punits / psecs), 2),
+            "same_results_as_plain": "bitwise per case (tested), so equal Laplace-pressure error",
+            "cpu_baseline": cpu_line, "timing": "host clock around synchronising step calls",
+            "dtype": "f32" if precision == 32 else "f64", "data": "synthetic",
+            "config": {"workload": f"batch_cases seed {sphcases.BATCH_SEED}", "step": "one advection step of every case",
                        "l2": f"inputs larger than L2 ({state_bytes / 1e9:.1f} GB of case state vs 129 MB L2)"}}
+
+
+def run_batch(args):
+    line = batch_measure(args.precision, args.cases, args.steps, args.warmup, args.plain_sample,
+                         cpu=not args.no_cpu_baseline)
+    line["mode"] = "batch"
     print(json.dumps(line), flush=True)
 
 
-def run_serve(args):
-    """The served workload: Poisson arrivals of droplet cases into the continuous-batching
-    server; p50/p99 time from submission to result."""
+def serve_measure(precision: int = 32, requests: int = 200, rate: float = 50.0, n_hi: float = 2e6,
+                  substeps: int = 128, capacity_cases: int = 24, budget_gb: float = 150.0):
+    """The served workload: Poisson arrivals of droplet cases into the
+    continuous-batching server; p50/p99 time from submission to result."""
     import torch
 
     import paper_2503_16082_gb300 as S
     from paper_2503_16082_gb300 import serve
 
     torch.cuda.set_device(0)
-    specs = sphcases.served_stream(args.requests, rate=args.rate, n_hi=args.serve_n_hi)
+    specs = sphcases.served_stream(requests, rate=rate, n_hi=n_hi)
     cases = [sp.build() for sp in specs]
     # capacity first: a batch of the stream's first cases, one advection step
     # each after a warm-up step; the offered load (arrival rate x mean fluid
     # particles x substeps per request) must stay below 0.9 of it, else the
     # substep count per request is lowered
-    probe = cases[:min(len(cases), args.capacity_cases)]
-    b = S.batch_create(args.precision)
-    hs = [S.case_from_spec(c, precision=args.precision) for c in probe]
+    probe = cases[:min(len(cases), capacity_cases)]
+    b = S.batch_create(precision)
+    hs = [S.case_from_spec(c, precision=precision) for c in probe]
     for h in hs:
         S.batch_add(b, h)
     S.batch_step(b, 1)
@@ -507,11 +612,11 @@ def run_serve(args):
         S.destroy(h)
     S.batch_destroy(b)
     mean_fluid = float(np.mean([c.n_fluid for c in cases]))
-    n_sub = args.serve_substeps
-    while n_sub > 1 and args.rate * mean_fluid * n_sub > 0.9 * capacity:
+    n_sub = substeps
+    while n_sub > 1 and rate * mean_fluid * n_sub > 0.9 * capacity:
         n_sub -= 1
-    offered = args.rate * mean_fluid * n_sub
-    srv = serve.Server(precision=args.precision, budget_bytes=args.budget_gb * 1e9)
+    offered = rate * mean_fluid * n_sub
+    srv = serve.Server(precision=precision, budget_bytes=budget_gb * 1e9)
     srv.start()
     t0 = time.perf_counter()
     futs = []
@@ -526,18 +631,24 @@ def run_serve(args):
     st = srv.stats()
     srv.close()
     lat = np.array([r.latency for r in res])
-    line = {"metric": METRIC, "mode": "serve", "value": round(st["particle_substeps"] / wall, 1),
-            "unit": METRIC, "requests": len(res), "arrival_rate_per_s": args.rate,
+    return {"metric": METRIC, "value": round(st["particle_substeps"] / wall, 1),
+            "unit": METRIC, "requests": len(res), "arrival_rate_per_s": rate,
             "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
             "p99_latency_s": round(float(np.percentile(lat, 99)), 4),
             "gpu_busy_fraction": round(st["busy_s"] / wall, 3), "rounds": st["rounds"],
             "failed": int(sum(1 for r in res if r.info["status"])),
-            "substeps_per_request": n_sub, "substeps_requested": args.serve_substeps,
+            "substeps_per_request": n_sub, "substeps_requested": substeps,
             "capacity": round(capacity, 1), "offered_load": round(offered, 1),
-            "offered_fraction": round(offered / capacity, 3), "budget_gb": args.budget_gb,
-            "particles_per_request_range": [5e3, args.serve_n_hi],
-            "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
-            "config": {"workload": "served_stream seed 20250321", "wall_s": round(wall, 2)}}
+            "offered_fraction": round(offered / capacity, 3), "budget_gb": budget_gb,
+            "particles_per_request_range": [5e3, n_hi],
+            "dtype": "f32" if precision == 32 else "f64", "data": "synthetic",
+            "config": {"workload": f"served_stream seed {sphcases.SERVE_SEED}", "wall_s": round(wall, 2)}}
+
+
+def run_serve(args):
+    line = serve_measure(args.precision, args.requests, args.rate, args.serve_n_hi, args.serve_substeps,
+                         args.capacity_cases, args.budget_gb)
+    line["mode"] = "serve"
     print(json.dumps(line), flush=True)
 
 
@@ -570,6 +681,11 @@ def main():
     ap.add_argument("--capacity-cases", type=int, default=24)
     ap.add_argument("--serve-n-hi", type=float, default=2e6)
     ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--batch-steps", type=int, default=5,
+                    help="timed advection steps of the batch object in the default line")
+    ap.add_argument("--no-batch", action="store_true", help="leave the batch object out of the default line")
+    ap.add_argument("--no-serve", action="store_true", help="leave the serve object out of the default line")
+    ap.add_argument("--no-one-thread", action="store_true", help="skip the one-thread oracle run")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -594,14 +710,17 @@ def main():
             return
         spec_n = workload(args.workload)
         config.update(particles=spec_n.n, fluid_particles=spec_n.n_fluid,
-                      l2="not applicable: the oracle runs on the host cores")
+                      l2="not applicable: the oracle runs on the host cores",
+                      substeps_per_step=res["substeps_per_step"])
         line = {"impl": "reference", "metric": METRIC, "value": round(res["value"], 1),
                 "unit": METRIC, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(res["ms_per_step"], 1), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config,
                 "cpu_baseline": {"value": round(res["value"], 1), "unit": METRIC, "cores": res["threads"],
-                                 "kind": "oracle", "sample": res["sample"]},
+                                 "kind": "oracle", "sample": res["sample"],
+                                 "setup_s": round(res["setup_s"], 3), "substep_s": round(res["substep_s"], 4),
+                                 "measured_s": round(res["measured_s"], 1)},
                 "e2e": {"value": round(res["value"], 1), "unit": METRIC,
                         "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
@@ -613,11 +732,17 @@ def main():
                   substeps_per_step=round(res["n_sub"] / args.steps, 2))
     cpu = None
     if rank == 0 and ws <= 1 and not args.no_cpu_baseline:
-        spec = workload(args.workload)
-        rate, dt, threads, nsub = oracle_sample(spec)
-        cpu = {"value": round(rate, 1), "unit": METRIC, "cores": threads, "kind": "oracle",
-               "sample": f"full {args.workload}: one advection-step set-up + {nsub} acoustic "
-                         f"substeps of the FP64 oracle, {dt:.1f} s"}
+        cpu = cpu_baseline(workload(args.workload), round(res["n_sub"] / args.steps, 2),
+                           one_thread=not args.no_one_thread)
+    # the batched and served workloads on the same GPU, bounded in time
+    extra = {}
+    if rank == 0 and ws <= 1 and args.precision == 32 and args.workload == "oscillating_3d":
+        if not args.no_batch:
+            extra["batch"] = batch_measure(32, args.cases, args.batch_steps, 3, args.plain_sample,
+                                           cpu=not args.no_cpu_baseline)
+        if not args.no_serve:
+            extra["serve"] = serve_measure(32, args.requests, args.rate, args.serve_n_hi, args.serve_substeps,
+                                           args.capacity_cases, args.budget_gb)
     dist.close()
     if rank != 0:
         return
@@ -627,6 +752,7 @@ def main():
             "data": "synthetic", "config": config, "roofline": res["roofline"],
             "cpu_baseline": cpu, "e2e": res["e2e"], "gpu_launches": res["gpu_launches"],
             "clocks": res["clocks"], "kernel_ms_one_step": res["kernel_ms"]}
+    line.update(extra)
     print(json.dumps(line), flush=True)
 
 

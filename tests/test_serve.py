@@ -119,3 +119,46 @@ def test_substep_stopping_rule():
     assert np.array_equal(r.fields[S.FIELD_POS], S.read_fields(h, S.FIELD_POS, 2))
     S.destroy(h)
     srv.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision,tol1,tol2", [(64, 1e-12, 1e-11), (32, 2e-4, 1e-3)])
+def test_served_results_equal_the_oracle(precision, tol1, tol2):
+    """Seeded cases of the batched workload (seed 20250320, 2D, all three
+    shapes, sigma 0.12-3.9) served with a memory budget that holds two at a
+    time, so later requests are admitted while others run; every result is
+    compared with the FP64 oracle's run of that case alone (fluid
+    particles, each field against its maximum)."""
+    import oracle
+
+    idx = (192, 481, 89, 153, 437, 64)
+    specs = [sphcases.batch_cases(512)[k].build() for k in idx]
+    steps = [1, 2, 1, 2, 1, 1]
+    srv = serve.Server(precision=precision, budget_bytes=1e12,
+                       fields=(S.FIELD_POS, S.FIELD_VEL, S.FIELD_RHO, S.FIELD_GRADC))
+    srv.budget = 2.2 * max(srv.footprint(s) for s in specs)
+    srv.start()
+    futs = []
+    for s, n in zip(specs, steps):
+        futs.append(srv.submit(s, n_adv=n))
+        time.sleep(0.005)
+    results = [f.result(timeout=300) for f in futs]
+    srv.stop()
+    srv.close()
+    assert any(r.admitted > min(q.finished for q in results) for r in results)   # admitted mid-run
+    for s, n, r in zip(specs, steps, results):
+        assert r.info["status"] == 0 and r.info["n_adv"] == n
+        pos, vel, rho, kind = s.flat()
+        p1, v1, r1, oinfo, gC, _ = oracle.run(oracle.params_for_case(s), pos, vel, rho, kind, n)
+        assert r.info["n_sub"] == oinfo["n_sub"]
+        fl = kind < 2
+        rho0 = np.asarray(s.fluid_props()[0])[kind[fl]]
+        d = s.dim
+        pairs = [(r.fields[S.FIELD_POS][fl] - pos[fl, :d], p1[fl, :d] - pos[fl, :d]),
+                 (r.fields[S.FIELD_VEL][fl], v1[fl, :d]),
+                 (r.fields[S.FIELD_RHO][fl] - rho0, r1[fl] - rho0),
+                 (r.fields[S.FIELD_GRADC][fl], gC[fl, :d])]
+        tol = tol1 if n == 1 else tol2
+        for a, b in pairs:
+            scale = np.abs(b).max()
+            assert np.abs(a - b).max() <= tol * scale + 4 * np.spacing(1000.0)
