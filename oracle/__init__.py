@@ -92,6 +92,8 @@ def _load():
                                           P(C.c_uint64), ip, lp]
             lib.ora_riemann_pair.restype = None
             lib.ora_riemann_pair.argtypes = [P(Params), d, d, dp, d, d, dp, dp, dp]
+            lib.ora_surface_pair.restype = None
+            lib.ora_surface_pair.argtypes = [P(Params), i32, i32, dp, dp, dp, d, dp]
             lib.ora_dt_advection.restype = d
             lib.ora_dt_advection.argtypes = [P(Params), dp, ip]
             lib.ora_dt_acoustic.restype = d
@@ -219,6 +221,18 @@ def riemann_pair(params: Params, rho_i, p_i, v_i, rho_j, p_j, v_j, e):
     lib.ora_riemann_pair(C.byref(params), rho_i, p_i, _dp(v_i), rho_j, p_j, _dp(v_j),
                          _dp(e), _dp(out))
     return out[0], out[1], out[2], out[3], out[4:7].copy()
+
+
+def surface_pair(params: Params, k_i: int, k_j: int, gradC_i, gradC_j, e, r: float) -> np.ndarray:
+    """S_ij e_ij of Eq. 33 for one pair of fluid particles (phases k_i, k_j
+    in {0, 1}) with colour gradients gradC_i, gradC_j, unit vector e_ij and
+    distance r; the pair adds it times W'(r) V_j / rho_i to a^s_i."""
+    lib = _load()
+    three = lambda v: np.ascontiguousarray(np.pad(np.asarray(v, float), (0, 3 - len(v))))
+    gi, gj, ee = three(gradC_i), three(gradC_j), three(e)
+    out = np.zeros(3)
+    lib.ora_surface_pair(C.byref(params), int(k_i), int(k_j), _dp(gi), _dp(gj), _dp(ee), float(r), _dp(out))
+    return out[:params.dim].copy()
 
 
 def dt_advection(params: Params, vmax, present=(1, 1)) -> float:

@@ -59,15 +59,20 @@
  *               with the viscous force and added to the positions once per
  *               advection step.
  *
- * Parity unpinned (no closed form or invariant fixes it; only agreement
- * with the CUDA path and the integral observables check it): the magnitude
- * of the same-phase penalty term away from special cases.  The integrator
- * and the wall reading's mirror pressure and volume are pinned in the
- * linear regime by acoustic modes (a standing wave, and the lowest mode
+ * Pinned by closed forms: every term of Eq. 33 for a single pair.  The
+ * cross-phase line by an isolated pair of different fluids; the same-phase
+ * line, through ora_surface_pair (the routine the force loop calls), by
+ * three configurations that reduce by hand: normals across the pair (no
+ * penalty with the default contraction, a repulsion with A^T A / |A|),
+ * normals along the pair (T-bar removes the penalty) and mirrored normals
+ * (a closed form that separates the three contractions of Eq. 30).  The
+ * integrator and the wall reading's mirror pressure and volume are pinned in
+ * the linear regime by acoustic modes (a standing wave, and the lowest mode
  * between walls), v* = v_w at a wall by the water hammer (p = rho c0 U
  * behind the front), the wall's dissipative term (mirrored normal velocity,
- * limiter) by the closed form of a fluid particle beside one wall particle;
- * the cross-phase penalty by the closed form of an isolated pair.
+ * limiter) by the closed form of a fluid particle beside one wall particle.
+ * Integral observables (the Laplace jump, the oscillation period) are
+ * checked against the paper's closed forms in runs of the whole scheme.
  */
 #include <math.h>
 #include <stdint.h>
@@ -722,6 +727,95 @@ static void viscous_acc(const ora_params *P, const state_t *S, const pairs_t *pp
     }
 }
 
+/* The pair matrix S_ij of Eq. 33 (the bracket that multiplies grad_i W_ij V_j)
+ * for fluids ki, kj with stresses si, sj (Eq. 24 and the projections below
+ * Eq. 33), colour gradients gi, gj, unit vector e = e_ij and distance r:
+ *   same phase:  Pi_i + Pi_j + xi gamma T-bar C-hat / r
+ *   other phase: 2 phi_j Pi_i + 2 phi_i Pi_j - 4 phi_i phi_j xi gamma N-bar C-hat / r
+ * with C-hat from Eq. 30 (the contraction of the flag penalty_form) and
+ * grad C-bar from Eq. 28 (the colour side of the flag grad_mode). */
+static void surface_pair_matrix(const ora_params *P, int32_t ki, int32_t kj, const stress_t *si,
+                                const stress_t *sj, const double *gi, const double *gj,
+                                const double *e, double r, double xi, double *S)
+{
+    const int dim = P->dim;
+    int same = kj == ki;
+    double Cij = same ? 0.0 : 1.0;
+    double phi_i = phi_of(P, ki, kj), phi_j = phi_of(P, kj, ki);
+    /* Eq. 28 average gradient; reading: common colour side */
+    double gbar[3] = {0, 0, 0};
+    double sgn = (same || P->grad_mode == 1) ? 1.0 : -1.0;
+    for (int d = 0; d < dim; ++d)
+        gbar[d] = 0.5 * (gi[d] + sgn * gj[d]);
+    /* Eq. 30: C-hat = C_ij I - (A/|A|) A, A = gbar (x) r_ij, with the
+     * matrix product taken as A A^T (penalty_form 0) or A^T A (1) */
+    double rvec[3] = {0, 0, 0};
+    for (int d = 0; d < dim; ++d) rvec[d] = r * e[d];
+    double A[9] = {0}, AtA[9] = {0}, normA = 0.0;
+    for (int a = 0; a < dim; ++a)
+        for (int b = 0; b < dim; ++b) {
+            A[3 * a + b] = gbar[a] * rvec[b];
+            normA += A[3 * a + b] * A[3 * a + b];
+        }
+    normA = sqrt(normA);
+    for (int a = 0; a < dim; ++a)
+        for (int b = 0; b < dim; ++b) {
+            double s = 0.0;
+            for (int c = 0; c < dim; ++c)
+                s += P->penalty_form == 0 ? A[3 * a + c] * A[3 * b + c]
+                                          : A[3 * c + a] * A[3 * c + b];
+            AtA[3 * a + b] = s;
+        }
+    double Chat[9] = {0};
+    double gr = dot3(gbar, rvec, dim);            /* Eq. 29: scalar C-hat */
+    for (int a = 0; a < dim; ++a)
+        for (int b = 0; b < dim; ++b)
+            Chat[3 * a + b] = P->penalty_form == 2
+                ? (a == b ? Cij - gr : 0.0)
+                : (a == b ? Cij : 0.0) - (normA > 0.0 ? AtA[3 * a + b] / normA : 0.0);
+    /* projection: T-bar (same phase) or N-bar (other phase) */
+    double M[9] = {0};
+    for (int a = 0; a < dim; ++a)
+        for (int b = 0; b < dim; ++b)
+            M[3 * a + b] = same ? 0.5 * (si->T[3 * a + b] + sj->T[3 * a + b])
+                                : 0.5 * (si->N[3 * a + b] + sj->N[3 * a + b]);
+    double MC[9] = {0};
+    for (int a = 0; a < dim; ++a)
+        for (int b = 0; b < dim; ++b) {
+            double s = 0.0;
+            for (int c = 0; c < dim; ++c) s += M[3 * a + c] * Chat[3 * c + b];
+            MC[3 * a + b] = s;
+        }
+    memset(S, 0, 9 * sizeof(double));
+    for (int a = 0; a < dim; ++a)
+        for (int b = 0; b < dim; ++b) {
+            double pen = xi * P->gamma * MC[3 * a + b] / r;
+            S[3 * a + b] = same
+                ? si->Pi[3 * a + b] + sj->Pi[3 * a + b] + (P->penalty_scope == 1 ? 0.0 : pen)
+                : 2.0 * phi_j * si->Pi[3 * a + b] + 2.0 * phi_i * sj->Pi[3 * a + b]
+                  - 4.0 * phi_i * phi_j * pen;
+        }
+}
+
+/* One pair's surface term of Eq. 33 on its own: S_ij e_ij for fluids ki and
+ * kj (0 or 1) with colour gradients gi, gj (3 entries), unit vector e (3
+ * entries) and distance r; out (3 entries) receives S_ij e_ij, so that the
+ * pair adds out W'_ij V_j / rho_i to a^s_i. */
+void ora_surface_pair(const ora_params *P, int32_t ki, int32_t kj, const double *gi,
+                      const double *gj, const double *e, double r, double *out)
+{
+    stress_t si, sj;
+    surface_stress(P, gi, &si);
+    surface_stress(P, gj, &sj);
+    double S[9];
+    surface_pair_matrix(P, ki, kj, &si, &sj, gi, gj, e, r, ora_xi(P), S);
+    for (int a = 0; a < 3; ++a) {
+        double s = 0.0;
+        for (int b = 0; b < P->dim; ++b) s += S[3 * a + b] * e[b];
+        out[a] = a < P->dim ? s : 0.0;
+    }
+}
+
 /* Eq. 7 (pressure) and Eq. 33 (surface tension with the projected penalty),
  * the latter divided by m_i.  ap and as receive the two accelerations. */
 static void pressure_surface_acc(const ora_params *P, const state_t *S,
@@ -771,65 +865,11 @@ static void pressure_surface_acc(const ora_params *P, const state_t *S,
                 if (!is_fluid(kj)) continue;
                 stress_t sj;
                 surface_stress(P, gradC + 3 * j, &sj);
-                int same = kj == ki;
-                double Cij = same ? 0.0 : 1.0;
-                double phi_i = phi_of(P, ki, kj), phi_j = phi_of(P, kj, ki);
-                /* Eq. 28 average gradient; reading: common colour side */
-                double gbar[3] = {0, 0, 0};
-                double sgn = (same || P->grad_mode == 1) ? 1.0 : -1.0;
-                for (int d = 0; d < dim; ++d)
-                    gbar[d] = 0.5 * (gradC[3 * i + d] + sgn * gradC[3 * j + d]);
-                /* Eq. 30: C-hat = C_ij I - (A/|A|) A, A = gbar (x) r_ij, with the
-                 * matrix product taken as A A^T (penalty_form 0) or A^T A (1) */
-                double rvec[3] = {0, 0, 0};
-                for (int d = 0; d < dim; ++d) rvec[d] = pp->r[k] * e[d];
-                double A[9] = {0}, AtA[9] = {0}, normA = 0.0;
-                for (int a = 0; a < dim; ++a)
-                    for (int b = 0; b < dim; ++b) {
-                        A[3 * a + b] = gbar[a] * rvec[b];
-                        normA += A[3 * a + b] * A[3 * a + b];
-                    }
-                normA = sqrt(normA);
-                for (int a = 0; a < dim; ++a)
-                    for (int b = 0; b < dim; ++b) {
-                        double s = 0.0;
-                        for (int c = 0; c < dim; ++c)
-                            s += P->penalty_form == 0 ? A[3 * a + c] * A[3 * b + c]
-                                                      : A[3 * c + a] * A[3 * c + b];
-                        AtA[3 * a + b] = s;
-                    }
-                double Chat[9] = {0};
-                double gr = dot3(gbar, rvec, dim);            /* Eq. 29: scalar C-hat */
-                for (int a = 0; a < dim; ++a)
-                    for (int b = 0; b < dim; ++b)
-                        Chat[3 * a + b] = P->penalty_form == 2
-                            ? (a == b ? Cij - gr : 0.0)
-                            : (a == b ? Cij : 0.0) - (normA > 0.0 ? AtA[3 * a + b] / normA : 0.0);
-                /* projection: T-bar (same phase) or N-bar (other phase) */
-                double M[9] = {0};
-                for (int a = 0; a < dim; ++a)
-                    for (int b = 0; b < dim; ++b)
-                        M[3 * a + b] = same ? 0.5 * (si.T[3 * a + b] + sj.T[3 * a + b])
-                                            : 0.5 * (si.N[3 * a + b] + sj.N[3 * a + b]);
-                double MC[9] = {0};
-                for (int a = 0; a < dim; ++a)
-                    for (int b = 0; b < dim; ++b) {
-                        double s = 0.0;
-                        for (int c = 0; c < dim; ++c) s += M[3 * a + c] * Chat[3 * c + b];
-                        MC[3 * a + b] = s;
-                    }
-                double S[9] = {0};
-                for (int a = 0; a < dim; ++a)
-                    for (int b = 0; b < dim; ++b) {
-                        double pen = xi * P->gamma * MC[3 * a + b] / pp->r[k];
-                        S[3 * a + b] = same
-                            ? si.Pi[3 * a + b] + sj.Pi[3 * a + b] + (P->penalty_scope == 1 ? 0.0 : pen)
-                            : 2.0 * phi_j * si.Pi[3 * a + b] + 2.0 * phi_i * sj.Pi[3 * a + b]
-                              - 4.0 * phi_i * phi_j * pen;
-                    }
+                double Sij[9];
+                surface_pair_matrix(P, ki, kj, &si, &sj, gradC + 3 * i, gradC + 3 * j, e, pp->r[k], xi, Sij);
                 for (int a = 0; a < dim; ++a) {
                     double s = 0.0;
-                    for (int b = 0; b < dim; ++b) s += S[3 * a + b] * gradW[b];
+                    for (int b = 0; b < dim; ++b) s += Sij[3 * a + b] * gradW[b];
                     a_s[a] += s * Vj / rho_i;
                 }
             }

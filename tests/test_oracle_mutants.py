@@ -12,8 +12,10 @@ reversed, the density update reversed (Eq. 6), the factor 2 of Eq. 6 dropped
 pressure dropped, the wall volume doubled, v* = v_i instead of the wall's
 velocity in the continuity equation, the wall's normal velocity not
 mirrored in the Riemann state, the cross-phase penalty weight
-4 phi_i phi_j halved (Eq. 33).  An unmodified copy passes
-the same harness."""
+4 phi_i phi_j halved (Eq. 33), the same-phase penalty of Eq. 33 halved or
+dropped, its projection T-bar replaced by N-bar, and the contraction of
+Eq. 30 transposed (A^T A for A A^T).  An unmodified copy passes the same
+harness."""
 import os
 import subprocess
 import sys
@@ -35,8 +37,15 @@ MUTANTS = {
                                "return 5.0 * wendland_alpha(dim, h) * q * t * t * t / h;"),
     "pressure force sign": ("a_p[d] += -2.0 / rho_i * Ps * gradW[d] * Vj;",
                             "a_p[d] += 2.0 / rho_i * Ps * gradW[d] * Vj;"),
-    "neighbour stress dropped": ("? si.Pi[3 * a + b] + sj.Pi[3 * a + b] + (P->penalty_scope",
-                                 "? si.Pi[3 * a + b] + si.Pi[3 * a + b] + (P->penalty_scope"),
+    "neighbour stress dropped": ("? si->Pi[3 * a + b] + sj->Pi[3 * a + b] + (P->penalty_scope",
+                                 "? si->Pi[3 * a + b] + si->Pi[3 * a + b] + (P->penalty_scope"),
+    "same-phase penalty halved": ("(P->penalty_scope == 1 ? 0.0 : pen)", "(P->penalty_scope == 1 ? 0.0 : 0.5 * pen)"),
+    "same-phase penalty dropped": ("(P->penalty_scope == 1 ? 0.0 : pen)", "(P->penalty_scope == 1 ? 0.0 : 0.0 * pen)"),
+    "same-phase projection N-bar instead of T-bar": (
+        "M[3 * a + b] = same ? 0.5 * (si->T[3 * a + b] + sj->T[3 * a + b])",
+        "M[3 * a + b] = same ? 0.5 * (si->N[3 * a + b] + sj->N[3 * a + b])"),
+    "penalty contraction transposed": ("s += P->penalty_form == 0 ? A[3 * a + c] * A[3 * b + c]",
+                                       "s += P->penalty_form == 0 ? A[3 * c + a] * A[3 * c + b]"),
     "colour weight of j": ("g[d] += 2.0 * phi_i * Cij * pp->dW[k] * pp->e[3 * k + d] * Vj;",
                            "g[d] += 2.0 * (1.0 - phi_i) * Cij * pp->dW[k] * pp->e[3 * k + d] * Vj;"),
     "arithmetic pair viscosity": ("? 2.0 * P->eta[ki] * P->eta[kj] / (P->eta[ki] + P->eta[kj])",

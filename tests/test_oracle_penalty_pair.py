@@ -53,3 +53,134 @@ def test_isolated_cross_phase_pair(penalty_form, r_over_dx):
     assert out["a_s"][1, :2] == pytest.approx(a_j, rel=1e-12, abs=1e-12 * abs(a_j[0]))
     # momentum: m_i a_i + m_j a_j = 0 (m = rho0 V)
     assert rho_a * out["a_s"][0, 0] + rho_b * out["a_s"][1, 0] == pytest.approx(0.0, abs=1e-12 * rho_a * abs(a_i[0]))
+
+
+# ---------------------------------------------------------------------------
+# The same-phase line of Eq. 33, S_ij e = (Pi_i + Pi_j) e + xi gamma T-bar C-hat e / r
+# (C_ij = 0), through the oracle's pair entry point, which is the routine its
+# force loop calls for every fluid pair.  For a pair of one phase with
+# colour gradients G_i n_i and G_j n_j, Eqs. 24-30 reduce by hand to:
+#   Pi e = gamma G (e - n (n.e));  grad C-bar = (G_i n_i + G_j n_j) / 2;
+#   C-hat e = -r |grad C-bar| (nbar.e) nbar      (contraction A A^T / |A|, the default)
+#           = -r |grad C-bar| e                  (A^T A / |A|, penalty_form 1)
+#           = -r (grad C-bar . e) e              (the scalar Eq. 29, penalty_form 2);
+#   T-bar c = c - (n_i (n_i.c) + n_j (n_j.c)) / 2.
+# Three configurations give closed forms that do not repeat those steps:
+# ---------------------------------------------------------------------------
+def rotation(seed):
+    q, _ = np.linalg.qr(np.random.default_rng(seed).normal(size=(3, 3)))
+    return q * np.sign(np.linalg.det(q))
+
+
+SAME_PHASE_GAMMA, SAME_PHASE_XI = 0.7, 2.5
+
+
+def same_phase_params(dim, form):
+    return oracle.make_params(dim, 0.1, 0.13, 10.0, SAME_PHASE_GAMMA, rho0=(3.0, 1.0), eta=(0.1, 0.1),
+                              xi=SAME_PHASE_XI, penalty_form=form)
+
+
+@pytest.mark.parametrize("form", [0, 1, 2])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_same_phase_normals_across_the_pair(form, kind):
+    """n_i = n_j = n perpendicular to e: the stresses pass e unchanged,
+    grad C-bar has no component along e, so the default and the scalar
+    contraction give no penalty while A^T A/|A| repels along the pair:
+    S e = gamma (G_i + G_j) e, times (1 - xi/2) for A^T A/|A|."""
+    g, xi = SAME_PHASE_GAMMA, SAME_PHASE_XI
+    for dim, R in ((2, np.eye(3)), (3, rotation(3))):
+        P = same_phase_params(dim, form)
+        n, e = R @ np.array([0.0, 1.0, 0.0]), R @ np.array([1.0, 0.0, 0.0])
+        Gi, Gj, r = 4.0, 2.5, 0.11
+        out = oracle.surface_pair(P, kind, kind, (Gi * n)[:dim], (Gj * n)[:dim], e[:dim], r)
+        want = g * (Gi + Gj) * (1.0 - xi / 2.0 if form == 1 else 1.0) * e[:dim]
+        assert out == pytest.approx(want, rel=1e-13, abs=1e-13 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("form", [0, 1, 2])
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_same_phase_normals_along_the_pair(form, sign):
+    """n_i = n_j = n = +-e: Pi e = 0 and C-hat e lies along n, which T-bar
+    removes, for every contraction: S e = 0 (the projection of Eq. 33 keeps
+    the same-phase penalty tangential)."""
+    for dim, R in ((2, np.eye(3)), (3, rotation(4))):
+        P = same_phase_params(dim, form)
+        e = R @ np.array([1.0, 0.0, 0.0])
+        n = sign * e
+        out = oracle.surface_pair(P, 0, 0, (3.0 * n)[:dim], (1.2 * n)[:dim], e[:dim], 0.09)
+        assert np.abs(out).max() <= 1e-14
+
+
+@pytest.mark.parametrize("form", [0, 1, 2])
+@pytest.mark.parametrize("alpha,beta", [(0.4, 0.0), (0.9, 0.3), (0.25, 1.2), (1.1, -0.7)])
+def test_same_phase_mirrored_normals(form, alpha, beta):
+    """n_i = (cos a, sin a), n_j = (cos a, -sin a), G_i = G_j = G and
+    e = (cos b, sin b) in a plane: grad C-bar = G cos a x, T-bar x =
+    sin^2 a x and T-bar e = (sin^2 a cos b, cos^2 a sin b), so
+      A A^T/|A|:  S e = gamma G (sin^2 a cos b (2 - xi cos a), 2 cos^2 a sin b)
+      A^T A/|A|:  S e = gamma G (2 - xi cos a) (sin^2 a cos b, cos^2 a sin b)
+      scalar:     S e = gamma G (2 - xi cos a cos b) (sin^2 a cos b, cos^2 a sin b)."""
+    g, xi, G, r = SAME_PHASE_GAMMA, SAME_PHASE_XI, 3.3, 0.07
+    ca, sa, cb, sb = math.cos(alpha), math.sin(alpha), math.cos(beta), math.sin(beta)
+    if form == 0:
+        want2 = g * G * np.array([sa * sa * cb * (2.0 - xi * ca), 2.0 * ca * ca * sb])
+    elif form == 1:
+        want2 = g * G * (2.0 - xi * ca) * np.array([sa * sa * cb, ca * ca * sb])
+    else:
+        want2 = g * G * (2.0 - xi * ca * cb) * np.array([sa * sa * cb, ca * ca * sb])
+    for dim, R in ((2, np.eye(3)), (3, rotation(5))):
+        P = same_phase_params(dim, form)
+        ni = R @ np.array([ca, sa, 0.0])
+        nj = R @ np.array([ca, -sa, 0.0])
+        e = R @ np.array([cb, sb, 0.0])
+        want = (R @ np.array([want2[0], want2[1], 0.0]))[:dim]
+        out = oracle.surface_pair(P, 1, 1, (G * ni)[:dim], (G * nj)[:dim], e[:dim], r)
+        assert out == pytest.approx(want, rel=1e-12, abs=1e-12 * g * G)
+
+
+def test_same_phase_penalty_scope_and_xi():
+    """The same-phase penalty is the only difference between xi = 0, the
+    printed scope and the cross-phase-only ablation: with the mirrored
+    normals the three give 2 gamma G sin^2 a cos b x-components
+    (xi = 0 and cross-only) and the full closed form (printed scope)."""
+    G, r, alpha = 2.0, 0.05, 0.6
+    ni = np.array([math.cos(alpha), math.sin(alpha)])
+    nj = np.array([math.cos(alpha), -math.sin(alpha)])
+    e = np.array([1.0, 0.0])
+    base = dict(rho0=(3.0, 1.0), eta=(0.1, 0.1))
+    full = oracle.surface_pair(oracle.make_params(2, 0.1, 0.13, 10.0, 1.0, xi=2.0, **base), 0, 0, G * ni, G * nj, e, r)
+    zero = oracle.surface_pair(oracle.make_params(2, 0.1, 0.13, 10.0, 1.0, xi=0.0, **base), 0, 0, G * ni, G * nj, e, r)
+    cross = oracle.surface_pair(oracle.make_params(2, 0.1, 0.13, 10.0, 1.0, xi=2.0, penalty_scope=1, **base),
+                                0, 0, G * ni, G * nj, e, r)
+    s2 = math.sin(alpha) ** 2
+    assert zero == pytest.approx([2.0 * G * s2, 0.0], abs=1e-14)
+    assert cross == pytest.approx(zero, abs=1e-15)
+    assert full == pytest.approx([G * s2 * (2.0 - 2.0 * math.cos(alpha)), 0.0], abs=1e-14)
+
+
+def test_force_loop_uses_the_pair_term():
+    """Wiring: on a small mixed cluster at rest, each particle's a^s from the
+    force loop equals the sum over its neighbours of the pair entry point's
+    S_ij e_ij times W'(r) V_j / rho_i (with the loop's own colour
+    gradients)."""
+    rng = np.random.default_rng(8)
+    dx = 0.1
+    h = 1.3 * dx
+    pos = np.zeros((12, 3))
+    pos[:, :2] = rng.uniform(0.0, 3 * dx, size=(12, 2))
+    kind = np.array([0] * 7 + [1] * 5, dtype=np.int32)
+    rho = np.where(kind == 0, 5.0, 1.0) * (1.0 + 0.01 * rng.normal(size=12))
+    P = oracle.make_params(2, dx, h, 10.0, 0.8, rho0=(5.0, 1.0), eta=(0.1, 0.01), n=12, tvf_alpha=0.0)
+    out = oracle.forces(P, pos, np.zeros((12, 3)), rho, kind)
+    gC = out["gradC"]
+    mass = np.where(kind == 0, 5.0, 1.0) * dx * dx
+    for i in range(12):
+        a = np.zeros(2)
+        for j in range(12):
+            rv = pos[i, :2] - pos[j, :2]
+            r = float(np.linalg.norm(rv))
+            if j == i or not (0.0 < r < 2 * h):
+                continue
+            Se = oracle.surface_pair(P, kind[i], kind[j], gC[i, :2], gC[j, :2], rv / r, r)
+            a += Se * oracle.kernel_dW(2, h, r) * (mass[j] / rho[j]) / rho[i]
+        assert out["a_s"][i, :2] == pytest.approx(a, rel=1e-11, abs=1e-12 * max(np.abs(out["a_s"]).max(), 1e-300))
