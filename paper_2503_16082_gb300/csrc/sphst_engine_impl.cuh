@@ -129,7 +129,7 @@ template <typename T> struct EngineT : Engine {
         ncases = (int)cases.size();
         block = blk;
         lanes = cases.empty() ? 1 : cases[0]->P.lanes;
-        if (lanes != 2 && lanes != 4) lanes = 1;
+        if (lanes != 2 && lanes != 4 && lanes != 8) lanes = 1;
         if (user_stream) {
             stream = user_stream;
         } else {

@@ -266,6 +266,21 @@ def test_lanes_per_particle_repeat_bitwise(lanes):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("lanes", [2, 4, 8])
+def test_lanes_change_the_summation_order(lanes):
+    # with L lanes a particle's list is split and the parts added in another
+    # order, so FP32 results differ from one lane's in the last bits: the
+    # L-lane kernels ran
+    case = small(3, n_side=11)
+    res = {}
+    for L in (1, lanes):
+        h = gpu_case(case, 32, lanes=L, block=64)
+        S.step(h, 1)
+        res[L] = S.read_fields(h, S.FIELD_VEL, 3)
+        S.destroy(h)
+    assert not np.array_equal(res[1], res[lanes])
+
+
 def test_profiled_launch_counts():
     # one advection step of a two-phase list case: every per-substep kernel
     # (criterion, A, S, B, C) runs once per substep
