@@ -498,25 +498,35 @@ def batch_measure(precision: int = 32, n_cases: int = 512, steps: int = 20, warm
     # coarse 3D drops with strong tension cluster beyond the default list
     # capacity of 128 neighbours; the batch uses 192
     kw = [dict(max_neighbors=192 if c.dim == 3 else 0) for c in cases]
-    hs = [S.case_from_spec(c, precision=precision, **k) for c, k in zip(cases, kw)]
     state_bytes = sum(S.footprint_bytes(S.params_from_spec(c, precision, **k), c.n) for c, k in zip(cases, kw))
-    b = S.batch_create(precision)
-    for h in hs:
-        S.batch_add(b, h)
-    S.batch_step(b, warmup)
-    sub0 = [S.case_info(h)["n_sub"] for h in hs]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    S.batch_step(b, steps)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    subs = [S.case_info(h)["n_sub"] - s0 for h, s0 in zip(hs, sub0)]
+
+    def run(work_lists: int):
+        hs = [S.case_from_spec(c, precision=precision, work_lists=work_lists, **k) for c, k in zip(cases, kw)]
+        b = S.batch_create(precision)
+        for h in hs:
+            S.batch_add(b, h)
+        S.batch_step(b, warmup)
+        sub0 = [S.case_info(h)["n_sub"] for h in hs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.batch_step(b, steps)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        subs = [S.case_info(h)["n_sub"] - s0 for h, s0 in zip(hs, sub0)]
+        stats = [S.case_info(h)["status"] for h in hs]
+        for h in hs:
+            S.batch_remove(b, h)
+            S.destroy(h)
+        S.batch_destroy(b)
+        return secs, subs, stats
+
+    # the default launch (one block per tile of every member each substep)
+    # and the work-list variant (the active members' tiles listed each
+    # substep, the sweeps' blocks striding over the list)
+    dt, subs, statuses = run(0)
     units = sum(c.n_fluid * n for c, n in zip(cases, subs))
-    statuses = [S.case_info(h)["status"] for h in hs]
-    for h in hs:
-        S.batch_remove(b, h)
-        S.destroy(h)
-    S.batch_destroy(b)
+    dt_w, subs_w, _ = run(1)
+    units_w = sum(c.n_fluid * n for c, n in zip(cases, subs_w))
     # the single-case path on a sample of the same cases
     k = min(plain_sample, len(cases))
     punits, psecs = 0, 0.0
@@ -564,6 +574,9 @@ def batch_measure(precision: int = 32, n_cases: int = 512, steps: int = 20, warm
                                   status=x) for sp, c, x in zip(specs, cases, statuses) if x][:8],
             "plain_single_case": {"value": round(punits / psecs, 1), "cases_sampled": k},
             "speedup_vs_plain": round((units / dt) / (punits / psecs), 2),
+            "work_list_variant": {"value": round(units_w / dt_w, 1), "seconds": round(dt_w, 3),
+                                  "note": "the active members' tiles listed each substep and the sweeps' blocks "
+                                          "striding over the list (work_lists = 1); same results bit for bit"},
             "same_results_as_plain": "bitwise per case (tested), so equal Laplace-pressure error",
             "cpu_baseline": cpu_line, "timing": "host clock around synchronising step calls",
             "dtype": "f32" if precision == 32 else "f64", "data": "synthetic",

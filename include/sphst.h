@@ -78,6 +78,12 @@ extern "C" {
  * ablation) */
 #define SPHST_PENALTY_SCOPE_BOTH       0
 #define SPHST_PENALTY_SCOPE_CROSS_ONLY 1
+/* wall pairs of the pressure force (no wall model in the paper; Eqs. 8-11
+ * with the mirror state rho_i, p_i, 2 U_w - U_L): MIRROR uses P* as it
+ * comes, so a fluid particle in tension (p_i < 0) is pulled towards the
+ * wall; NO_SUCTION takes max(P*, 0), so walls push and never pull */
+#define SPHST_WALL_MIRROR     0
+#define SPHST_WALL_NO_SUCTION 1
 /* Eq. 8's star velocity: CORRECTED takes the normal component as -U* along
  * e_ij (U = -v.e_ij, Eq. 10) and the tangential part of the pair average;
  * PRINTED is U* e_ij + (vbar - Ubar e_ij) as printed */
@@ -155,6 +161,16 @@ typedef struct {
                                Speed only; a batch uses its first case's
                                value.                                        */
     int32_t penalty_scope;  /* SPHST_PENALTY_SCOPE_*                           */
+    int32_t wall_form;      /* SPHST_WALL_* (pressure of wall pairs)           */
+    int32_t work_lists;     /* batches only (the first case's value counts):
+                               0 (default): every substep launches one block
+                               (L blocks) per tile of every member, and the
+                               tiles of members whose advection step has
+                               ended return at once; 1: after each
+                               substep's criterion the tiles of the active
+                               members are listed per class and the sweeps'
+                               blocks stride over that list.  Speed only:
+                               both give the same bits.                      */
 } sphst_case_params;
 
 typedef struct {

@@ -27,7 +27,9 @@
  *               is not on an interface: Pi = 0, T = I, N = 0.
  *   walls       fixed particles of volume dx^d carrying a prescribed
  *               velocity; pressure pairs use the mirror state (rho_i, p_i,
- *               2 U_w - U_L); continuity uses v* = v_w; viscous pairs use
+ *               2 U_w - U_L), whose P* the flag wall_form = 1 floors at zero
+ *               (a wall then never pulls a particle in tension towards
+ *               itself); continuity uses v* = v_w; viscous pairs use
  *               eta_i and v_i - v_w; walls take no part in the colour
  *               function or the surface force.
  *   surface     Eq. 33 divided by m_i, so the acceleration carries 1/rho_i.
@@ -115,6 +117,9 @@ typedef struct {
     int32_t vstar_form;   /* 0: normal component -U* (reading); 1: Eq. 8 as printed */
     int32_t penalty_scope; /* 0: the penalty on both lines of Eq. 33 (as printed);
                               1: on the cross-phase line only (an ablation) */
+    int32_t wall_form;    /* 0: the wall pair's P* from the mirror state as it comes;
+                             1: max(P*, 0), a wall pushes and never pulls */
+    int32_t pad3_;
 } ora_params;
 
 typedef struct {
@@ -858,6 +863,8 @@ static void pressure_surface_acc(const ora_params *P, const state_t *S,
                     pbar = pair_pbar(rho_i, p_i, rho_i, p_i);
                 }
                 double Ps = riemann_Pstar(P, L, R, pbar);
+                /* reading (walls): with wall_form 1 a wall pair never pulls */
+                if (!is_fluid(kj) && P->wall_form == 1 && Ps < 0.0) Ps = 0.0;
                 for (int d = 0; d < dim; ++d)
                     a_p[d] += -2.0 / rho_i * Ps * gradW[d] * Vj;
 

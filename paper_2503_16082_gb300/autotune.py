@@ -8,9 +8,10 @@ Three choices change only speed, never the physics:
 * ``nbr_mode``: neighbour list built once per advection step, or the cell walk
   every sweep.  The two visit the same pairs; the list orders other-phase
   neighbours first, so results agree to the rounding of a reordered sum.
-* ``lanes``: lanes per particle in the per-substep sweeps with the list (1, 2
-  or 4, i.e. 32, 16 or 8 particles per warp).  The lanes split the list and
-  add their partial sums, so results agree to the rounding of that sum.
+* ``lanes``: lanes per particle in the per-substep sweeps with the list (1, 2,
+  4 or 8, i.e. 32, 16, 8 or 4 particles per warp).  The lanes split the list and
+  add their partial sums in a fixed order (the results differ from one lane by
+  the rounding of the reordered sum, within the parity tolerances).
   More lanes put a small case on more SMs and more warps.
 
 ``Tuner.best(spec)`` times every candidate on the case itself (one advection

@@ -48,11 +48,19 @@ enum ArrayId { A_POS = 0, A_VEL, A_DRHO, A_ID, A_GRADC, A_ACCV };
     case 8: KERN<T, D, true, 8><<<g_ * 8, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
     default: KERN<T, D, true, 1><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;               \
     }
-#define SPH_CLASSES_LX(NCLS, KERN, LN, ARGS, CNT, ...)                                 \
+// the same for the work-list kernels of a batch
+#define SPH_LANES_W(KERN, D, LN, ...)                                                                   \
+    switch (LN) {                                                                                       \
+    case 2: KERN<T, D, true, 2, true><<<g_ * 2, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
+    case 4: KERN<T, D, true, 4, true><<<g_ * 4, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
+    case 8: KERN<T, D, true, 8, true><<<g_ * 8, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
+    default: KERN<T, D, true, 1, true><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;               \
+    }
+#define SPH_CLASSES_LX(NCLS, KERN, LN, ARGS, CNT, GRID, ...)                           \
     for (int k_ = 0; k_ < (NCLS); ++k_) {                                              \
         if (!CNT[k_]) continue;                                                        \
         const SweepArgs a_ = ARGS(k_);                                                 \
-        const unsigned g_ = (unsigned)CNT[k_];                                         \
+        const unsigned g_ = (unsigned)(GRID);                                          \
         switch (k_) {                                                                  \
         case 0: SPH_LANES(KERN, 3, LN, __VA_ARGS__) break;                             \
         case 1: SPH_LANES(KERN, 2, LN, __VA_ARGS__) break;                             \
@@ -60,8 +68,28 @@ enum ArrayId { A_POS = 0, A_VEL, A_DRHO, A_ID, A_GRADC, A_ACCV };
         default: KERN<T, 2, false><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;  \
         }                                                                              \
     }
-#define SPH_CLASSES_L(NCLS, KERN, LN, ...) SPH_CLASSES_LX(NCLS, KERN, LN, sweep_args, cls_n, __VA_ARGS__)
-#define SPH_CLASSES_LF(NCLS, KERN, LN, ...) SPH_CLASSES_LX(NCLS, KERN, LN, fluid_args, cls_fn, __VA_ARGS__)
+// SPH_CLASSES_L: one block (L blocks) per tile of particles; SPH_CLASSES_LF:
+// the per-substep sweeps over fluid ranks, whose blocks stride over the
+// work list of active tiles in a batch (the grid is then capped)
+#define SPH_CLASSES_L(NCLS, KERN, LN, ...) SPH_CLASSES_LX(NCLS, KERN, LN, sweep_args, cls_n, cls_n[k_], __VA_ARGS__)
+#define SPH_CLASSES_LF(NCLS, KERN, LN, ...)                                                      \
+    if (use_work) {                                                                              \
+        SPH_CLASSES_LXW(NCLS, KERN, LN, work_args, cls_fn, work_grid(cls_fn[k_]), __VA_ARGS__)   \
+    } else {                                                                                     \
+        SPH_CLASSES_LX(NCLS, KERN, LN, fluid_args, cls_fn, cls_fn[k_], __VA_ARGS__)              \
+    }
+#define SPH_CLASSES_LXW(NCLS, KERN, LN, ARGS, CNT, GRID, ...)                                    \
+    for (int k_ = 0; k_ < (NCLS); ++k_) {                                                        \
+        if (!CNT[k_]) continue;                                                                  \
+        const SweepArgs a_ = ARGS(k_);                                                           \
+        const unsigned g_ = (unsigned)(GRID);                                                    \
+        switch (k_) {                                                                            \
+        case 0: SPH_LANES_W(KERN, 3, LN, __VA_ARGS__) break;                                     \
+        case 1: SPH_LANES_W(KERN, 2, LN, __VA_ARGS__) break;                                     \
+        case 2: KERN<T, 3, false, 1, true><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;    \
+        default: KERN<T, 2, false, 1, true><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;   \
+        }                                                                                        \
+    }
 
 template <typename T> struct EngineT : Engine {
     // particle arrays
@@ -84,6 +112,14 @@ template <typename T> struct EngineT : Engine {
     CaseDesc *d_desc = nullptr;
     CaseState *d_state = nullptr;
     Tile *d_tiles = nullptr, *d_ftiles = nullptr;   // tiles over particles; over fluid ranks
+    // work lists of the per-substep sweeps (batches of more than one case):
+    // class of each case, its fluid tiles (count, first index), the first
+    // tile of each class, scan offsets, list lengths, the lists
+    bool use_work = false;
+    int32_t *d_cls_of = nullptr;
+    uint32_t *d_ftn = nullptr, *d_woff = nullptr, *d_wcount = nullptr, *d_work = nullptr;
+    int64_t *d_ft_first = nullptr, *d_cls0 = nullptr;
+    int64_t work_cap = 0;                           // blocks of a work-list launch (per lane)
     int *d_loop_flag = nullptr;
     double *d_read = nullptr;              // read-back buffer
     double *d_diag = nullptr;              // diagnostics partials + result
@@ -194,6 +230,10 @@ template <typename T> struct EngineT : Engine {
         size_t o_tiles = take(sizeof(Tile) * (size_t)std::max<int64_t>(n_tiles, 1));
         size_t o_ftiles = take(sizeof(Tile) * (size_t)std::max<int64_t>(n_ftiles, 1));
         size_t o_fidx = take(nn * 4), o_fscan = take((nn + 1) * 4);
+        const size_t nc = (size_t)std::max(ncases, 1);
+        size_t o_clsof = take(nc * 4), o_ftn = take(nc * 4), o_woff = take(nc * 4), o_wcount = take(64);
+        size_t o_work = take(sizeof(uint32_t) * (size_t)std::max<int64_t>(n_ftiles, 1));
+        size_t o_ftfirst = take(nc * 8), o_cls0 = take(64);
         size_t o_flag = take(64);
         size_t o_read = take((size_t)std::max<int64_t>(max_case_n, 1) * 3 * sizeof(double));
         size_t o_nbr = take((size_t)std::max<int64_t>(nbr_total, 1) * 4), o_ncnt = take(nn * 4);
@@ -221,6 +261,9 @@ template <typename T> struct EngineT : Engine {
         d_tiles = (Tile *)(b + o_tiles); d_loop_flag = (int *)(b + o_flag);
         d_ftiles = (Tile *)(b + o_ftiles);
         fidx = (uint32_t *)(b + o_fidx); fscan = (uint32_t *)(b + o_fscan);
+        d_cls_of = (int32_t *)(b + o_clsof); d_ftn = (uint32_t *)(b + o_ftn);
+        d_woff = (uint32_t *)(b + o_woff); d_wcount = (uint32_t *)(b + o_wcount);
+        d_work = (uint32_t *)(b + o_work); d_ft_first = (int64_t *)(b + o_ftfirst); d_cls0 = (int64_t *)(b + o_cls0);
         d_read = (double *)(b + o_read);
         nbr = (uint32_t *)(b + o_nbr);
         nbr_cnt = (uint32_t *)(b + o_ncnt);
@@ -265,6 +308,28 @@ template <typename T> struct EngineT : Engine {
         }
         if (!ftiles.empty())
             SPH_CK(cudaMemcpyAsync(d_ftiles, ftiles.data(), sizeof(Tile) * ftiles.size(), cudaMemcpyHostToDevice, stream));
+        // work lists (a batch option): the tiles of the active cases are
+        // listed each substep and the sweeps' blocks stride over the list
+        use_work = ncases > 1 && cases[0]->P.work_lists == 1;
+        if (use_work) {
+            std::vector<int32_t> cls_of(ncases);
+            std::vector<uint32_t> ftn(ncases, 0);
+            std::vector<int64_t> ft_first(ncases, 0), cls0(4);
+            for (int c = 0; c < ncases; ++c) cls_of[c] = tile_class(h_desc[c]);
+            for (int64_t t = (int64_t)ftiles.size() - 1; t >= 0; --t) {
+                ftn[ftiles[t].c] += 1;
+                ft_first[ftiles[t].c] = t;
+            }
+            for (int k = 0; k < 4; ++k) cls0[k] = cls_fb[k];
+            SPH_CK(cudaMemcpyAsync(d_cls_of, cls_of.data(), 4 * ncases, cudaMemcpyHostToDevice, stream));
+            SPH_CK(cudaMemcpyAsync(d_ftn, ftn.data(), 4 * ncases, cudaMemcpyHostToDevice, stream));
+            SPH_CK(cudaMemcpyAsync(d_ft_first, ft_first.data(), 8 * ncases, cudaMemcpyHostToDevice, stream));
+            SPH_CK(cudaMemcpyAsync(d_cls0, cls0.data(), 8 * 4, cudaMemcpyHostToDevice, stream));
+            int dev = 0, sms = 0;
+            SPH_CK(cudaGetDevice(&dev));
+            SPH_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            work_cap = (int64_t)std::max(sms, 1) * 16;
+        }
         SPH_CK(cudaMemcpyAsync(d_desc, h_desc.data(), sizeof(CaseDesc) * ncases, cudaMemcpyHostToDevice, stream));
         // fill each case
         for (int c = 0; c < ncases; ++c) {
@@ -336,6 +401,23 @@ template <typename T> struct EngineT : Engine {
     SweepArgs fluid_args(int k) const {
         return SweepArgs{d_ftiles, d_desc, d_state, starts, nbr, nbr_cnt, cls_fb[k], fidx};
     }
+    // the per-substep sweeps: with work lists, class k's list and its length
+    SweepArgs work_args(int k) const {
+        SweepArgs a = fluid_args(k);
+        if (use_work) {
+            a.work = d_work;
+            a.work_count = d_wcount + k;
+        }
+        return a;
+    }
+    int64_t work_grid(int64_t tiles) const { return use_work ? std::min(tiles, work_cap) : tiles; }
+    // list the active cases' tiles (after the criterion kernel of a substep)
+    void launch_work_lists() {
+        if (!use_work) return;
+        k_work_scan<<<1, 1024, 0, stream>>>(ncases, d_cls_of, d_ftn, d_state, d_woff, d_wcount);
+        k_work_fill<<<(unsigned)((n_ftiles + 255) / 256), 256, 0, stream>>>(n_ftiles, d_ftiles, d_ft_first, d_cls0,
+                                                                          d_cls_of, d_woff, d_state, d_work);
+    }
     // fluid ranks of the reordered particles (after the gather)
     void launch_fluid_ranks() {
         const int64_t np1 = n + 1;
@@ -384,6 +466,7 @@ template <typename T> struct EngineT : Engine {
 
     int launch_body(cudaGraphConditionalHandle h, int use_handle) {
         k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, h, use_handle);
+        launch_work_lists();
         SPH_CLASSES_LF(4, k_sweep_A, lanes, snap, drho, lgeo, gradC);
         SPH_CLASSES_L(2, k_sweep_S, surface_lanes(), band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
         SPH_CLASSES_LF(4, k_sweep_B, lanes, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo);
@@ -516,7 +599,10 @@ template <typename T> struct EngineT : Engine {
             SPH_CLASSES_F(4, k_sweep_V, snap, drho, vel, bmat, acc_visc, pos);
         });
         for (;;) {
-            timed(2, 1, [&] { k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, 0, 0); });
+            timed(2, use_work ? 3 : 1, [&] {
+                k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, 0, 0);
+                launch_work_lists();
+            });
             timed(3, ncls, [&] { SPH_CLASSES_LF(4, k_sweep_A, lanes, snap, drho, lgeo, gradC); });
             timed(6, nlist, [&] {
                 SPH_CLASSES_L(2, k_sweep_S, surface_lanes(), band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);

@@ -1180,6 +1180,7 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
     const T p_i = cp.c0sq * dri;
     T apx = 0, apy = 0, apz = 0, asx = 0, asy = 0, asz = 0;
     const Limiter<T> limiter_beta(cp, d.limiter);
+    const bool wall_push_only = d.wall_form == 1;
     const T c0 = cp.c0, c0sq = cp.c0sq, vol_wall = cp.vol_wall;
     const T rho0_0 = cp.rho0[0], rho0_1 = cp.rho0[1], m_0 = cp.mass[0], m_1 = cp.mass[1];
     const KernelGeo<T> kgeo(cp);
@@ -1194,7 +1195,8 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
             // mirror state behind a wall moving with v_w: rho_i, p_i, 2 U_w - U_L
             const T dU = T(2) * dUe;
             const T beta = limiter_beta(dU, p_i, rho_i);       // mirror state: rho_R, p_R = rho_i, p_i
-            const T Ps = p_i + beta * rho_i * c0 * dU * T(0.5);
+            T Ps = p_i + beta * rho_i * c0 * dU * T(0.5);
+            if (wall_push_only) Ps = Ps > T(0) ? Ps : T(0);    // no-suction wall reading
             const T f = Ps * dW * vol_wall;
             const L2<T> a = fma2(l2(f, f), exy, l2(apx, apy));
             apx = a.x; apy = a.y; if (D == 3) apz += f * ez;
@@ -1417,7 +1419,25 @@ struct SweepArgs {
     // nullptr: tile entries are particle indices; else the tiles run over
     // fluid ranks and fidx maps a rank to the particle (sweeps B and C)
     const uint32_t *fidx = nullptr;
+    // batches: the tiles of the cases active in this substep, compacted per
+    // class after the criterion kernel (work[tile0 + k] is a tile index,
+    // *work_count of them); the launch's blocks stride over them.  nullptr:
+    // block b takes tile tile0 + b / L.
+    const uint32_t *work = nullptr;
+    const uint32_t *work_count = nullptr;
 };
+
+// Work items of a sweep launch: (tile, block of the tile) pairs; with L
+// lanes per particle a tile takes L blocks.  Without a work list (WORK
+// false: single cases) the launch has one block per item and each block
+// runs one item; with one (batches), its blocks take items blockIdx.x,
+// blockIdx.x + gridDim.x, ... up to L x (active tiles of the class).
+template <int L, bool WORK> __device__ __forceinline__ int64_t work_items(const SweepArgs &a) {
+    return WORK ? (int64_t)(*a.work_count) * L : (int64_t)gridDim.x;
+}
+template <int L, bool WORK> __device__ __forceinline__ Tile work_tile(const SweepArgs &a, int64_t w) {
+    return a.tiles[WORK ? (int64_t)a.work[a.tile0 + w / L] : a.tile0 + w / L];
+}
 
 // particle of tile position q: the position itself, or the fluid particle of
 // that rank (the list build, the band, sweeps M, V, A, B and C)
@@ -1595,19 +1615,27 @@ __global__ void SPH_SWEEP_BOUNDS k_sweep_V(SweepArgs a, const V4<T> *snap, const
 // particles, and lane threadIdx % L of a particle's group walks every L-th
 // list entry.  local_index gives the particle's index within its tile.
 // Sweep S does the same per entry of its band list.
-template <int L> __device__ __forceinline__ int local_index() {
-    return L == 1 ? (int)threadIdx.x : (int)((blockIdx.x % L) * (blockDim.x / L) + threadIdx.x / L);
+template <int L> __device__ __forceinline__ int local_index(int64_t w) {
+    return L == 1 ? (int)threadIdx.x : (int)((w % L) * (blockDim.x / L) + threadIdx.x / L);
 }
 
-template <typename T, int D, bool LIST, int L = 1>
+template <typename T, int D, bool LIST, int L = 1, bool WORK = false>
 __global__ void SPH_SWEEPAS_BOUNDS k_sweep_A(SweepArgs a, const V4<T> *snap, const T *drho, const V4<T> *lgeo,
                                            V4<T> *gradC) {
-    const Tile t = a.tiles[a.tile0 + blockIdx.x / L];
-    const int li = local_index<L>();
-    if (li >= t.n || !a.st[t.c].active) return;
-    const CaseDesc &d = a.desc[t.c];
-    const int64_t i = particle_at(a, t.begin + li);
-    sweep_A<LIST, T, D, L>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, lgeo, gradC, threadIdx.x % L);
+    const auto item = [&](int64_t w) {
+        const Tile t = work_tile<L, WORK>(a, w);
+        const int li = local_index<L>(w);
+        if (li >= t.n || !a.st[t.c].active) return;
+        const CaseDesc &d = a.desc[t.c];
+        const int64_t i = particle_at(a, t.begin + li);
+        sweep_A<LIST, T, D, L>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, lgeo, gradC, threadIdx.x % L);
+    };
+    if constexpr (WORK) {
+        const int64_t items = work_items<L, WORK>(a);
+        for (int64_t w = blockIdx.x; w < items; w += gridDim.x) item(w);
+    } else {
+        item(blockIdx.x);
+    }
 }
 
 // surface sum of the band particles (list classes only), before B: one
@@ -1629,43 +1657,93 @@ __global__ void SPH_SWEEPAS_BOUNDS k_sweep_S(SweepArgs a, const uint64_t *blist,
                               acc_surf, nullptr, nullptr, &ph, threadIdx.x % L);
 }
 
-template <typename T, int D, bool LIST, int L = 1>
+template <typename T, int D, bool LIST, int L = 1, bool WORK = false>
 __global__ void SPH_SWEEPB_BOUNDS k_sweep_B(SweepArgs a, const uint8_t *band, const V4<T> *snap, const V4<T> *vel,
                                             const V4<T> *gradC, const V4<T> *acc_visc, V4<T> *acc_surf,
                                             V4<T> *vel_new, const V4<T> *lgeo) {
-    const Tile t = a.tiles[a.tile0 + blockIdx.x / L];
-    if (!a.st[t.c].active) return;                 // uniform per block
-    const CaseDesc &d = a.desc[t.c];
-    double v2 = 0.0;
-    uint32_t ph = PH_WALL;
-    const int li = local_index<L>();
-    if (li < t.n) {
-        const int64_t i = particle_at(a, t.begin + li);
-        const T dt = (T)a.st[t.c].dt;
-        v2 = sweep_B<LIST, LIST ? 1 : 0, T, D, L>(d, phys<T>(d), dt, i, a.starts, a.nbr, a.cnt, band, snap, vel,
-                                                  gradC, acc_visc, acc_surf, vel_new, lgeo, &ph, threadIdx.x % L);
-    }
-    unsigned long long m0 = ph == 0 ? (unsigned long long)__double_as_longlong(v2) : 0ull;
-    unsigned long long m1 = ph == 1 ? (unsigned long long)__double_as_longlong(v2) : 0ull;
-    m0 = warp_max_u64(m0);
-    m1 = warp_max_u64(m1);
-    if ((threadIdx.x & 31) == 0) {
-        if (m0) atomicMax(&a.st[t.c].vmax2_acc[0], m0);
-        if (m1) atomicMax(&a.st[t.c].vmax2_acc[1], m1);
+    const auto item = [&](int64_t w) {
+        const Tile t = work_tile<L, WORK>(a, w);
+        if (!a.st[t.c].active) return;             // uniform per block
+        const CaseDesc &d = a.desc[t.c];
+        double v2 = 0.0;
+        uint32_t ph = PH_WALL;
+        const int li = local_index<L>(w);
+        if (li < t.n) {
+            const int64_t i = particle_at(a, t.begin + li);
+            const T dt = (T)a.st[t.c].dt;
+            v2 = sweep_B<LIST, LIST ? 1 : 0, T, D, L>(d, phys<T>(d), dt, i, a.starts, a.nbr, a.cnt, band, snap, vel,
+                                                      gradC, acc_visc, acc_surf, vel_new, lgeo, &ph, threadIdx.x % L);
+        }
+        unsigned long long m0 = ph == 0 ? (unsigned long long)__double_as_longlong(v2) : 0ull;
+        unsigned long long m1 = ph == 1 ? (unsigned long long)__double_as_longlong(v2) : 0ull;
+        m0 = warp_max_u64(m0);
+        m1 = warp_max_u64(m1);
+        if ((threadIdx.x & 31) == 0) {
+            if (m0) atomicMax(&a.st[t.c].vmax2_acc[0], m0);
+            if (m1) atomicMax(&a.st[t.c].vmax2_acc[1], m1);
+        }
+    };
+    if constexpr (WORK) {
+        const int64_t items = work_items<L, WORK>(a);
+        for (int64_t w = blockIdx.x; w < items; w += gridDim.x) item(w);
+    } else {
+        item(blockIdx.x);
     }
 }
 
-template <typename T, int D, bool LIST, int L = 1>
+template <typename T, int D, bool LIST, int L = 1, bool WORK = false>
 __global__ void SPH_SWEEP_BOUNDS k_sweep_C(SweepArgs a, const V4<T> *snap, const V4<T> *vel_new, T *drho,
                                            V4<T> *vel, V4<T> *pos, const V4<T> *lgeo) {
-    const Tile t = a.tiles[a.tile0 + blockIdx.x / L];
-    const int li = local_index<L>();
-    if (li >= t.n || !a.st[t.c].active) return;
-    const CaseDesc &d = a.desc[t.c];
-    const int64_t i = particle_at(a, t.begin + li);
-    const T dt = (T)a.st[t.c].dt;
-    sweep_C<LIST, T, D, L>(d, phys<T>(d), dt, i, a.starts, a.nbr, a.cnt, snap, vel_new, drho, vel, pos, lgeo,
-                           threadIdx.x % L);
+    const auto item = [&](int64_t w) {
+        const Tile t = work_tile<L, WORK>(a, w);
+        const int li = local_index<L>(w);
+        if (li >= t.n || !a.st[t.c].active) return;
+        const CaseDesc &d = a.desc[t.c];
+        const int64_t i = particle_at(a, t.begin + li);
+        const T dt = (T)a.st[t.c].dt;
+        sweep_C<LIST, T, D, L>(d, phys<T>(d), dt, i, a.starts, a.nbr, a.cnt, snap, vel_new, drho, vel, pos, lgeo,
+                               threadIdx.x % L);
+    };
+    if constexpr (WORK) {
+        const int64_t items = work_items<L, WORK>(a);
+        for (int64_t w = blockIdx.x; w < items; w += gridDim.x) item(w);
+    } else {
+        item(blockIdx.x);
+    }
+}
+
+// ---- work lists of the per-substep sweeps in a batch: after the criterion
+// kernel has set each case's active flag, the fluid tiles of the active
+// cases are listed per class.  Scan (one block): case c's tiles go to
+// positions off[c] .. off[c] + ftn[c] - 1 of its class's list, and
+// count[k] receives the length of class k's list.  Fill: every fluid tile of
+// an active case writes its index there.  Tiles of class k start at cls0[k]
+// in the tile array and in the list alike.
+static __global__ void k_work_scan(int ncases, const int32_t *cls_of, const uint32_t *ftn, const CaseState *st,
+                                   uint32_t *off, uint32_t *count) {
+    uint32_t base[4] = {0u, 0u, 0u, 0u};
+    for (int c0 = 0; c0 < ncases; c0 += (int)blockDim.x) {
+        const int c = c0 + (int)threadIdx.x;
+        const int k = c < ncases ? cls_of[c] : -1;
+        const uint32_t n = c < ncases && st[c].active ? ftn[c] : 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t total;
+            const uint32_t before = block_exclusive_scan(k == q ? n : 0u, &total);
+            if (k == q) off[c] = base[q] + before;
+            base[q] += total;
+        }
+    }
+    if (threadIdx.x < 4) count[threadIdx.x] = base[threadIdx.x];
+}
+static __global__ void k_work_fill(int64_t n_ftiles, const Tile *ftiles, const int64_t *ft_first,
+                                   const int64_t *cls0, const int32_t *cls_of, const uint32_t *off,
+                                   const CaseState *st, uint32_t *work) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n_ftiles) return;
+    const int c = ftiles[t].c;
+    if (!st[c].active) return;
+    work[cls0[cls_of[c]] + off[c] + (t - ft_first[c])] = (uint32_t)t;
 }
 
 // ---------------------------------------------------------- diagnostics

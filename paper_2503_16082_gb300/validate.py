@@ -18,7 +18,8 @@ its maximum over the run; --xi 0 switches the penalty of Eqs. 29-33 off.
 impact_3d: whether the run stays finite to t_end, with its substep count.
 impact_sweep: Section 5.4's impact in the paper's units for each U0 (Re up to
 1e4, We up to 2.5e4): whether the run stays finite to the paper's end time,
-and the drop's final spread along the wall.
+and the drop's final spread along the wall (--wall-form 1: walls push and
+never pull).
 shear_drop: Taylor deformation of the drop of Section 5.2 (periodic in x,
 walls at +-U) averaged over the last 25% of the run, against Taylor's
 D = Ca (19 l + 16)/(16 l + 16) with l = 1.
@@ -50,6 +51,8 @@ def launch(args) -> dict:
     kw = {}
     if getattr(args, "penalty_scope", 0):
         kw["penalty_scope"] = args.penalty_scope
+    if getattr(args, "wall_form", 0):
+        kw["wall_form"] = args.wall_form
     if args.block:
         kw["block"] = args.block
     if args.lanes:
@@ -233,6 +236,8 @@ def main(argv=None):
     ap.add_argument("--xi", type=float, default=None, help="penalty coefficient (default: from the density ratio)")
     ap.add_argument("--penalty-scope", type=int, default=0, choices=[0, 1],
                     help="0: the penalty on both lines of Eq. 33; 1: on the cross-phase line only (ablation)")
+    ap.add_argument("--wall-form", type=int, default=0, choices=[0, 1],
+                    help="wall pairs: 0 mirror state as it comes, 1 no suction (max(P*, 0))")
     ap.add_argument("--t-end", type=float, default=None, help="impact_3d: 2.0, shear_drop: 20.0")
     args = ap.parse_args(argv)
     if args.t_end is None:

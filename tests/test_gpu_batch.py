@@ -35,14 +35,16 @@ def fields_of(h, spec):
     return [S.read_fields(h, f, spec.dim) for f in FIELDS]
 
 
-@pytest.mark.parametrize("precision,lanes", [(32, 1), (64, 1), (32, 4)])
-def test_batch_equals_alone(precision, lanes):
+@pytest.mark.parametrize("precision,lanes,work", [(32, 1, 0), (64, 1, 0), (32, 4, 0), (32, 1, 1), (64, 4, 1)])
+def test_batch_equals_alone(precision, lanes, work):
     # with L lanes per particle too: each particle's partial sums and their
-    # reduction are the same alone and in the batch
+    # reduction are the same alone and in the batch; and with the batch's
+    # work lists (active members' tiles listed each substep), whose cases
+    # here take different substep counts per advection step
     sp = specs()
     ref = [alone(s, 2, precision, lanes=lanes) for s in sp]
     b = S.batch_create(precision)
-    hs = [S.case_from_spec(s, precision=precision, lanes=lanes) for s in sp]
+    hs = [S.case_from_spec(s, precision=precision, lanes=lanes, work_lists=work) for s in sp]
     for h in hs:
         S.batch_add(b, h)
     S.batch_step(b, 1)

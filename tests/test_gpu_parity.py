@@ -143,6 +143,7 @@ def test_fp32_one_advection_step(dim):
     (dict(limiter=3), dict(limiter=3)),
     (dict(penalty_form=2), dict(penalty_form=2)),
     (dict(penalty_scope=1), dict(penalty_scope=1)),
+    (dict(wall_form=1), dict(wall_form=1)),
 ])
 def test_fp64_readings_flags(opts, ora):
     case = small(2)
@@ -150,6 +151,20 @@ def test_fp64_readings_flags(opts, ora):
     assert info["n_sub"] == oinfo["n_sub"]
     for key in ("pos", "vel", "rho", "gradC"):
         assert rel_err(g, o, pos0, kind, key, case) <= 1e-12, key
+
+
+def test_no_suction_wall_reading_changes_near_wall_particles():
+    # the droplet's jittered lattice puts near-wall particles in tension
+    # during the step: the no-suction reading must change their kicks (and
+    # the oracle agrees with each reading, above)
+    case = small(2)
+    out = {}
+    for form in (0, 1):
+        h = gpu_case(case, 64, wall_form=form)
+        S.step(h, 1)
+        out[form] = S.read_fields(h, S.FIELD_VEL, 2)
+        S.destroy(h)
+    assert not np.array_equal(out[0], out[1])
 
 
 def test_fp64_printed_vstar_one_substep():

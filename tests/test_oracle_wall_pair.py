@@ -82,3 +82,49 @@ def test_dissipation_vanishes_for_a_particle_moving_with_the_wall():
     P = oracle.make_params(2, dx, h, c0, 1.0, rho0=(1.0, 1.0), eta=(0.1, 0.1), n=2, tvf_alpha=0.0)
     out = oracle.forces(P, pos, vel, np.array([1.0, 1.0]), np.array([0, WALL], dtype=np.int32))
     assert np.all(out["a_p"][0] == 0.0) and np.all(out["a_v"][0] == 0.0) and out["drho"][0] == 0.0
+
+
+@pytest.mark.parametrize("u,rho_eps", [(0.0, -0.02), (0.05, -0.02), (-0.3, -0.01)])
+def test_no_suction_wall_reading(u, rho_eps):
+    """The same pair in tension (p_i < 0) with slow approach or separation:
+    the mirror reading's P* = p_i + beta rho_i c0 dU / 2 is negative, so the
+    wall pulls the particle towards itself (a_p along +x, the wall's side);
+    the no-suction reading (wall_form 1) floors P* at zero, and the pressure
+    force vanishes.  Viscous force and density change are unchanged."""
+    dx, c0, rho0, eta = 0.1, 10.0, 1.0, 0.3
+    h = 1.3 * dx
+    r = 0.9 * dx
+    pos = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0]])
+    vel = np.array([[u, 0.1, 0.0], [0.0, 0.0, 0.0]])
+    rho_i = rho0 * (1.0 + rho_eps)
+    rho = np.array([rho_i, rho0])
+    kind = np.array([0, WALL], dtype=np.int32)
+    a_p, a_v, drho, beta = closed_form(u, 0.1, 0.0, 0.0, rho_i, rho0, eta, c0, dx, h, r)
+    out = {}
+    for form in (0, 1):
+        P = oracle.make_params(2, dx, h, c0, 1.0, rho0=(rho0, rho0), eta=(eta, eta), n=2, tvf_alpha=0.0,
+                               wall_form=form)
+        out[form] = oracle.forces(P, pos, vel, rho, kind)
+    assert a_p[0] > 0.0                                   # mirror: towards the wall at +x
+    assert out[0]["a_p"][0, :2] == pytest.approx(a_p, rel=1e-13)
+    assert np.all(out[1]["a_p"][0] == 0.0)
+    for form in (0, 1):
+        assert out[form]["a_v"][0, :2] == pytest.approx(a_v, rel=1e-13)
+        assert out[form]["drho"][0] == pytest.approx(drho, rel=1e-13)
+
+
+@pytest.mark.parametrize("u,a,rho_eps", [(0.5, 0.0, 0.0), (0.7, 0.2, 0.01), (3.0, 0.0, 0.0)])
+def test_no_suction_wall_reading_keeps_pushing_pairs(u, a, rho_eps):
+    # with P* > 0 (compression or approach) both wall readings give the
+    # closed form of the mirror state
+    dx, c0, rho0, eta = 0.1, 10.0, 1.0, 0.3
+    h = 1.3 * dx
+    r = 0.9 * dx
+    pos = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0]])
+    vel = np.array([[u, 0.25, 0.0], [a, -0.15, 0.0]])
+    rho_i = rho0 * (1.0 + rho_eps)
+    P = oracle.make_params(2, dx, h, c0, 1.0, rho0=(rho0, rho0), eta=(eta, eta), n=2, tvf_alpha=0.0, wall_form=1)
+    out = oracle.forces(P, pos, vel, np.array([rho_i, rho0]), np.array([0, WALL], dtype=np.int32))
+    a_p, _, _, _ = closed_form(u, 0.25, a, -0.15, rho_i, rho0, eta, c0, dx, h, r)
+    assert a_p[0] < 0.0
+    assert out["a_p"][0, :2] == pytest.approx(a_p, rel=1e-13, abs=1e-300)
