@@ -7,8 +7,12 @@ closed forms the paper and textbooks give:
 * the 2D drop of §5.1 (velocity of Eq. 34): the GPU's shape-anisotropy
   signal equals the oracle's while the two FP64 trajectories still coincide
   (the flow is chaotic: last-bit differences grow over thousands of
-  substeps); at density ratio 1 the fitted period equals the textbook n = 2
-  value 2 pi sqrt(2 R^3 rho / (6 gamma)) within 20% at R = 12 dp;
+  substeps); at density ratio 1 with the paper's V0 = 10, the paper's own
+  check: the centre of mass of the drop's upper-right quarter converges
+  with resolution (R/dp 12, 24, 48);
+* the Laplace jump against resolution (R = 10, 20, 40 dp): within 5% with
+  full Riemann dissipation; with the default limiter it does not converge
+  (an expected failure that states the measured values);
 * total momentum of a wall-free run is conserved to FP32 rounding.
 """
 import math
@@ -87,12 +91,74 @@ def period_series_gpu(case, t_end, precision=64, chunk=10):
     return np.array(ts), np.array(an)
 
 
-def test_oscillating_drop_period_ratio1_matches_textbook():
-    case = sphcases.oscillating_2d(ratio=1.0)
-    want = 2 * math.pi * math.sqrt(2 * 0.2 ** 3 * 1.0 / (6 * 1.0))
-    ts, an = period_series_gpu(case, 3 * want)
-    period = ob.fit_period(ts, an, want)
-    assert abs(period - want) <= 0.20 * want, (period, want)
+def quarter_centroid_series(r_over_dp, precision=64, t_end=0.5, every=2):
+    """Section 5.1, density ratio 1, V0 = 10 (the paper's values; the peak
+    initial speed is V0/e, so c0 = 10 x 3.7 = 37): centre of mass of the
+    particles that start in the drop's upper-right quarter, against time."""
+    case = sphcases.oscillating_2d(ratio=1.0, R_over_dp=r_over_dp, V0=10.0, c0=37.0)
+    liq = case.phases[0].pos
+    sel = np.where((liq[:, 0] > 0.5) & (liq[:, 1] > 0.5))[0]
+    h = S.case_from_spec(case, precision=precision, lanes=4, block=64)
+    ts, xs = [0.0], [liq[sel].mean(0)]
+    info = S.case_info(h)
+    while info["t"] < t_end:
+        info = S.step(h, every)
+        ts.append(info["t"])
+        xs.append(S.read_fields(h, S.FIELD_POS, 2)[sel].mean(0))
+    S.destroy(h)
+    tg = np.linspace(0.0, t_end - 0.01, 200)
+    xs = np.array(xs)
+    return np.stack([np.interp(tg, ts, xs[:, 0]), np.interp(tg, ts, xs[:, 1])], axis=1)
+
+
+def test_oscillating_drop_quarter_centroid_converges():
+    # the paper's own check of the ratio-1 drop (Section 5.1): the quarter's
+    # centre of mass at three resolutions.  Measured (FP64 = oracle): the
+    # largest gap between R/dp 12 and 24 is 1.0e-3, between 24 and 48
+    # 0.74e-3, against an excursion of 0.016 over the run
+    a, b, c = (quarter_centroid_series(r) for r in (12, 24, 48))
+    d1, d2 = np.abs(a - b).max(), np.abs(b - c).max()
+    excursion = c[:, 0].max() - c[:, 0].min()
+    assert excursion > 0.01
+    assert d2 < d1, (d1, d2)
+    assert d2 < 0.06 * excursion, (d2, excursion)
+
+
+def laplace_jump_resolution(n_side, **params):
+    """Time-averaged Delta p R / gamma of the viscous 2D drop (density and
+    viscosity ratio 1, eta = 0.05, gamma = 1, R = n_side / 4 dp) over
+    t in [0.4, 1.0], FP64."""
+    case = sphcases.small_droplet(2, n_side, R_frac=0.25, rho_l=1.0, rho_g=1.0, mu_l=0.05, mu_g=0.05, c0=20.0)
+    h = S.case_from_spec(case, precision=64, lanes=4, block=64, **params)
+    phase = S.read_fields(h, S.FIELD_PHASE, 2)
+    out = []
+    info = S.case_info(h)
+    while info["t"] < 1.0:
+        info = S.step(h, 5)
+        if info["t"] > 0.4:
+            dp, R = ob.laplace_jump(S.read_fields(h, S.FIELD_POS, 2), S.read_fields(h, S.FIELD_PRESSURE, 2),
+                                    phase, case.dx, case.h_factor * case.dx)
+            out.append(dp * R / case.gamma)
+    S.destroy(h)
+    return float(np.mean(out))
+
+
+def test_laplace_jump_with_full_riemann_dissipation():
+    # with beta = 1 in Eq. 9 (full dissipation) the static drop settles and
+    # Eq. 37 holds within 5% at R = 10, 20 and 40 dp (measured 1.006, 1.041,
+    # 1.047: the error does not fall below the h = 1.3 dp smoothing's)
+    for n in (40, 80, 160):
+        x = laplace_jump_resolution(n, limiter=1)
+        assert abs(x - 1.0) <= 0.05, (n / 4, x)
+
+
+@pytest.mark.xfail(strict=True, reason="measured: with the dimensionless reading of the limiter of Eq. 11 the "
+                                       "parasitic currents grow with resolution (peak speeds 0.27, 0.55, 0.80) and "
+                                       "Delta p R / gamma is 1.07, 1.28, 1.25 at R = 10, 20, 40 dp")
+def test_laplace_jump_converges_with_the_default_limiter():
+    x = [laplace_jump_resolution(n) for n in (40, 80, 160)]
+    err = [abs(v - 1.0) for v in x]
+    assert err[2] < err[1] < err[0] and err[2] <= 0.05, x
 
 
 def test_oscillating_drop_period_fp32_against_fp64():
@@ -262,3 +328,51 @@ def test_laplace_jump_3d_static_drop():
     finally:
         S.destroy(h)
     assert 0.85 < np.mean(samples) < 1.15
+
+
+def square_drop_jump(dp, **params):
+    """Section 5.3: square drop of side l = 1 in a 2 x 2 box, density ratio
+    1000, viscosity ratio 100, gamma = 1; Delta p averaged over t in
+    [0.7, 1.0] against Eq. 37's gamma sqrt(pi) / l (FP64)."""
+    case = sphcases.droplet_case("square", 2, [0, 0], [2, 2], dp, [1.0, 1.0], 1.0 / math.sqrt(math.pi),
+                                 shape="square", rho_l=1.0, rho_g=1e-3, mu_l=0.05, mu_g=5e-4, sigma=1.0, c0=10.0)
+    h = S.case_from_spec(case, precision=64, lanes=4, block=64, **params)
+    phase = S.read_fields(h, S.FIELD_PHASE, 2)
+    out = []
+    info = S.case_info(h)
+    while info["t"] < 1.0:
+        info = S.step(h, 20)
+        if info["t"] > 0.7:
+            jump, _ = ob.laplace_jump(S.read_fields(h, S.FIELD_POS, 2), S.read_fields(h, S.FIELD_PRESSURE, 2),
+                                      phase, case.dx, case.h_factor * case.dx)
+            out.append(jump)
+    S.destroy(h)
+    return float(np.mean(out)) / math.sqrt(math.pi)
+
+
+@pytest.mark.xfail(strict=True, reason="measured: at density ratio 1000 the jump is 0.60, 0.52, 0.41 of Eq. 37 at "
+                                       "dp = 0.04, 0.02, 0.01 (0.69, 0.57, 0.45 with beta = 1), the paper reports "
+                                       "close agreement at dp = 0.01; the printed weights 2 phi of Eqs. 22 and 26 "
+                                       "give the liquid 0.70 of the CSF surface force at every resolution")
+def test_square_drop_laplace_jump_at_density_ratio_1000():
+    x = square_drop_jump(0.02)
+    assert abs(x - 1.0) <= 0.10, x
+
+
+@pytest.mark.xfail(strict=True, reason="measured: at density ratio 1000 (V0 = 1, gamma = 0.5) the fitted period is "
+                                       "0.436 and 0.372 at R = 12 and 24 dp against Eq. 35's 0.324; at gamma = 1 "
+                                       "the signal has no regular period; the paper reports < 5% for every gamma")
+def test_oscillating_drop_period_at_density_ratio_1000():
+    case = sphcases.oscillating_2d(ratio=1000.0, R_over_dp=24, V0=1.0, gamma=0.5)
+    tau = 2 * math.pi * math.sqrt(0.2 ** 3 * 1.0 / (6 * 0.5))
+    h = S.case_from_spec(case, precision=64, lanes=4, block=64)
+    phase = S.read_fields(h, S.FIELD_PHASE, 2)
+    ts, an = [], []
+    info = S.case_info(h)
+    while info["t"] < 3 * tau:
+        info = S.step(h, 5)
+        ts.append(info["t"])
+        an.append(ob.anisotropy(S.read_fields(h, S.FIELD_POS, 2), phase))
+    S.destroy(h)
+    period = ob.fit_period(ts, an, tau)
+    assert abs(period - tau) <= 0.05 * tau, (period, tau)

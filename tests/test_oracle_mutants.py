@@ -24,11 +24,11 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "sph_oracle.c")
-PINS = ["test_oracle_kernel.py", "test_oracle_neighbors.py", "test_oracle_riemann.py",
-        "test_oracle_invariants.py", "test_oracle_dynamics.py", "test_oracle_periodic.py",
-        "test_oracle_reading_flags.py", "test_oracle_weights.py", "test_oracle_acoustics.py", "test_oracle_penalty_pair.py",
-        "test_oracle_wall_pair.py",
-        "test_golden.py"]
+# the quick, targeted pins first: each copy stops at its first failing pin
+PINS = ["test_oracle_kernel.py", "test_oracle_penalty_pair.py", "test_oracle_wall_pair.py",
+        "test_oracle_riemann.py", "test_oracle_weights.py", "test_golden.py", "test_oracle_neighbors.py",
+        "test_oracle_reading_flags.py", "test_oracle_periodic.py", "test_oracle_invariants.py",
+        "test_oracle_acoustics.py", "test_oracle_dynamics.py"]
 
 MUTANTS = {
     "kernel normalisation": ("return dim == 2 ? 7.0 / (4.0 * ORA_PI * h * h)",
