@@ -423,7 +423,7 @@ __device__ __forceinline__ void walk_list_aux(const CaseDesc &d, const CasePhys<
         f(e >> NBR_SHIFT, sj, aj, rx, ry, rz, norm2<T, D>(rx, ry, rz));
     };
 #if SPHST_PIPE
-    static_assert(L == 1, "the two-deep pipeline walks one list per thread");
+    if constexpr (L == 1) {               // the two-deep pipeline walks one list per thread
     if (c == 0) return;
     uint32_t e = ld_list(p, pol);
     p += stride;
@@ -443,7 +443,9 @@ __device__ __forceinline__ void walk_list_aux(const CaseDesc &d, const CasePhys<
         }
         pair(ec, sc, ac);
     }
-#else
+    return;
+    }
+#endif
 #if SPHST_LIST_PREFETCH
     uint32_t next = sub < c ? ld_list(p, pol) : 0u;
 #endif
@@ -460,7 +462,6 @@ __device__ __forceinline__ void walk_list_aux(const CaseDesc &d, const CasePhys<
         const uint32_t j = e >> NBR_SHIFT;
         pair(e, ld4_keep(snap + j, pol), ld4_keep(aux + j, pol));
     }
-#endif
 }
 
 // neighbours of i with aux[j] loaded for f(j, s_j, aux_j, r_ij, r^2), from the

@@ -53,6 +53,8 @@ def launch(args) -> dict:
         kw["penalty_scope"] = args.penalty_scope
     if getattr(args, "wall_form", 0):
         kw["wall_form"] = args.wall_form
+    if getattr(args, "limiter", None) is not None:
+        kw["limiter"] = args.limiter
     if args.block:
         kw["block"] = args.block
     if args.lanes:
@@ -236,6 +238,8 @@ def main(argv=None):
     ap.add_argument("--xi", type=float, default=None, help="penalty coefficient (default: from the density ratio)")
     ap.add_argument("--penalty-scope", type=int, default=0, choices=[0, 1],
                     help="0: the penalty on both lines of Eq. 33; 1: on the cross-phase line only (ablation)")
+    ap.add_argument("--limiter", type=int, default=None, choices=[0, 1, 2, 3],
+                    help="Eq. 11 reading (0 dimensionless low-dissipation, 1 beta = 1, 2 beta = 0, 3 as printed)")
     ap.add_argument("--wall-form", type=int, default=0, choices=[0, 1],
                     help="wall pairs: 0 mirror state as it comes, 1 no suction (max(P*, 0))")
     ap.add_argument("--t-end", type=float, default=None, help="impact_3d: 2.0, shear_drop: 20.0")

@@ -221,6 +221,22 @@ def test_shear_drop_deformation_matches_taylor(precision):
     assert abs(D - ref) <= 0.15 * ref, (D, ref)
 
 
+def test_impact_at_u0_10_reaches_the_papers_end_time_with_full_dissipation():
+    # Section 5.4 in the paper's units at U0 = 10 (Re 2000, We 1000), d = 20
+    # dp: with the low-dissipation limiter of Eq. 11 (the default reading) the
+    # run stops at t = 1.1 of 4 (2.6 with walls that never pull); with
+    # beta = 1 it reaches t = 4 with every particle finite
+    case = sphcases.impact_sweep_case(10.0, 20)
+    h = S.case_from_spec(case, precision=32, limiter=1)
+    info = S.case_info(h)
+    while info["t"] < case.t_end:
+        info = S.step(h, 40)
+    vel = S.read_fields(h, S.FIELD_VEL, 3)
+    S.destroy(h)
+    assert info["status"] == 0 and info["t"] >= case.t_end
+    assert np.all(np.isfinite(vel))
+
+
 def test_impact_at_highest_reynolds_and_weber_stays_finite():
     # Section 5.4 at U0 = 50 (Re = 1e4, We = 2.5e4), coarse (d = 10 dp), the
     # first fifth of the paper's end time: no numerical instability
