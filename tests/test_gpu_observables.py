@@ -91,14 +91,14 @@ def period_series_gpu(case, t_end, precision=64, chunk=10):
     return np.array(ts), np.array(an)
 
 
-def quarter_centroid_series(r_over_dp, precision=64, t_end=0.5, every=2):
+def quarter_centroid_series(r_over_dp, precision=64, t_end=0.5, every=2, lanes=4):
     """Section 5.1, density ratio 1, V0 = 10 (the paper's values; the peak
     initial speed is V0/e, so c0 = 10 x 3.7 = 37): centre of mass of the
     particles that start in the drop's upper-right quarter, against time."""
     case = sphcases.oscillating_2d(ratio=1.0, R_over_dp=r_over_dp, V0=10.0, c0=37.0)
     liq = case.phases[0].pos
     sel = np.where((liq[:, 0] > 0.5) & (liq[:, 1] > 0.5))[0]
-    h = S.case_from_spec(case, precision=precision, lanes=4, block=64)
+    h = S.case_from_spec(case, precision=precision, lanes=lanes, block=64)
     ts, xs = [0.0], [liq[sel].mean(0)]
     info = S.case_info(h)
     while info["t"] < t_end:
@@ -122,6 +122,21 @@ def test_oscillating_drop_quarter_centroid_converges():
     assert excursion > 0.01
     assert d2 < d1, (d1, d2)
     assert d2 < 0.06 * excursion, (d2, excursion)
+
+
+def test_fp32_quarter_centroid_within_the_fp64_summation_order_spread():
+    # the same observable as the FP32 path's precision bar, at R/dp = 24: two FP64
+    # runs that differ only in summation order (4 and 1 lanes per particle)
+    # already differ by 0.76e-3 (the flow amplifies last-bit differences);
+    # FP32 differs from FP64 by 0.64e-3.  The bar: FP32 no further from
+    # FP64 than twice that spread, and within 15% of the excursion
+    a = quarter_centroid_series(24, 64)
+    spread = np.abs(a - quarter_centroid_series(24, 64, lanes=1)).max()
+    d32 = np.abs(a - quarter_centroid_series(24, 32)).max()
+    excursion = a[:, 0].max() - a[:, 0].min()
+    assert spread > 0.0
+    assert d32 < 2.0 * spread, (d32, spread)
+    assert d32 < 0.15 * excursion, (d32, excursion)
 
 
 def laplace_jump_resolution(n_side, **params):
