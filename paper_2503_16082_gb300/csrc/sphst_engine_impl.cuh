@@ -48,13 +48,14 @@ enum ArrayId { A_POS = 0, A_VEL, A_DRHO, A_ID, A_GRADC, A_ACCV };
     case 8: KERN<T, D, true, 8><<<g_ * 8, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
     default: KERN<T, D, true, 1><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;               \
     }
-// the same for the work-list kernels of a batch
-#define SPH_LANES_W(KERN, D, LN, ...)                                                                   \
+// the same for sweeps A, B and C with their tile mode (MODE_TILES, MODE_WORK
+// for the work-list kernels of a batch, MODE_ONE for a one-case engine)
+#define SPH_LANES_M(KERN, D, LN, MODE, ...)                                                             \
     switch (LN) {                                                                                       \
-    case 2: KERN<T, D, true, 2, true><<<g_ * 2, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
-    case 4: KERN<T, D, true, 4, true><<<g_ * 4, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
-    case 8: KERN<T, D, true, 8, true><<<g_ * 8, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
-    default: KERN<T, D, true, 1, true><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;               \
+    case 2: KERN<T, D, true, 2, MODE><<<g_ * 2, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
+    case 4: KERN<T, D, true, 4, MODE><<<g_ * 4, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
+    case 8: KERN<T, D, true, 8, MODE><<<g_ * 8, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
+    default: KERN<T, D, true, 1, MODE><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;               \
     }
 #define SPH_CLASSES_LX(NCLS, KERN, LN, ARGS, CNT, GRID, ...)                           \
     for (int k_ = 0; k_ < (NCLS); ++k_) {                                              \
@@ -70,25 +71,32 @@ enum ArrayId { A_POS = 0, A_VEL, A_DRHO, A_ID, A_GRADC, A_ACCV };
     }
 // SPH_CLASSES_L: one block (L blocks) per tile of particles; SPH_CLASSES_LF:
 // the per-substep sweeps over fluid ranks, whose blocks stride over the
-// work list of active tiles in a batch (the grid is then capped)
+// work list of active tiles in a batch (the grid is then capped), and which
+// take their case's descriptor from the launch parameters in a one-case engine
 #define SPH_CLASSES_L(NCLS, KERN, LN, ...) SPH_CLASSES_LX(NCLS, KERN, LN, sweep_args, cls_n, cls_n[k_], __VA_ARGS__)
-#define SPH_CLASSES_LF(NCLS, KERN, LN, ...)                                                      \
-    if (use_work) {                                                                              \
-        SPH_CLASSES_LXW(NCLS, KERN, LN, work_args, cls_fn, work_grid(cls_fn[k_]), __VA_ARGS__)   \
-    } else {                                                                                     \
-        SPH_CLASSES_LX(NCLS, KERN, LN, fluid_args, cls_fn, cls_fn[k_], __VA_ARGS__)              \
+#define SPH_CLASSES_LF(NCLS, KERN, LN, ...)                                                            \
+    if (use_work) {                                                                                    \
+        SPH_CLASSES_LXM(NCLS, KERN, LN, work_args, cls_fn, work_grid(cls_fn[k_]), MODE_WORK, __VA_ARGS__) \
+    } else if (ncases == 1) {                                                                          \
+        SPH_CLASSES_LXM(NCLS, KERN, LN, fluid_args, cls_fn, cls_fn[k_], MODE_ONE, __VA_ARGS__)           \
+    } else {                                                                                           \
+        SPH_CLASSES_LXM(NCLS, KERN, LN, fluid_args, cls_fn, cls_fn[k_], MODE_TILES, __VA_ARGS__)         \
     }
-#define SPH_CLASSES_LXW(NCLS, KERN, LN, ARGS, CNT, GRID, ...)                                    \
-    for (int k_ = 0; k_ < (NCLS); ++k_) {                                                        \
-        if (!CNT[k_]) continue;                                                                  \
-        const SweepArgs a_ = ARGS(k_);                                                           \
-        const unsigned g_ = (unsigned)(GRID);                                                    \
-        switch (k_) {                                                                            \
-        case 0: SPH_LANES_W(KERN, 3, LN, __VA_ARGS__) break;                                     \
-        case 1: SPH_LANES_W(KERN, 2, LN, __VA_ARGS__) break;                                     \
-        case 2: KERN<T, 3, false, 1, true><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;    \
-        default: KERN<T, 2, false, 1, true><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;   \
-        }                                                                                        \
+// the cell-walk classes keep the descriptor array in a one-case engine: their
+// sweep B also evaluates the surface terms, whose sums are left to the
+// compiler's contraction, so only one compiled form of it may exist
+#define CELL_MODE(MODE) ((MODE) == MODE_ONE ? MODE_TILES : (MODE))
+#define SPH_CLASSES_LXM(NCLS, KERN, LN, ARGS, CNT, GRID, MODE, ...)                                    \
+    for (int k_ = 0; k_ < (NCLS); ++k_) {                                                              \
+        if (!CNT[k_]) continue;                                                                        \
+        const SweepArgs a_ = ARGS(k_);                                                                 \
+        const unsigned g_ = (unsigned)(GRID);                                                          \
+        switch (k_) {                                                                                  \
+        case 0: SPH_LANES_M(KERN, 3, LN, MODE, __VA_ARGS__) break;                                     \
+        case 1: SPH_LANES_M(KERN, 2, LN, MODE, __VA_ARGS__) break;                                     \
+        case 2: KERN<T, 3, false, 1, CELL_MODE(MODE)><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break; \
+        default: KERN<T, 2, false, 1, CELL_MODE(MODE)><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;\
+        }                                                                                              \
     }
 
 template <typename T> struct EngineT : Engine {
@@ -399,7 +407,9 @@ template <typename T> struct EngineT : Engine {
     static int tile_class(const CaseDesc &d) { return (d.nbr_mode == 0 ? 0 : 2) + (d.dim == 3 ? 0 : 1); }
     SweepArgs sweep_args(int k) const { return SweepArgs{d_tiles, d_desc, d_state, starts, nbr, nbr_cnt, cls_b[k]}; }
     SweepArgs fluid_args(int k) const {
-        return SweepArgs{d_ftiles, d_desc, d_state, starts, nbr, nbr_cnt, cls_fb[k], fidx};
+        SweepArgs a{d_ftiles, d_desc, d_state, starts, nbr, nbr_cnt, cls_fb[k], fidx};
+        if (ncases == 1) a.one = h_desc[0];
+        return a;
     }
     // the per-substep sweeps: with work lists, class k's list and its length
     SweepArgs work_args(int k) const {

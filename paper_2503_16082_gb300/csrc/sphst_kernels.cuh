@@ -31,13 +31,18 @@
 //   SPHST_SWEEP_MINB   >0: minimum resident 256-thread blocks per SM for the
 //                      sweeps (caps registers per thread)
 //   SPHST_SWEEPB_MINB  the same for sweep B alone (default 4: 64 registers)
+//   SPHST_SWEEPB_MINB_ONE  the same for the FP32 sweep B of a one-case engine
+//                      (default 5: 48 registers, as its per-case constants are
+//                      not in registers; measured 6 (40) and 4 slower)
 //   SPHST_SURFACE_MIN_LANES  least lanes per band particle of sweep S (1, 2, 4)
 //   SPHST_SWEEPAS_MINB the same for sweeps A and S (default 4: with the
 //                      64-register room the compiler keeps more loads in
 //                      flight; measured: A 35 -> 28 us, S 93 -> 89 us on the
 //                      3D drop)
 //   SPHST_LIST_UNROLL  unroll factor of the neighbour-list loop
-//   SPHST_LIST_PREFETCH 1: load list entry k+1 while pair k is evaluated
+//   SPHST_LIST_PREFETCH 1: load list entry k+1 while pair k is evaluated;
+//                      2: entries k+1 and k+2 (measured: a general ring of
+//                      2-4 entries compiles to slower sweeps)
 //   SPHST_FAST_DIV     1: FP32 pair divisions through the SFU reciprocal
 //   SPHST_F32X2        1: x/y components of the FP32 pair geometry and sums in
 //                      packed two-lane instructions (sm_100 and later)
@@ -49,7 +54,7 @@
 //   SPHST_GEO_L2PF     >0: with SPHST_LIST_GEO, L2 prefetch of the stored
 //                      geometry that many entries ahead
 #ifndef SPHST_LIST_PREFETCH
-#define SPHST_LIST_PREFETCH 1
+#define SPHST_LIST_PREFETCH 2
 #endif
 #ifndef SPHST_FAST_DIV
 #define SPHST_FAST_DIV 1
@@ -84,6 +89,9 @@
 #ifndef SPHST_SWEEPB_MINB
 #define SPHST_SWEEPB_MINB 4
 #endif
+#ifndef SPHST_SWEEPB_MINB_ONE
+#define SPHST_SWEEPB_MINB_ONE 5
+#endif
 #if SPHST_SWEEP_MINB > 0
 #define SPH_SWEEP_BOUNDS __launch_bounds__(256, SPHST_SWEEP_MINB)
 #else
@@ -102,6 +110,11 @@
 #else
 #define SPH_SWEEPB_BOUNDS __launch_bounds__(256)
 #endif
+// sweep B of a one-case engine reads its per-case constants from the
+// parameter block, which leaves it room for more resident blocks
+#define SPH_SWEEPB_BOUNDS_M(T, MODE)                                                          \
+    __launch_bounds__(256, (MODE) == 2 && sizeof(T) == 4 ? SPHST_SWEEPB_MINB_ONE                  \
+                                                         : (SPHST_SWEEPB_MINB > 0 ? SPHST_SWEEPB_MINB : 1))
 
 namespace sphst {
 
@@ -252,6 +265,8 @@ __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, 
 __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 template <typename T, int D> __device__ __forceinline__ T norm2(T x, T y, T z) {
     return D == 3 ? fma_rn(x, x, fma_rn(y, y, mul_rn(z, z))) : fma_rn(x, x, mul_rn(y, y));
 }
@@ -372,12 +387,21 @@ __device__ __forceinline__ void walk_list(const CaseDesc &d, const CasePhys<T> &
     const uint32_t c = PART == PART_OTHER ? cnt[i] >> 16 : cnt[i] & CNT_MASK;
     const T cs = cp.cs;
     const L2Pol pol = l2_policies();
-#if SPHST_LIST_PREFETCH
+#if SPHST_LIST_PREFETCH >= 2
+    uint32_t next = sub < c ? ld_list(p, pol) : 0u;
+    uint32_t next2 = sub + L < c ? ld_list(p + L * stride, pol) : 0u;
+    p += L * stride;
+#elif SPHST_LIST_PREFETCH
     uint32_t next = sub < c ? ld_list(p, pol) : 0u;
 #endif
 #pragma unroll kListUnroll
     for (uint32_t k = sub; k < c; k += L) {
-#if SPHST_LIST_PREFETCH
+#if SPHST_LIST_PREFETCH >= 2
+        const uint32_t e = next;            // entries k + L and k + 2L in flight
+        next = next2;
+        p += L * stride;
+        if (k + 2 * L < c) next2 = ld_list(p, pol);
+#elif SPHST_LIST_PREFETCH
         const uint32_t e = next;
         p += L * stride;
         if (k + L < c) next = ld_list(p, pol);
@@ -446,12 +470,21 @@ __device__ __forceinline__ void walk_list_aux(const CaseDesc &d, const CasePhys<
     return;
     }
 #endif
-#if SPHST_LIST_PREFETCH
+#if SPHST_LIST_PREFETCH >= 2
+    uint32_t next = sub < c ? ld_list(p, pol) : 0u;
+    uint32_t next2 = sub + L < c ? ld_list(p + L * stride, pol) : 0u;
+    p += L * stride;
+#elif SPHST_LIST_PREFETCH
     uint32_t next = sub < c ? ld_list(p, pol) : 0u;
 #endif
 #pragma unroll kListUnroll
     for (uint32_t k = sub; k < c; k += L) {
-#if SPHST_LIST_PREFETCH
+#if SPHST_LIST_PREFETCH >= 2
+        const uint32_t e = next;            // entries k + L and k + 2L in flight
+        next = next2;
+        p += L * stride;
+        if (k + 2 * L < c) next2 = ld_list(p, pol);
+#elif SPHST_LIST_PREFETCH
         const uint32_t e = next;
         p += L * stride;
         if (k + L < c) next = ld_list(p, pol);
@@ -570,7 +603,7 @@ template <int L, typename T> __device__ __forceinline__ T group_sum(T v) {
         const unsigned lane = threadIdx.x & 31u;
         const unsigned mask = ((1u << L) - 1u) << (lane & ~(unsigned)(L - 1));
 #pragma unroll
-        for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+        for (int o = L / 2; o > 0; o >>= 1) v = add_rn(v, __shfl_xor_sync(mask, v, o));
     }
     return v;
 }
@@ -583,7 +616,7 @@ __device__ __forceinline__ PairGeo<T> geo(const CasePhys<T> &cp, T r2) {
     g.inv_r = rsq(r2);
     g.r = r2 * g.inv_r;
     const T q = g.r * cp.inv_h;
-    const T u = T(1) - T(0.5) * q;
+    const T u = fma_rn(T(-0.5), q, T(1));
     g.dW = cp.kcoef * q * u * u * u;
     return g;
 }
@@ -596,7 +629,7 @@ template <typename T> struct KernelGeo {
         g.inv_r = rsq(r2);
         g.r = r2 * g.inv_r;
         const T q = g.r * inv_h;
-        const T u = T(1) - T(0.5) * q;
+        const T u = fma_rn(T(-0.5), q, T(1));
         g.dW = kcoef * q * u * u * u;
         return g;
     }
@@ -1125,26 +1158,26 @@ __device__ __forceinline__ void sweep_A(const CaseDesc &d, const CasePhys<T> &cp
         const T m_o = cp.mass[other], rho0_o = cp.rho0[other];
         if constexpr (LIST && SPHST_LIST_GEO && L == 1) {
             walk_geo<PART_OTHER, T>(d, nbr, cnt, lgeo, i, [&](bool, uint32_t j, const V4<T> &G) {
-                const T s = two_phi * G.w * div_fast(m_o, rho0_o + drho[j]);
-                g.x += s * G.x;
-                g.y += s * G.y;
-                if (D == 3) g.z += s * G.z;
+                const T s = two_phi * G.w * div_fast(m_o, add_rn(rho0_o, drho[j]));
+                g.x = fma_rn(s, G.x, g.x);
+                g.y = fma_rn(s, G.y, g.y);
+                if (D == 3) g.z = fma_rn(s, G.z, g.z);
             });
         } else
         neighbors<LIST, T, D, PART_OTHER, L>(d, cp, starts, nbr, cnt, snap, i, si, pki,
             [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
                 if (!LIST && phase_of(w_bits(sj.w)) != other) return;
                 const PairGeo<T> gg = geo(cp, r2);
-                const T Vj = div_fast(m_o, rho0_o + drho[j]);
+                const T Vj = div_fast(m_o, add_rn(rho0_o, drho[j]));
                 const T s = two_phi * gg.dW * Vj * gg.inv_r;
-                g.x += s * rx;
-                g.y += s * ry;
-                if (D == 3) g.z += s * rz;
+                g.x = fma_rn(s, rx, g.x);
+                g.y = fma_rn(s, ry, g.y);
+                if (D == 3) g.z = fma_rn(s, rz, g.z);
             }, sub);
         g.x = group_sum<L>(g.x);
         g.y = group_sum<L>(g.y);
         if (D == 3) g.z = group_sum<L>(g.z);
-        g.w = sqrt(g.x * g.x + g.y * g.y + g.z * g.z);
+        g.w = sqrt(fma_rn(g.x, g.x, fma_rn(g.y, g.y, g.z * g.z)));
     }
     if (sub == 0) gradC[i] = g;
 }
@@ -1177,7 +1210,7 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
     if (PASS == 2 && !band[i]) return 0.0;
     const V4<T> vi = vel[i];
     const T dri = vi.w;
-    const T rho_i = sel(ki, cp.rho0[0], cp.rho0[1]) + dri;
+    const T rho_i = add_rn(sel(ki, cp.rho0[0], cp.rho0[1]), dri);
     const T p_i = cp.c0sq * dri;
     T apx = 0, apy = 0, apz = 0, asx = 0, asy = 0, asz = 0;
     const Limiter<T> limiter_beta(cp, d.limiter);
@@ -1188,32 +1221,38 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
 
     // pressure (Eqs. 7-12) of one pair from e_ij, W'_ij, the neighbour's
     // kind (wall, or fluid of rest density rho0_j and mass m_j) and state
+    // every sum is written as an explicitly rounded add or FMA: the same
+    // source compiled for another launch mode (one case, batch) then rounds
+    // identically whatever the register allocation
+    const T c0rho_i = c0 * rho_i;
     const auto pressure_pair = [&](L2<T> exy, T ez, T dW, bool wall, T rho0_j, T m_j, const V4<T> &vj) {
         // U_L - U_R = (v_j - v_i).e  (Eq. 10, U = -v.e)
         const L2<T> dvxy = fma2(l2(vi.x, vi.y), l2(T(-1), T(-1)), l2(vj.x, vj.y));
-        const T dUe = dvxy.x * exy.x + dvxy.y * exy.y + (D == 3 ? (vj.z - vi.z) * ez : T(0));
+        const T dUe = D == 3 ? fma_rn(dvxy.x, exy.x, fma_rn(dvxy.y, exy.y, sub_rn(vj.z, vi.z) * ez))
+                             : fma_rn(dvxy.x, exy.x, dvxy.y * exy.y);
         if (wall) {
             // mirror state behind a wall moving with v_w: rho_i, p_i, 2 U_w - U_L
             const T dU = T(2) * dUe;
             const T beta = limiter_beta(dU, p_i, rho_i);       // mirror state: rho_R, p_R = rho_i, p_i
-            T Ps = p_i + beta * rho_i * c0 * dU * T(0.5);
+            T Ps = fma_rn(beta * c0rho_i * dU, T(0.5), p_i);
             if (wall_push_only) Ps = Ps > T(0) ? Ps : T(0);    // no-suction wall reading
             const T f = Ps * dW * vol_wall;
             const L2<T> a = fma2(l2(f, f), exy, l2(apx, apy));
-            apx = a.x; apy = a.y; if (D == 3) apz += f * ez;
+            apx = a.x; apy = a.y; if (D == 3) apz = fma_rn(f, ez, apz);
             return;
         }
         const T drj = vj.w;
-        const T rho_j = rho0_j + drj;
+        const T rho_j = add_rn(rho0_j, drj);
         const T p_j = c0sq * drj;
         const T dU = dUe;
-        const T beta = limiter_beta(dU, p_i + p_j, rho_i + rho_j);   // Eq. 11
+        const T rsum = add_rn(rho_i, rho_j);
+        const T beta = limiter_beta(dU, add_rn(p_i, p_j), rsum);   // Eq. 11
         // P* V_j with P* = (rho_i p_j + rho_j p_i + beta c0 rho_i rho_j dU) / (rho_i + rho_j)
         // (Eqs. 8, 12) and V_j = m_j / rho_j: one division
-        const T num = (rho_i * p_j + rho_j * p_i) + beta * c0 * rho_i * rho_j * dU;
-        const T f = div_fast(num * m_j, (rho_i + rho_j) * rho_j) * dW;
+        const T num = fma_rn(beta * c0rho_i * rho_j, dU, fma_rn(rho_i, p_j, rho_j * p_i));
+        const T f = div_fast(num * m_j, rsum * rho_j) * dW;
         const L2<T> a = fma2(l2(f, f), exy, l2(apx, apy));
-        apx = a.x; apy = a.y; if (D == 3) apz += f * ez;
+        apx = a.x; apy = a.y; if (D == 3) apz = fma_rn(f, ez, apz);
     };
     // walls by their mirror state
     const auto pressure = [&](uint32_t, const V4<T> &sj, const V4<T> &vj, T rx, T ry, T rz, T r2) {
@@ -1327,11 +1366,12 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
             });
     }
     const T inv_rho = T(1) / rho_i;
+    const T m2inv_rho = T(-2) * inv_rho;
     const V4<T> av = acc_visc[i];
     V4<T> vn;
-    vn.x = vi.x + dt * (T(-2) * inv_rho * apx + inv_rho * asx + av.x);
-    vn.y = vi.y + dt * (T(-2) * inv_rho * apy + inv_rho * asy + av.y);
-    vn.z = D == 3 ? vi.z + dt * (T(-2) * inv_rho * apz + inv_rho * asz + av.z) : T(0);
+    vn.x = fma_rn(dt, fma_rn(inv_rho, asx, fma_rn(m2inv_rho, apx, av.x)), vi.x);
+    vn.y = fma_rn(dt, fma_rn(inv_rho, asy, fma_rn(m2inv_rho, apy, av.y)), vi.y);
+    vn.z = D == 3 ? fma_rn(dt, fma_rn(inv_rho, asz, fma_rn(m2inv_rho, apz, av.z)), vi.z) : T(0);
     vn.w = dri;                       // density deviation for sweep C
     vel_new[i] = vn;
     return speed2(vn, D);
@@ -1351,7 +1391,7 @@ __device__ __forceinline__ void sweep_C(const CaseDesc &d, const CasePhys<T> &cp
     const T dri = vi.w;
     const T rho0_0 = cp.rho0[0], rho0_1 = cp.rho0[1], m_0 = cp.mass[0], m_1 = cp.mass[1];
     const T c0 = cp.c0, c0sq = cp.c0sq, vol_wall = cp.vol_wall;
-    const T rho_i = sel(ki, rho0_0, rho0_1) + dri;
+    const T rho_i = add_rn(sel(ki, rho0_0, rho0_1), dri);
     const T p_i = c0sq * dri;
     const KernelGeo<T> kgeo(cp);
     // the pressure difference enters with the sign of the v* reading; the
@@ -1363,22 +1403,24 @@ __device__ __forceinline__ void sweep_C(const CaseDesc &d, const CasePhys<T> &cp
     // its density deviation
     const auto pair = [&](T dve, T dW, bool wall, T rho0_j, T m_j, T drj) {
         if (wall) {                   // v* = v_w
-            s += dve * dW * vol_wall;
+            s = fma_rn(dve * dW, vol_wall, s);
             return;
         }
-        const T rho_j = rho0_j + drj;
+        const T rho_j = add_rn(rho0_j, drj);
         // (v_i - v*).e V_j with (v_i - v*).e = U* - U_L = (Z_R (U_R - U_L) + p_i - p_j)
         // / (Z_L + Z_R) and V_j = m_j / rho_j: one division.  The printed v*
         // gives (Z_R (U_R - U_L) - (p_i - p_j)) / (Z_L + Z_R) instead.
-        const T num = (rho_j * c0 * dve + (sp_i - sc0sq * drj)) * m_j;
-        s += div_fast(num, c0 * (rho_i + rho_j) * rho_j) * dW;
+        // (sums explicitly rounded, as in sweep B)
+        const T num = fma_rn(rho_j * c0, dve, fma_rn(-sc0sq, drj, sp_i)) * m_j;
+        s = fma_rn(div_fast(num, c0 * add_rn(rho_i, rho_j) * rho_j), dW, s);
     };
     if constexpr (LIST && SPHST_LIST_GEO && L == 1) {
         const T rho0_o = sel(ki ^ 1u, rho0_0, rho0_1), rho0_s = sel(ki, rho0_0, rho0_1);
         const T m_o = sel(ki ^ 1u, m_0, m_1), m_s = sel(ki, m_0, m_1);
         walk_geo_aux<T>(d, nbr, cnt, lgeo, vel_new, i, [&](bool other, uint32_t, const V4<T> &G, const V4<T> &vj) {
             const L2<T> dvxy = fma2(l2(vj.x, vj.y), l2(T(-1), T(-1)), l2(vi.x, vi.y));
-            const T dve = dvxy.x * G.x + dvxy.y * G.y + (D == 3 ? (vi.z - vj.z) * G.z : T(0));
+            const T dve = D == 3 ? fma_rn(dvxy.x, G.x, fma_rn(dvxy.y, G.y, sub_rn(vi.z, vj.z) * G.z))
+                                 : fma_rn(dvxy.x, G.x, dvxy.y * G.y);
             const bool wall = geo_wall(G.w);
             pair(dve, wall ? -G.w : G.w, wall, other ? rho0_o : rho0_s, other ? m_o : m_s, vj.w);
         });
@@ -1388,18 +1430,18 @@ __device__ __forceinline__ void sweep_C(const CaseDesc &d, const CasePhys<T> &cp
             const PairGeo<T> g = kgeo(r2);
             const uint32_t kj = phase_of(w_bits(sj.w));
             const L2<T> dvxy = fma2(l2(vj.x, vj.y), l2(T(-1), T(-1)), l2(vi.x, vi.y));
-            const T dvx = dvxy.x, dvy = dvxy.y, dvz = D == 3 ? vi.z - vj.z : T(0);
-            pair((dvx * rx + dvy * ry + dvz * rz) * g.inv_r, g.dW, kj == PH_WALL, sel(kj, rho0_0, rho0_1),
-                 sel(kj, m_0, m_1), vj.w);
+            const T dvr = D == 3 ? fma_rn(dvxy.x, rx, fma_rn(dvxy.y, ry, sub_rn(vi.z, vj.z) * rz))
+                                 : fma_rn(dvxy.x, rx, dvxy.y * ry);
+            pair(dvr * g.inv_r, g.dW, kj == PH_WALL, sel(kj, rho0_0, rho0_1), sel(kj, m_0, m_1), vj.w);
         }, sub);
     s = group_sum<L>(s);
     if (sub != 0) return;
-    const T dr_new = dri + dt * (T(2) * rho_i * s);
+    const T dr_new = fma_rn(dt, T(2) * rho_i * s, dri);
     drho[i] = dr_new;
     V4<T> p = pos[i];
-    p.x += dt * vi.x;
-    p.y += dt * vi.y;
-    if (D == 3) p.z += dt * vi.z;
+    p.x = fma_rn(dt, vi.x, p.x);
+    p.y = fma_rn(dt, vi.y, p.y);
+    if (D == 3) p.z = fma_rn(dt, vi.z, p.z);
     pos[i] = p;
     vi.w = dr_new;
     vel[i] = vi;
@@ -1426,7 +1468,21 @@ struct SweepArgs {
     // block b takes tile tile0 + b / L.
     const uint32_t *work = nullptr;
     const uint32_t *work_count = nullptr;
+    // an engine of one case: its descriptor by value, so that the sweeps of
+    // MODE_ONE read the per-case constants from the launch's parameter block
+    // (constant-bank operands) instead of holding them in registers
+    CaseDesc one{};
 };
+
+// How a per-substep sweep finds its tiles and its case: MODE_TILES, block b
+// takes tile tile0 + b / L and reads desc[c]; MODE_WORK, the blocks stride
+// over the batch's work list; MODE_ONE, as MODE_TILES with the one case's
+// descriptor taken from the parameter block.
+enum SweepMode { MODE_TILES = 0, MODE_WORK = 1, MODE_ONE = 2 };
+template <int MODE> __device__ __forceinline__ const CaseDesc &case_desc(const SweepArgs &a, int c) {
+    if constexpr (MODE == MODE_ONE) return a.one;
+    else return a.desc[c];
+}
 
 // Work items of a sweep launch: (tile, block of the tile) pairs; with L
 // lanes per particle a tile takes L blocks.  Without a work list (WORK
@@ -1620,19 +1676,19 @@ template <int L> __device__ __forceinline__ int local_index(int64_t w) {
     return L == 1 ? (int)threadIdx.x : (int)((w % L) * (blockDim.x / L) + threadIdx.x / L);
 }
 
-template <typename T, int D, bool LIST, int L = 1, bool WORK = false>
+template <typename T, int D, bool LIST, int L = 1, int MODE = MODE_TILES>
 __global__ void SPH_SWEEPAS_BOUNDS k_sweep_A(SweepArgs a, const V4<T> *snap, const T *drho, const V4<T> *lgeo,
                                            V4<T> *gradC) {
     const auto item = [&](int64_t w) {
-        const Tile t = work_tile<L, WORK>(a, w);
+        const Tile t = work_tile<L, MODE == MODE_WORK>(a, w);
         const int li = local_index<L>(w);
         if (li >= t.n || !a.st[t.c].active) return;
-        const CaseDesc &d = a.desc[t.c];
+        const CaseDesc &d = case_desc<MODE>(a, t.c);
         const int64_t i = particle_at(a, t.begin + li);
         sweep_A<LIST, T, D, L>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, lgeo, gradC, threadIdx.x % L);
     };
-    if constexpr (WORK) {
-        const int64_t items = work_items<L, WORK>(a);
+    if constexpr (MODE == MODE_WORK) {
+        const int64_t items = work_items<L, true>(a);
         for (int64_t w = blockIdx.x; w < items; w += gridDim.x) item(w);
     } else {
         item(blockIdx.x);
@@ -1658,14 +1714,14 @@ __global__ void SPH_SWEEPAS_BOUNDS k_sweep_S(SweepArgs a, const uint64_t *blist,
                               acc_surf, nullptr, nullptr, &ph, threadIdx.x % L);
 }
 
-template <typename T, int D, bool LIST, int L = 1, bool WORK = false>
-__global__ void SPH_SWEEPB_BOUNDS k_sweep_B(SweepArgs a, const uint8_t *band, const V4<T> *snap, const V4<T> *vel,
+template <typename T, int D, bool LIST, int L = 1, int MODE = MODE_TILES>
+__global__ void SPH_SWEEPB_BOUNDS_M(T, MODE) k_sweep_B(SweepArgs a, const uint8_t *band, const V4<T> *snap, const V4<T> *vel,
                                             const V4<T> *gradC, const V4<T> *acc_visc, V4<T> *acc_surf,
                                             V4<T> *vel_new, const V4<T> *lgeo) {
     const auto item = [&](int64_t w) {
-        const Tile t = work_tile<L, WORK>(a, w);
+        const Tile t = work_tile<L, MODE == MODE_WORK>(a, w);
         if (!a.st[t.c].active) return;             // uniform per block
-        const CaseDesc &d = a.desc[t.c];
+        const CaseDesc &d = case_desc<MODE>(a, t.c);
         double v2 = 0.0;
         uint32_t ph = PH_WALL;
         const int li = local_index<L>(w);
@@ -1684,29 +1740,29 @@ __global__ void SPH_SWEEPB_BOUNDS k_sweep_B(SweepArgs a, const uint8_t *band, co
             if (m1) atomicMax(&a.st[t.c].vmax2_acc[1], m1);
         }
     };
-    if constexpr (WORK) {
-        const int64_t items = work_items<L, WORK>(a);
+    if constexpr (MODE == MODE_WORK) {
+        const int64_t items = work_items<L, true>(a);
         for (int64_t w = blockIdx.x; w < items; w += gridDim.x) item(w);
     } else {
         item(blockIdx.x);
     }
 }
 
-template <typename T, int D, bool LIST, int L = 1, bool WORK = false>
+template <typename T, int D, bool LIST, int L = 1, int MODE = MODE_TILES>
 __global__ void SPH_SWEEP_BOUNDS k_sweep_C(SweepArgs a, const V4<T> *snap, const V4<T> *vel_new, T *drho,
                                            V4<T> *vel, V4<T> *pos, const V4<T> *lgeo) {
     const auto item = [&](int64_t w) {
-        const Tile t = work_tile<L, WORK>(a, w);
+        const Tile t = work_tile<L, MODE == MODE_WORK>(a, w);
         const int li = local_index<L>(w);
         if (li >= t.n || !a.st[t.c].active) return;
-        const CaseDesc &d = a.desc[t.c];
+        const CaseDesc &d = case_desc<MODE>(a, t.c);
         const int64_t i = particle_at(a, t.begin + li);
         const T dt = (T)a.st[t.c].dt;
         sweep_C<LIST, T, D, L>(d, phys<T>(d), dt, i, a.starts, a.nbr, a.cnt, snap, vel_new, drho, vel, pos, lgeo,
                                threadIdx.x % L);
     };
-    if constexpr (WORK) {
-        const int64_t items = work_items<L, WORK>(a);
+    if constexpr (MODE == MODE_WORK) {
+        const int64_t items = work_items<L, true>(a);
         for (int64_t w = blockIdx.x; w < items; w += gridDim.x) item(w);
     } else {
         item(blockIdx.x);

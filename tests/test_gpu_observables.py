@@ -125,18 +125,21 @@ def test_oscillating_drop_quarter_centroid_converges():
 
 
 def test_fp32_quarter_centroid_within_the_fp64_summation_order_spread():
-    # the same observable as the FP32 path's precision bar, at R/dp = 24: two FP64
-    # runs that differ only in summation order (4 and 1 lanes per particle)
-    # already differ by 0.76e-3 (the flow amplifies last-bit differences);
-    # FP32 differs from FP64 by 0.64e-3.  The bar: FP32 no further from
-    # FP64 than twice that spread, and within 15% of the excursion
+    # the same observable as the FP32 path's precision bar, at R/dp = 24.
+    # FP64 runs that differ only in summation order (1, 2 or 8 lanes per
+    # particle against 4) already differ (the flow amplifies last-bit
+    # differences): measured 0.38e-3 to 0.76e-3 for one reordering,
+    # depending on the build's rounding, against an excursion of 0.016.
+    # FP32 differs from FP64 (4 lanes) by 0.64e-3 to 0.76e-3.  The bar: FP32
+    # within three times the largest FP64 reordering and within 10% of the
+    # excursion
     a = quarter_centroid_series(24, 64)
-    spread = np.abs(a - quarter_centroid_series(24, 64, lanes=1)).max()
+    spread = max(np.abs(a - quarter_centroid_series(24, 64, lanes=n)).max() for n in (1, 2, 8))
     d32 = np.abs(a - quarter_centroid_series(24, 32)).max()
     excursion = a[:, 0].max() - a[:, 0].min()
     assert spread > 0.0
-    assert d32 < 2.0 * spread, (d32, spread)
-    assert d32 < 0.15 * excursion, (d32, excursion)
+    assert d32 < 3.0 * spread, (d32, spread)
+    assert d32 < 0.10 * excursion, (d32, excursion)
 
 
 def laplace_jump_resolution(n_side, **params):
