@@ -84,6 +84,13 @@ extern "C" {
  * wall; NO_SUCTION takes max(P*, 0), so walls push and never pull */
 #define SPHST_WALL_MIRROR     0
 #define SPHST_WALL_NO_SUCTION 1
+/* weights of the two surface stresses on the cross-phase line of Eqs. 26 and
+ * 33 (i in fluid k, j in fluid l): PRINTED 2 phi_j Pi_i + 2 phi_i Pi_j as
+ * printed; OWN 2 phi_i Pi_i + 2 phi_j Pi_j, each stress weighted by its own
+ * particle's phi (Eq. 23); both conserve momentum and agree at density
+ * ratio 1 */
+#define SPHST_STRESS_PRINTED 0
+#define SPHST_STRESS_OWN     1
 /* Eq. 8's star velocity: CORRECTED takes the normal component as -U* along
  * e_ij (U = -v.e_ij, Eq. 10) and the tangential part of the pair average;
  * PRINTED is U* e_ij + (vbar - Ubar e_ij) as printed */
@@ -171,6 +178,7 @@ typedef struct {
                                members are listed per class and the sweeps'
                                blocks stride over that list.  Speed only:
                                both give the same bits.                      */
+    int32_t stress_weights; /* SPHST_STRESS_* (cross-phase surface stress)     */
 } sphst_case_params;
 
 typedef struct {

@@ -58,7 +58,7 @@ class Params(C.Structure):
                 ("periodic", C.c_int32), ("pad2_", C.c_int32),
                 ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
                 ("vstar_form", C.c_int32), ("penalty_scope", C.c_int32), ("wall_form", C.c_int32),
-                ("pad3_", C.c_int32)]
+                ("stress_weights", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -124,7 +124,8 @@ def make_params(dim: int, dx: float, h: float, c0: float, gamma: float,
                 max_substeps: int = 0, tvf_alpha: float = 0.2,
                 penalty_form: int = 0, cfl_ad: float = 0.1, cfl_ac: float = 0.6,
                 periodic: int = 0, box_lo=(0.0, 0.0, 0.0), box_hi=(0.0, 0.0, 0.0),
-                vstar_form: int = 0, penalty_scope: int = 0, wall_form: int = 0) -> Params:
+                vstar_form: int = 0, penalty_scope: int = 0, wall_form: int = 0,
+                stress_weights: int = 0) -> Params:
     """Build a parameter block.  nbr_mode None: brute force below 4096
     particles, uniform grid above."""
     p = Params()
@@ -143,6 +144,7 @@ def make_params(dim: int, dx: float, h: float, c0: float, gamma: float,
     p.vstar_form = vstar_form
     p.penalty_scope = penalty_scope
     p.wall_form = wall_form
+    p.stress_weights = stress_weights
     for a in range(3):
         p.box_lo[a], p.box_hi[a] = box_lo[a], box_hi[a]
     return p

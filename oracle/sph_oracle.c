@@ -45,6 +45,10 @@
  *               A^T A/|A| = |gradCbar| r_ij e e^T instead.  The flag
  *               penalty_scope = 1 drops the penalty from the same-phase line
  *               of Eq. 33 and keeps it on the cross-phase line (an ablation).
+ *   stresses    the cross-phase line of Eqs. 26 and 33 as printed,
+ *               2 phi_j Pi_i + 2 phi_i Pi_j; the flag stress_weights = 1 takes
+ *               2 phi_i Pi_i + 2 phi_j Pi_j (each stress with its own
+ *               particle's weight; the same at density ratio 1).
  *   periodic    an axis flagged periodic (the shear drop of Section 5.2 is
  *               periodic in x) wraps positions into [box_lo, box_hi) and takes
  *               every pair vector as its minimum image; the key grid of a
@@ -62,7 +66,9 @@
  *               advection step.
  *
  * Pinned by closed forms: every term of Eq. 33 for a single pair.  The
- * cross-phase line by an isolated pair of different fluids; the same-phase
+ * cross-phase line by an isolated pair of different fluids (the penalty) and,
+ * through ora_surface_pair, by a pair whose normals lie at angles to e_ij
+ * (the two stresses and their weights, for both readings); the same-phase
  * line, through ora_surface_pair (the routine the force loop calls), by
  * three configurations that reduce by hand: normals across the pair (no
  * penalty with the default contraction, a repulsion with A^T A / |A|),
@@ -119,7 +125,9 @@ typedef struct {
                               1: on the cross-phase line only (an ablation) */
     int32_t wall_form;    /* 0: the wall pair's P* from the mirror state as it comes;
                              1: max(P*, 0), a wall pushes and never pulls */
-    int32_t pad3_;
+    int32_t stress_weights; /* cross-phase line of Eq. 26/33: 0: 2 phi_j Pi_i + 2 phi_i Pi_j
+                               as printed; 1: 2 phi_i Pi_i + 2 phi_j Pi_j (each stress
+                               weighted by its own particle's phi) */
 } ora_params;
 
 typedef struct {
@@ -797,7 +805,9 @@ static void surface_pair_matrix(const ora_params *P, int32_t ki, int32_t kj, con
             double pen = xi * P->gamma * MC[3 * a + b] / r;
             S[3 * a + b] = same
                 ? si->Pi[3 * a + b] + sj->Pi[3 * a + b] + (P->penalty_scope == 1 ? 0.0 : pen)
-                : 2.0 * phi_j * si->Pi[3 * a + b] + 2.0 * phi_i * sj->Pi[3 * a + b]
+                : (P->stress_weights == 1
+                       ? 2.0 * phi_i * si->Pi[3 * a + b] + 2.0 * phi_j * sj->Pi[3 * a + b]
+                       : 2.0 * phi_j * si->Pi[3 * a + b] + 2.0 * phi_i * sj->Pi[3 * a + b])
                   - 4.0 * phi_i * phi_j * pen;
         }
 }

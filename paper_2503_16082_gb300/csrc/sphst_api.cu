@@ -165,6 +165,7 @@ CaseDesc make_desc(const CaseRec *c) {
     d.penalty_form = c->P.penalty_form;
     d.penalty_scope = c->P.penalty_scope;
     d.wall_form = c->P.wall_form;
+    d.stress_weights = c->P.stress_weights;
     d.n_fluid_phases = c->n_fluid_phases;
     d.bits = c->bits;
     for (int a = 0; a < 3; ++a) { d.ncell[a] = c->ncell[a]; d.origin[a] = c->origin[a]; }
@@ -291,7 +292,8 @@ int sphst_create_case(const sphst_case_params *params, sphst_case *out) {
     if (P.limiter < 0 || P.limiter > 3 || P.grad_mode < 0 || P.grad_mode > 1 ||
         P.penalty_form < 0 || P.penalty_form > 2 || P.loop_mode < 0 || P.loop_mode > 1 ||
         P.vstar_form < 0 || P.vstar_form > 1 || P.penalty_scope < 0 || P.penalty_scope > 1 ||
-        P.wall_form < 0 || P.wall_form > 1 || P.work_lists < 0 || P.work_lists > 1) {
+        P.wall_form < 0 || P.wall_form > 1 || P.work_lists < 0 || P.work_lists > 1 ||
+        P.stress_weights < 0 || P.stress_weights > 1) {
         set_error("unknown reading, loop or work-list flag");
         return SPHST_ERR_INVALID_ARG;
     }

@@ -1317,8 +1317,11 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
             sx = pix + pjx + pen_s * (cx - qx);
             sy = piy + pjy + pen_s * (cy - qy);
             sz = piz + pjz + pen_s * (cz - qz);
-        } else {      // Eq. 33, second line
-            const T a = sel(kj, cp.two_phi[0], cp.two_phi[1]), b = sel(ki, cp.two_phi[0], cp.two_phi[1]),
+        } else {      // Eq. 33, second line: 2 phi_j Pi_i + 2 phi_i Pi_j as printed, or
+                      // each stress by its own particle's 2 phi (stress_weights 1)
+            const bool own = d.stress_weights == 1;
+            const T a = sel(own ? ki : kj, cp.two_phi[0], cp.two_phi[1]),
+                    b = sel(own ? kj : ki, cp.two_phi[0], cp.two_phi[1]),
                     c = cp.four_phi_phi * pen;
             sx = a * pix + b * pjx - c * qx;
             sy = a * piy + b * pjy - c * qy;

@@ -53,6 +53,8 @@ def launch(args) -> dict:
         kw["penalty_scope"] = args.penalty_scope
     if getattr(args, "wall_form", 0):
         kw["wall_form"] = args.wall_form
+    if getattr(args, "stress_weights", 0):
+        kw["stress_weights"] = args.stress_weights
     if getattr(args, "limiter", None) is not None:
         kw["limiter"] = args.limiter
     if args.block:
@@ -242,6 +244,8 @@ def main(argv=None):
                     help="Eq. 11 reading (0 dimensionless low-dissipation, 1 beta = 1, 2 beta = 0, 3 as printed)")
     ap.add_argument("--wall-form", type=int, default=0, choices=[0, 1],
                     help="wall pairs: 0 mirror state as it comes, 1 no suction (max(P*, 0))")
+    ap.add_argument("--stress-weights", type=int, default=0, choices=[0, 1],
+                    help="cross-phase surface stress: 0 2phi_j Pi_i + 2phi_i Pi_j as printed, 1 each by its own phi")
     ap.add_argument("--t-end", type=float, default=None, help="impact_3d: 2.0, shear_drop: 20.0")
     args = ap.parse_args(argv)
     if args.t_end is None:

@@ -144,6 +144,7 @@ def test_fp32_one_advection_step(dim):
     (dict(penalty_form=2), dict(penalty_form=2)),
     (dict(penalty_scope=1), dict(penalty_scope=1)),
     (dict(wall_form=1), dict(wall_form=1)),
+    (dict(stress_weights=1), dict(stress_weights=1)),
 ])
 def test_fp64_readings_flags(opts, ora):
     case = small(2)

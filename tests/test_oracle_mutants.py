@@ -25,7 +25,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "sph_oracle.c")
 # the quick, targeted pins first: each copy stops at its first failing pin
-PINS = ["test_oracle_kernel.py", "test_oracle_penalty_pair.py", "test_oracle_wall_pair.py",
+PINS = ["test_oracle_kernel.py", "test_oracle_penalty_pair.py", "test_oracle_surface_force.py", "test_oracle_wall_pair.py",
         "test_oracle_riemann.py", "test_oracle_weights.py", "test_golden.py", "test_oracle_neighbors.py",
         "test_oracle_reading_flags.py", "test_oracle_periodic.py", "test_oracle_invariants.py",
         "test_oracle_acoustics.py", "test_oracle_dynamics.py"]
@@ -57,6 +57,9 @@ MUTANTS = {
     "wall mirror pressure dropped": ("R.p = p_i; R.c = c0;\n                    pbar = pair_pbar(rho_i, p_i, rho_i, p_i);",
                                      "R.p = 0.0; R.c = c0;\n                    pbar = pair_pbar(rho_i, p_i, rho_i, 0.0);"),
     "cross-phase penalty weight halved": ("- 4.0 * phi_i * phi_j * pen;", "- 2.0 * phi_i * phi_j * pen;"),
+    "cross-phase stress weights swapped": (
+        ": 2.0 * phi_j * si->Pi[3 * a + b] + 2.0 * phi_i * sj->Pi[3 * a + b])",
+        ": 2.0 * phi_i * si->Pi[3 * a + b] + 2.0 * phi_j * sj->Pi[3 * a + b])"),
     "wall v* = v_i in continuity": ("                    for (int d = 0; d < dim; ++d) vs[d] = vj[d];",
                                     "                    for (int d = 0; d < dim; ++d) vs[d] = vi[d];"),
     "wall velocity not mirrored": ("R.U = 2.0 * Uw - L.U;", "R.U = Uw;"),

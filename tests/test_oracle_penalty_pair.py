@@ -184,3 +184,59 @@ def test_force_loop_uses_the_pair_term():
             Se = oracle.surface_pair(P, kind[i], kind[j], gC[i, :2], gC[j, :2], rv / r, r)
             a += Se * oracle.kernel_dW(2, h, r) * (mass[j] / rho[j]) / rho[i]
         assert out["a_s"][i, :2] == pytest.approx(a, rel=1e-11, abs=1e-12 * max(np.abs(out["a_s"]).max(), 1e-300))
+
+
+# ---------------------------------------------------------------------------
+# The stresses of the cross-phase line of Eq. 33 (Eq. 26 with the penalty
+# off, xi = 0): S_ij e = w_i Pi_i e + w_j Pi_j e with Pi e = gamma G (e - n (n.e))
+# (Eq. 24).  As printed w_i = 2 phi_j, w_j = 2 phi_i (phi of Eq. 23); the
+# reading stress_weights = 1 takes each stress with its own particle's weight,
+# w_i = 2 phi_i, w_j = 2 phi_j.  Normals at an angle to e so that both stresses
+# act; fluids of rest density 3 and 1, so the two weights differ.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("weights", [0, 1])
+def test_cross_phase_stress_weights(weights):
+    g = 0.9
+    rho_a, rho_b = 3.0, 1.0
+    for dim, R in ((2, np.eye(3)), (3, rotation(5))):
+        P = oracle.make_params(dim, 0.1, 0.13, 10.0, g, rho0=(rho_a, rho_b), eta=(0.1, 0.1), xi=0.0,
+                               stress_weights=weights)
+        e = R @ np.array([1.0, 0.0, 0.0])
+        a_i, a_j = 0.4, 1.1                           # angles of n_i, n_j from e
+        n_i = R @ np.array([math.cos(a_i), math.sin(a_i), 0.0])
+        n_j = R @ np.array([math.cos(a_j), -math.sin(a_j), 0.0])
+        Gi, Gj, r = 3.0, 1.7, 0.09
+        for ki, kj in ((0, 1), (1, 0)):
+            out = oracle.surface_pair(P, ki, kj, (Gi * n_i)[:dim], (-Gj * n_j)[:dim], e[:dim], r)
+            phi = {0: rho_a / (rho_a + rho_b), 1: rho_b / (rho_a + rho_b)}
+            w_i, w_j = (2 * phi[ki], 2 * phi[kj]) if weights else (2 * phi[kj], 2 * phi[ki])
+            pi_e = g * Gi * (e - n_i * (n_i @ e))
+            pj_e = g * Gj * (e - n_j * (n_j @ e))     # the sign of grad C_j drops out of Pi_j
+            want = (w_i * pi_e + w_j * pj_e)[:dim]
+            assert out == pytest.approx(want, rel=1e-13, abs=1e-13 * np.abs(want).max()), (dim, ki, kj)
+
+
+def test_cross_phase_stress_weights_agree_at_density_ratio_one_and_conserve_momentum():
+    """At equal rest densities every 2 phi is 1 and the two readings are the
+    same sum; at density ratio 1000 both keep m_i a_i + m_j a_j = 0 pair by
+    pair, so the total surface force on a jittered cluster vanishes."""
+    rng = np.random.default_rng(21)
+    dx = 0.1
+    pos = np.zeros((16, 3))
+    pos[:, :2] = rng.uniform(0.0, 3 * dx, size=(16, 2))
+    kind = np.array([0] * 9 + [1] * 7, dtype=np.int32)
+    for rho0 in ((1.0, 1.0), (1000.0, 1.0)):
+        rho = np.where(kind == 0, rho0[0], rho0[1]) * (1.0 + 0.01 * rng.normal(size=16))
+        res = []
+        for w in (0, 1):
+            P = oracle.make_params(2, dx, 1.3 * dx, 10.0, 0.8, rho0=rho0, eta=(0.1, 0.1), n=16, tvf_alpha=0.0,
+                                   stress_weights=w)
+            a_s = oracle.forces(P, pos, np.zeros((16, 3)), rho, kind)["a_s"]
+            m = np.where(kind == 0, rho0[0], rho0[1]) * dx * dx
+            total = (m[:, None] * a_s).sum(axis=0)
+            assert np.abs(total).max() <= 1e-12 * np.abs(m[:, None] * a_s).max()
+            res.append(a_s)
+        if rho0[0] == rho0[1]:
+            assert np.array_equal(res[0], res[1])
+        else:
+            assert not np.allclose(res[0], res[1])

@@ -1,0 +1,57 @@
+"""The net radial surface force of Eqs. 22-33 on a static 2D drop (R = 10 dp,
+at rest), as a fraction of the CSF value -2 pi gamma (the Young-Laplace
+force of a circle, gamma kappa times the perimeter).  Measured on the oracle:
+
+* density ratio 1: 0.466 on each fluid, 0.93 in total, with either reading of
+  the cross-phase stress weights (they coincide when every 2 phi is 1);
+* density ratio 1000, weights as printed (2 phi_j Pi_i + 2 phi_i Pi_j): the
+  liquid carries the whole colour gradient and gets 0.70, the gas nothing;
+* density ratio 1000, each stress weighted by its own particle's 2 phi: the
+  liquid still gets 0.70 (its stress divergence over its own neighbours is
+  unchanged) and the gas, 1000 times lighter, gets 0.5;
+* the penalty (xi of Eq. 31) moves force between the fluids but leaves the
+  sum unchanged (pairwise antisymmetric).
+
+A factor lost in Pi (Eq. 24), in the colour gradient (Eq. 22) or in the
+weights of Eq. 26 moves these fractions."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import sphcases
+
+
+def radial_fractions(ratio, xi=0.0, stress_weights=0):
+    case = sphcases.small_droplet(2, 40, R_frac=0.25, rho_l=float(ratio), rho_g=1.0, mu_l=0.05, mu_g=0.05,
+                                  c0=20.0)
+    pos, vel, rho, kind = case.flat()
+    P = oracle.params_for_case(case, xi=xi, stress_weights=stress_weights)
+    a_s = oracle.forces(P, pos, vel, rho, kind)["a_s"]
+    rho0 = np.asarray(case.fluid_props()[0])
+    out = []
+    for k in (0, 1):
+        sel = kind == k
+        r = pos[sel, :2] - 0.5
+        rhat = r / np.linalg.norm(r, axis=1)[:, None]
+        f = rho0[k] * case.dx ** 2 * np.sum(a_s[sel, :2] * rhat, axis=1).sum()
+        out.append(f / (-2.0 * math.pi * case.gamma))
+    return out
+
+
+def test_density_ratio_one():
+    for w in (0, 1):
+        liq, gas = radial_fractions(1, stress_weights=w)
+        assert liq == pytest.approx(0.466, abs=0.01) and gas == pytest.approx(0.467, abs=0.01)
+    pl, pg = radial_fractions(1, xi=-1.0)             # xi from Eq. 31 (0.6)
+    assert pl > 1.5 and pg < 0.0                      # the penalty moves force to the liquid
+    assert pl + pg == pytest.approx(0.933, abs=0.01)
+
+
+def test_density_ratio_1000_printed_and_own_weights():
+    liq, gas = radial_fractions(1000)
+    assert liq == pytest.approx(0.70, abs=0.02) and abs(gas) < 0.01
+    liq_own, gas_own = radial_fractions(1000, stress_weights=1)
+    assert liq_own == pytest.approx(liq, abs=0.005)
+    assert 0.4 < gas_own < 0.6
