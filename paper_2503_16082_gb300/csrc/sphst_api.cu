@@ -179,6 +179,13 @@ CaseDesc make_desc(const CaseRec *c) {
     d.max_substeps = c->P.max_substeps > 0 ? c->P.max_substeps : 1000000;
     d.cfl_ad = c->P.cfl_ad;
     d.cfl_ac = c->P.cfl_ac;
+    // Eq. 17's surface-tension bound sqrt(rho0 h^3 / (2 pi gamma)) depends on
+    // the case only: formed once here, with the same IEEE operations in the
+    // same order as the per-substep criterion used to
+    for (int k = 0; k < 2; ++k)
+        d.dt_surf[k] = d.gamma > 0.0
+                           ? std::sqrt((c->rho0[k] * d.h * d.h * d.h) / (2.0 * 3.14159265358979323846 * d.gamma))
+                           : 0.0;
     d.nbr_mode = c->P.nbr_mode;
     d.periodic = c->P.periodic;
     d.vstar_printed = c->P.vstar_form == SPHST_VSTAR_PRINTED;

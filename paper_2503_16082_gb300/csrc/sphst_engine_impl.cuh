@@ -38,9 +38,8 @@ enum ArrayId { A_POS = 0, A_VEL, A_DRHO, A_ID, A_GRADC, A_ACCV };
         }                                                                              \
     }
 
-// SPH_CLASSES_L: the same for sweeps A, S, B and C, whose list classes run
-// with LN lanes per particle (L blocks per tile); SPH_CLASSES_LF runs the
-// tiles over fluid ranks (sweeps B and C).
+// SPH_LANES / SPH_CLASSES_LX: the same for the sweeps whose list classes run
+// with LN lanes per particle (L blocks per tile or per grid block).
 #define SPH_LANES(KERN, D, LN, ...)                                                               \
     switch (LN) {                                                                                 \
     case 2: KERN<T, D, true, 2><<<g_ * 2, block, 0, stream>>>(a_, __VA_ARGS__); break;            \
@@ -69,11 +68,13 @@ enum ArrayId { A_POS = 0, A_VEL, A_DRHO, A_ID, A_GRADC, A_ACCV };
         default: KERN<T, 2, false><<<g_, block, 0, stream>>>(a_, __VA_ARGS__); break;  \
         }                                                                              \
     }
-// SPH_CLASSES_L: one block (L blocks) per tile of particles; SPH_CLASSES_LF:
-// the per-substep sweeps over fluid ranks, whose blocks stride over the
-// work list of active tiles in a batch (the grid is then capped), and which
-// take their case's descriptor from the launch parameters in a one-case engine
-#define SPH_CLASSES_L(NCLS, KERN, LN, ...) SPH_CLASSES_LX(NCLS, KERN, LN, sweep_args, cls_n, cls_n[k_], __VA_ARGS__)
+// SPH_CLASSES_BAND: the sweeps over a list class's band list (S, and A of
+// the list classes): a few blocks per SM whose threads stride over the list
+#define SPH_CLASSES_BAND(KERN, LN, ...) SPH_CLASSES_LX(2, KERN, LN, sweep_args, cls_n, band_grid(cls_n[k_], LN), __VA_ARGS__)
+// SPH_CLASSES_LF: the per-substep sweeps over fluid ranks, whose blocks
+// stride over the work list of active tiles in a batch (the grid is then
+// capped), and which take their case's descriptor from the launch parameters
+// in a one-case engine
 #define SPH_CLASSES_LF(NCLS, KERN, LN, ...)                                                            \
     if (use_work) {                                                                                    \
         SPH_CLASSES_LXM(NCLS, KERN, LN, work_args, cls_fn, work_grid(cls_fn[k_]), MODE_WORK, __VA_ARGS__) \
@@ -82,12 +83,22 @@ enum ArrayId { A_POS = 0, A_VEL, A_DRHO, A_ID, A_GRADC, A_ACCV };
     } else {                                                                                           \
         SPH_CLASSES_LXM(NCLS, KERN, LN, fluid_args, cls_fn, cls_fn[k_], MODE_TILES, __VA_ARGS__)         \
     }
+// the same from class K0 on
+#define SPH_CLASSES_LFK(K0, NCLS, KERN, LN, ...)                                                        \
+    if (use_work) {                                                                                    \
+        SPH_CLASSES_LXMK(K0, NCLS, KERN, LN, work_args, cls_fn, work_grid(cls_fn[k_]), MODE_WORK, __VA_ARGS__) \
+    } else if (ncases == 1) {                                                                          \
+        SPH_CLASSES_LXMK(K0, NCLS, KERN, LN, fluid_args, cls_fn, cls_fn[k_], MODE_ONE, __VA_ARGS__)      \
+    } else {                                                                                           \
+        SPH_CLASSES_LXMK(K0, NCLS, KERN, LN, fluid_args, cls_fn, cls_fn[k_], MODE_TILES, __VA_ARGS__)    \
+    }
 // the cell-walk classes keep the descriptor array in a one-case engine: their
 // sweep B also evaluates the surface terms, whose sums are left to the
 // compiler's contraction, so only one compiled form of it may exist
 #define CELL_MODE(MODE) ((MODE) == MODE_ONE ? MODE_TILES : (MODE))
-#define SPH_CLASSES_LXM(NCLS, KERN, LN, ARGS, CNT, GRID, MODE, ...)                                    \
-    for (int k_ = 0; k_ < (NCLS); ++k_) {                                                              \
+#define SPH_CLASSES_LXM(NCLS, KERN, LN, ARGS, CNT, GRID, MODE, ...) SPH_CLASSES_LXMK(0, NCLS, KERN, LN, ARGS, CNT, GRID, MODE, __VA_ARGS__)
+#define SPH_CLASSES_LXMK(K0, NCLS, KERN, LN, ARGS, CNT, GRID, MODE, ...)                              \
+    for (int k_ = (K0); k_ < (NCLS); ++k_) {                                                              \
         if (!CNT[k_]) continue;                                                                        \
         const SweepArgs a_ = ARGS(k_);                                                                 \
         const unsigned g_ = (unsigned)(GRID);                                                          \
@@ -128,6 +139,7 @@ template <typename T> struct EngineT : Engine {
     uint32_t *d_ftn = nullptr, *d_woff = nullptr, *d_wcount = nullptr, *d_work = nullptr;
     int64_t *d_ft_first = nullptr, *d_cls0 = nullptr;
     int64_t work_cap = 0;                           // blocks of a work-list launch (per lane)
+    int64_t sm_count = 0;                           // SMs of the device (band-list grids)
     int *d_loop_flag = nullptr;
     double *d_read = nullptr;              // read-back buffer
     double *d_diag = nullptr;              // diagnostics partials + result
@@ -338,6 +350,12 @@ template <typename T> struct EngineT : Engine {
             SPH_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
             work_cap = (int64_t)std::max(sms, 1) * 16;
         }
+        {
+            int dev = 0, sms = 0;
+            SPH_CK(cudaGetDevice(&dev));
+            SPH_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            sm_count = std::max(sms, 1);
+        }
         SPH_CK(cudaMemcpyAsync(d_desc, h_desc.data(), sizeof(CaseDesc) * ncases, cudaMemcpyHostToDevice, stream));
         // fill each case
         for (int c = 0; c < ncases; ++c) {
@@ -421,6 +439,11 @@ template <typename T> struct EngineT : Engine {
         return a;
     }
     int64_t work_grid(int64_t tiles) const { return use_work ? std::min(tiles, work_cap) : tiles; }
+    // blocks (per lane) of a band-list sweep: at most one per tile, at most 8
+    // blocks of all lanes per SM
+    int64_t band_grid(int64_t tiles, int lanes_) const {
+        return std::max<int64_t>(1, std::min<int64_t>(tiles, sm_count * 8 / std::max(lanes_, 1)));
+    }
     // list the active cases' tiles (after the criterion kernel of a substep)
     void launch_work_lists() {
         if (!use_work) return;
@@ -474,11 +497,19 @@ template <typename T> struct EngineT : Engine {
         return SPHST_OK;
     }
 
+    // colour gradient: over the interface band in the list classes (zero
+    // elsewhere, from the start of the advection step), over every fluid
+    // particle in the cell-walk classes
+    void launch_colour() {
+        SPH_CLASSES_BAND(k_sweep_A_band, lanes, band_list + band_base[k_], band_count + k_, snap, drho, gradC);
+        SPH_CLASSES_LFK(2, 4, k_sweep_A, lanes, snap, drho, lgeo, gradC);
+    }
+
     int launch_body(cudaGraphConditionalHandle h, int use_handle) {
         k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, h, use_handle);
         launch_work_lists();
-        SPH_CLASSES_LF(4, k_sweep_A, lanes, snap, drho, lgeo, gradC);
-        SPH_CLASSES_L(2, k_sweep_S, surface_lanes(), band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
+        launch_colour();
+        SPH_CLASSES_BAND(k_sweep_S, surface_lanes(), band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
         SPH_CLASSES_LF(4, k_sweep_B, lanes, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo);
         SPH_CLASSES_LF(4, k_sweep_C, lanes, snap, vel_new, drho, vel, pos, lgeo);
         SPH_CK(cudaGetLastError());
@@ -613,9 +644,9 @@ template <typename T> struct EngineT : Engine {
                 k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, 0, 0);
                 launch_work_lists();
             });
-            timed(3, ncls, [&] { SPH_CLASSES_LF(4, k_sweep_A, lanes, snap, drho, lgeo, gradC); });
+            timed(3, ncls, [&] { launch_colour(); });
             timed(6, nlist, [&] {
-                SPH_CLASSES_L(2, k_sweep_S, surface_lanes(), band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
+                SPH_CLASSES_BAND(k_sweep_S, surface_lanes(), band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
             });
             timed(4, ncls, [&] { SPH_CLASSES_LF(4, k_sweep_B, lanes, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo); });
             timed(5, ncls, [&] { SPH_CLASSES_LF(4, k_sweep_C, lanes, snap, vel_new, drho, vel, pos, lgeo); });

@@ -118,6 +118,7 @@ struct CaseDesc {
     double rho0[2], eta[2];
     int64_t max_substeps;
     double cfl_ad, cfl_ac;
+    double dt_surf[2];         // the surface-tension bound of Eq. 17 per fluid (0: none)
     int32_t nbr_mode;          // 0: neighbour list built per advection step; 1: cell walk
     int32_t nbr_k;             // list capacity per particle
     int64_t nbr_base;          // first list word of this case

@@ -875,12 +875,11 @@ __global__ void k_fluid_scatter(int64_t n, const V4<T> *snap, const uint32_t *ra
                                 V4<T> *gradC, uint32_t *cnt) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    if (phase_of(w_bits(snap[i].w)) != PH_WALL) {
-        fidx[rank[i]] = (uint32_t)i;
-    } else {
-        gradC[i] = V4<T>{T(0), T(0), T(0), T(0)};
-        cnt[i] = 0u;
-    }
+    // the colour gradient starts every advection step at zero: the list
+    // classes' colour sweep then writes only the interface band
+    gradC[i] = V4<T>{T(0), T(0), T(0), T(0)};
+    if (phase_of(w_bits(snap[i].w)) != PH_WALL) fidx[rank[i]] = (uint32_t)i;
+    else cnt[i] = 0u;
 }
 
 // ================================================================ time step
@@ -977,11 +976,7 @@ static __global__ void k_dt(int ncases, const CaseDesc *desc, CaseState *st, int
             if (!s.present[k]) continue;
             if (!(vmax[k] <= 1e300)) finite = false;
             double t = __ddiv_rn(d.h, __dadd_rn(d.c0, vmax[k]));
-            if (d.gamma > 0.0) {
-                const double ts = sqrt(__ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(d.rho0[k], d.h), d.h), d.h),
-                                                 __dmul_rn(__dmul_rn(2.0, 3.14159265358979323846), d.gamma)));
-                if (ts < t) t = ts;
-            }
+            if (d.gamma > 0.0 && d.dt_surf[k] < t) t = d.dt_surf[k];   // formed on the host (Eq. 17)
             const double cand = __dmul_rn(d.cfl_ac, t);
             if (cand < dt_ac) dt_ac = cand;
         }
@@ -1698,23 +1693,45 @@ __global__ void SPH_SWEEPAS_BOUNDS k_sweep_A(SweepArgs a, const V4<T> *snap, con
     }
 }
 
+// colour gradient of the band particles (list classes): one thread (L lanes)
+// per entry of the class's compacted band list, as in S; the launch's
+// threads stride over the list (the grid is a few blocks per SM, since the
+// list's length is known only on the device).  A particle outside
+// the band has no neighbour of the other fluid, so its colour gradient is the
+// zero written at the start of the advection step.
+template <typename T, int D, bool LIST, int L = 1>
+__global__ void SPH_SWEEPAS_BOUNDS k_sweep_A_band(SweepArgs a, const uint64_t *blist, const uint32_t *bcount,
+                                                const V4<T> *snap, const T *drho, V4<T> *gradC) {
+    const int64_t items = (int64_t)*bcount * L;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < items; t += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t e = blist[t / L];
+        const int c = (int)(e >> 32);
+        const int64_t i = (int64_t)(uint32_t)e;
+        if (!a.st[c].active) continue;
+        const CaseDesc &d = a.desc[c];
+        sweep_A<LIST, T, D, L>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, nullptr, gradC, threadIdx.x % L);
+    }
+}
+
 // surface sum of the band particles (list classes only), before B: one
 // thread (L lanes) per entry of the class's compacted band list, so warps
-// are full of band particles; threads past the list's length exit at once
+// are full of band particles; the threads stride over the list (a group of
+// L lanes stays together: the stride is a multiple of L)
 template <typename T, int D, bool LIST, int L = 1>
 __global__ void SPH_SWEEPAS_BOUNDS k_sweep_S(SweepArgs a, const uint64_t *blist, const uint32_t *bcount,
                                            const uint8_t *band, const V4<T> *snap, const V4<T> *vel,
                                            const V4<T> *gradC, V4<T> *acc_surf) {
-    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L;
-    if (k >= (int64_t)*bcount) return;
-    const uint64_t e = blist[k];
-    const int c = (int)(e >> 32);
-    const int64_t i = (int64_t)(uint32_t)e;
-    if (!a.st[c].active) return;
-    const CaseDesc &d = a.desc[c];
-    uint32_t ph;
-    sweep_B<LIST, 2, T, D, L>(d, phys<T>(d), T(0), i, a.starts, a.nbr, a.cnt, band, snap, vel, gradC, nullptr,
-                              acc_surf, nullptr, nullptr, &ph, threadIdx.x % L);
+    const int64_t items = (int64_t)*bcount * L;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < items; t += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t e = blist[t / L];
+        const int c = (int)(e >> 32);
+        const int64_t i = (int64_t)(uint32_t)e;
+        if (!a.st[c].active) continue;
+        const CaseDesc &d = a.desc[c];
+        uint32_t ph;
+        sweep_B<LIST, 2, T, D, L>(d, phys<T>(d), T(0), i, a.starts, a.nbr, a.cnt, band, snap, vel, gradC, nullptr,
+                                  acc_surf, nullptr, nullptr, &ph, threadIdx.x % L);
+    }
 }
 
 template <typename T, int D, bool LIST, int L = 1, int MODE = MODE_TILES>
