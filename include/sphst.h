@@ -104,7 +104,9 @@ extern "C" {
 /* how the sweeps find neighbours: LIST builds a neighbour list of the frozen
  * configuration once per advection step (Section 3.3) and every substep's
  * sweeps read it; CELLS walks the 3^d cells around each particle every time.
- * Both visit neighbours in the same order and give identical results. */
+ * Both find the same neighbours; the list holds those of the other fluid
+ * first, each part in increasing particle index, so the sums are the same
+ * terms in another order and agree to rounding. */
 #define SPHST_NBR_LIST  0
 #define SPHST_NBR_CELLS 1
 

@@ -51,6 +51,8 @@
 //                      unchanged, sweep C 40% slower; off)
 //   SPHST_PIPE         1: sweeps B and C load the next neighbour's position and
 //                      state while the current pair is evaluated
+//   SPHST_LIST_SORTED  1: the neighbour list holds each part in increasing j
+//                      (cells by table index); 0: in the cell walk's order
 //   SPHST_GEO_L2PF     >0: with SPHST_LIST_GEO, L2 prefetch of the stored
 //                      geometry that many entries ahead
 #ifndef SPHST_LIST_PREFETCH
@@ -88,6 +90,14 @@
 #endif
 #ifndef SPHST_SWEEPB_MINB
 #define SPHST_SWEEPB_MINB 4
+#endif
+#ifndef SPHST_LIST_SORTED
+#define SPHST_LIST_SORTED 1
+#endif
+#if SPHST_LIST_SORTED
+#define LIST_WALK walk_sorted
+#else
+#define LIST_WALK walk
 #endif
 #ifndef SPHST_SWEEPB_MINB_ONE
 #define SPHST_SWEEPB_MINB_ONE 5
@@ -364,7 +374,8 @@ __device__ __forceinline__ bool walk(const CaseDesc &d, const CasePhys<T> &cp,
 // lanes read 32 consecutive words).  An entry is j << 6 | cell code, the code
 // holding (o + 1) per axis in 2 bits, o the neighbour cell's offset.  Each
 // list holds the neighbours of the other fluid phase first, then the rest,
-// each part in cell-walk order; cnt[i] = count | (other-phase count << 16),
+// each part in increasing j (SPHST_LIST_SORTED; else in cell-walk order);
+// cnt[i] = count | (other-phase count << 16),
 // so the colour-gradient sweep reads only the first part.
 constexpr uint32_t NBR_SHIFT = 6;
 constexpr uint32_t CNT_MASK = 0xffffu;
@@ -372,6 +383,62 @@ enum NbrPart { PART_ALL = 0, PART_OTHER = 1 };
 template <int D>
 __device__ __forceinline__ uint32_t cell_code(int ox, int oy, int oz) {
     return (uint32_t)(ox + 1) | ((uint32_t)(oy + 1) << 2) | (D == 3 ? ((uint32_t)(oz + 1) << 4) : 0u);
+}
+
+// The same neighbours as walk(), visited in increasing index j: the 3^D
+// cells are taken in increasing order of their cell-table index (the cells
+// are stored in that order, each cell's particles in index order).  The
+// neighbour list is built in this order, so that the 32 lanes of a warp,
+// neighbouring particles with largely the same neighbours, gather entries k
+// that lie close together in memory.
+template <typename T, int D, typename F>
+__device__ __forceinline__ bool walk_sorted(const CaseDesc &d, const CasePhys<T> &cp,
+                                            const uint32_t *__restrict__ starts,
+                                            const V4<T> *__restrict__ snap, int64_t i,
+                                            const V4<T> &si, uint32_t pki, F &&f) {
+    constexpr int NC = D == 3 ? 27 : 9;
+    const int cx = cell_x<D>(pki), cy = cell_y<D>(pki), cz = cell_z<D>(pki);
+    const uint32_t toff = (uint32_t)d.table_off;
+    uint32_t cell[NC];
+    uint32_t code[NC];
+    int nc = 0;
+    for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz) {
+        int nz = cz + oz;
+        if (D == 3 && !wrap_cell(d, 2, nz)) continue;
+        for (int oy = -1; oy <= 1; ++oy) {
+            int ny = cy + oy;
+            if (!wrap_cell(d, 1, ny)) continue;
+            for (int ox = -1; ox <= 1; ++ox) {
+                int nx = cx + ox;
+                if (!wrap_cell(d, 0, nx)) continue;
+                // insertion by cell-table index
+                const uint32_t m = toff + morton<D>(nx, ny, nz), c = cell_code<D>(ox, oy, oz);
+                int b = nc++;
+                while (b > 0 && cell[b - 1] > m) { cell[b] = cell[b - 1]; code[b] = code[b - 1]; --b; }
+                cell[b] = m;
+                code[b] = c;
+            }
+        }
+    }
+    const T cs = cp.cs, R2 = cp.four_h2;
+    bool coincident = false;
+    for (int q = 0; q < nc; ++q) {
+        const int ox = (int)(code[q] & 3u) - 1, oy = (int)((code[q] >> 2) & 3u) - 1, oz = (int)((code[q] >> 4) & 3u) - 1;
+        const T sx = sub_rn(si.x, mul_rn(T(ox), cs)), sy = sub_rn(si.y, mul_rn(T(oy), cs));
+        const T sz = D == 3 ? sub_rn(si.z, mul_rn(T(oz), cs)) : T(0);
+        const uint32_t b = __ldg(starts + cell[q]), e = __ldg(starts + cell[q] + 1);
+        for (uint32_t j = b; j < e; ++j) {
+            const V4<T> sj = ld4(snap + j);
+            const T rx = sub_rn(sx, sj.x), ry = sub_rn(sy, sj.y);
+            const T rz = D == 3 ? sub_rn(sz, sj.z) : T(0);
+            const T r2 = norm2<T, D>(rx, ry, rz);
+            if (r2 < R2 && j != (uint32_t)i) {
+                if (r2 > T(0)) f(j, sj, rx, ry, rz, r2);
+                else coincident = true;
+            }
+        }
+    }
+    return coincident;
 }
 
 // With L lanes per particle, lane `sub` of the particle's group takes the
@@ -1529,11 +1596,11 @@ __device__ __forceinline__ void build_list(const CaseDesc &d, const CasePhys<T> 
     };
     // one walk: the rest goes straight to the list, other-phase entries to a
     // small buffer; then, where there are any, the rest moves up and the
-    // buffer goes in front (each part keeps the walk order)
+    // buffer goes in front (each part keeps the walk's order)
     constexpr uint32_t OBUF = 32;
     uint32_t obuf[OBUF];
     uint32_t c_rest = 0, c_other = 0;
-    bool coinc = walk<T, D>(d, cp, starts, snap, i, si, pki,
+    bool coinc = LIST_WALK<T, D>(d, cp, starts, snap, i, si, pki,
         [&](uint32_t j, const V4<T> &sj, T, T, T, T) {
             const uint32_t pkj = w_bits(sj.w);
             if (phase_of(pkj) == other) {
@@ -1550,7 +1617,7 @@ __device__ __forceinline__ void build_list(const CaseDesc &d, const CasePhys<T> 
         // rare: more other-phase neighbours than the buffer holds; two walks
         c = 0;
         for (int part = 0; part < 2; ++part) {
-            coinc |= walk<T, D>(d, cp, starts, snap, i, si, pki,
+            coinc |= LIST_WALK<T, D>(d, cp, starts, snap, i, si, pki,
                 [&](uint32_t j, const V4<T> &sj, T, T, T, T) {
                     const uint32_t pkj = w_bits(sj.w);
                     if ((phase_of(pkj) == other) != (part == 0)) return;
