@@ -498,10 +498,11 @@ template <typename T> struct EngineT : Engine {
     }
 
     // colour gradient: over the interface band in the list classes (zero
-    // elsewhere, from the start of the advection step), over every fluid
-    // particle in the cell-walk classes
+    // elsewhere, from the start of the advection step), with the surface
+    // sweep's lanes per band particle; over every fluid particle in the
+    // cell-walk classes
     void launch_colour() {
-        SPH_CLASSES_BAND(k_sweep_A_band, lanes, band_list + band_base[k_], band_count + k_, snap, drho, gradC);
+        SPH_CLASSES_BAND(k_sweep_A_band, surface_lanes(), band_list + band_base[k_], band_count + k_, snap, drho, gradC);
         SPH_CLASSES_LFK(2, 4, k_sweep_A, lanes, snap, drho, lgeo, gradC);
     }
 
