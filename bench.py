@@ -311,7 +311,11 @@ def run_ours(args, dist: Dist):
     roofs = device_roofs()
     peak = roofs["fp32_tflops"] if f32 else FP64_PEAK_TFLOPS
     roofline = {"bound": "alu",
-                "kernel": f"k_sweep_B<{'float' if f32 else 'double'}, {spec.dim}, {'false' if surf_in_b else 'true'}>",
+                # the instantiation a one-case engine launches: <T, D, list, lanes, mode>
+                # (mode 2: the case's constants in the launch parameters; the
+                # cell-walk classes run mode 0)
+                "kernel": (f"k_sweep_B<{'float' if f32 else 'double'}, {spec.dim}, {0 if surf_in_b else 1}, "
+                           f"{1 if surf_in_b else (args.lanes or 1)}, {0 if surf_in_b else 2}>"),
                 "achieved": round(achieved, 3),
                 "peak": round(peak, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4),
@@ -333,6 +337,13 @@ def run_ours(args, dist: Dist):
         roofline["issue"] = {"warp_instructions": insts, "achieved": round(insts / b_avg / 1e12, 4),
                              "peak": round(issue_peak / 1e12, 4), "unit": "T warp-instructions/s",
                              "frac": round(insts / b_avg / issue_peak, 4)}
+    # the L1 throughput of the same launch (ncu, recorded with the traffic):
+    # the list sweeps' gathers are what holds them
+    l1 = (recorded_traffic(f"sweeps_{args.workload}_f{args.precision}_{args.nbr}.md", "k_sweep_B",
+                           "l1tex_throughput_permille") if f32 and not surf_in_b else None)
+    if l1:
+        roofline["l1"] = {"throughput_frac": l1 / 1000.0,
+                          "metric": "l1tex__throughput.avg.pct_of_peak_sustained_active (ncu)"}
     try:                                   # measured FMA roof beside the derived one
         roofline["peak_measured_fma"] = round(S.fma_peak(args.precision)["tflops"], 2)
         roofline["frac_of_measured_fma"] = round(achieved / roofline["peak_measured_fma"], 4)
