@@ -58,7 +58,7 @@ class Params(C.Structure):
                 ("periodic", C.c_int32), ("pad2_", C.c_int32),
                 ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
                 ("vstar_form", C.c_int32), ("penalty_scope", C.c_int32), ("wall_form", C.c_int32),
-                ("stress_weights", C.c_int32)]
+                ("stress_weights", C.c_int32), ("surface_corr", C.c_int32), ("pad4_", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -93,12 +93,16 @@ def _load():
                                           P(C.c_uint64), ip, lp]
             lib.ora_riemann_pair.restype = None
             lib.ora_riemann_pair.argtypes = [P(Params), d, d, dp, d, d, dp, dp, dp]
+            lib.ora_surface_pair_apply.restype = None
+            lib.ora_surface_pair_apply.argtypes = [P(Params), i32, i32, dp, dp, dp, d, dp, dp]
             lib.ora_surface_pair.restype = None
             lib.ora_surface_pair.argtypes = [P(Params), i32, i32, dp, dp, dp, d, dp]
             lib.ora_dt_advection.restype = d
             lib.ora_dt_advection.argtypes = [P(Params), dp, ip]
             lib.ora_dt_acoustic.restype = d
             lib.ora_dt_acoustic.argtypes = [P(Params), dp, ip]
+            lib.ora_correction_matrices.restype = C.c_int
+            lib.ora_correction_matrices.argtypes = [P(Params), i64, dp, dp, dp, ip, dp, dp]
             lib.ora_forces.restype = C.c_int
             lib.ora_forces.argtypes = [P(Params), i64, dp, dp, dp, ip, dp, dp, dp, dp, dp, dp]
             lib.ora_run.restype = C.c_int
@@ -125,7 +129,7 @@ def make_params(dim: int, dx: float, h: float, c0: float, gamma: float,
                 penalty_form: int = 0, cfl_ad: float = 0.1, cfl_ac: float = 0.6,
                 periodic: int = 0, box_lo=(0.0, 0.0, 0.0), box_hi=(0.0, 0.0, 0.0),
                 vstar_form: int = 0, penalty_scope: int = 0, wall_form: int = 0,
-                stress_weights: int = 0) -> Params:
+                stress_weights: int = 0, surface_corr: int = 0) -> Params:
     """Build a parameter block.  nbr_mode None: brute force below 4096
     particles, uniform grid above."""
     p = Params()
@@ -145,6 +149,7 @@ def make_params(dim: int, dx: float, h: float, c0: float, gamma: float,
     p.penalty_scope = penalty_scope
     p.wall_form = wall_form
     p.stress_weights = stress_weights
+    p.surface_corr = surface_corr
     for a in range(3):
         p.box_lo[a], p.box_hi[a] = box_lo[a], box_hi[a]
     return p
@@ -239,6 +244,18 @@ def surface_pair(params: Params, k_i: int, k_j: int, gradC_i, gradC_j, e, r: flo
     return out[:params.dim].copy()
 
 
+def surface_pair_apply(params: Params, k_i: int, k_j: int, gradC_i, gradC_j, e, r: float, v) -> np.ndarray:
+    """The pair matrix S_ij of Eq. 33 (as in ``surface_pair``) applied to the
+    vector v instead of e_ij."""
+    lib = _load()
+    three = lambda x: np.ascontiguousarray(np.pad(np.asarray(x, float), (0, 3 - len(x))))
+    gi, gj, ee, vv = three(gradC_i), three(gradC_j), three(e), three(v)
+    out = np.zeros(3)
+    lib.ora_surface_pair_apply(C.byref(params), int(k_i), int(k_j), _dp(gi), _dp(gj), _dp(ee), float(r), _dp(vv),
+                               _dp(out))
+    return out[:params.dim].copy()
+
+
 def dt_advection(params: Params, vmax, present=(1, 1)) -> float:
     v = np.asarray(vmax, dtype=np.float64)
     pr = np.asarray(present, dtype=np.int32)
@@ -268,6 +285,23 @@ def forces(params: Params, pos, vel, rho, kind):
     if st != 0:
         raise ValueError(f"oracle status {st}")
     return out
+
+
+def correction_matrices(params: Params, pos, vel, rho, kind):
+    """Eq. 15's correction matrix of every particle, over all neighbours and
+    over the neighbours of the particle's own fluid: two (n, 3, 3) arrays."""
+    lib = _load()
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    vel = np.ascontiguousarray(vel, dtype=np.float64)
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    kind = np.ascontiguousarray(kind, dtype=np.int32)
+    n = len(pos)
+    B = np.zeros((n, 9))
+    Bk = np.zeros((n, 9))
+    st = lib.ora_correction_matrices(C.byref(params), n, _dp(pos), _dp(vel), _dp(rho), _ip(kind), _dp(B), _dp(Bk))
+    if st != 0:
+        raise ValueError(f"oracle status {st}")
+    return B.reshape(n, 3, 3), Bk.reshape(n, 3, 3)
 
 
 def run(params: Params, pos, vel, rho, kind, n_adv: int):

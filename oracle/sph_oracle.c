@@ -45,6 +45,10 @@
  *               A^T A/|A| = |gradCbar| r_ij e e^T instead.  The flag
  *               penalty_scope = 1 drops the penalty from the same-phase line
  *               of Eq. 33 and keeps it on the cross-phase line (an ablation).
+ *   correction  the same-phase line of Eq. 33 with grad_i W_ij as printed; the
+ *               flag surface_corr = 1 takes (B^k_i + B^k_j)/2 grad_i W_ij, B^k
+ *               the correction matrix of Eq. 15 summed over the particle's own
+ *               fluid (once per advection step, frozen configuration).
  *   stresses    the cross-phase line of Eqs. 26 and 33 as printed,
  *               2 phi_j Pi_i + 2 phi_i Pi_j; the flag stress_weights = 1 takes
  *               2 phi_i Pi_i + 2 phi_j Pi_j (each stress with its own
@@ -128,6 +132,10 @@ typedef struct {
     int32_t stress_weights; /* cross-phase line of Eq. 26/33: 0: 2 phi_j Pi_i + 2 phi_i Pi_j
                                as printed; 1: 2 phi_i Pi_i + 2 phi_j Pi_j (each stress
                                weighted by its own particle's phi) */
+    int32_t surface_corr; /* same-phase line of Eq. 33: 0: grad_i W_ij as printed;
+                             1: (B^k_i + B^k_j)/2 grad_i W_ij with B^k the correction
+                             matrix of Eq. 15 summed over the particle's own fluid */
+    int32_t pad4_;
 } ora_params;
 
 typedef struct {
@@ -831,10 +839,28 @@ void ora_surface_pair(const ora_params *P, int32_t ki, int32_t kj, const double 
     }
 }
 
+/* The same pair matrix S_ij applied to any vector v (3 entries): out = S_ij v.
+ * With the surface_corr reading the force loop applies the same-phase S_ij
+ * to the corrected kernel gradient instead of e_ij. */
+void ora_surface_pair_apply(const ora_params *P, int32_t ki, int32_t kj, const double *gi,
+                            const double *gj, const double *e, double r, const double *v, double *out)
+{
+    stress_t si, sj;
+    surface_stress(P, gi, &si);
+    surface_stress(P, gj, &sj);
+    double S[9];
+    surface_pair_matrix(P, ki, kj, &si, &sj, gi, gj, e, r, ora_xi(P), S);
+    for (int a = 0; a < 3; ++a) {
+        double s = 0.0;
+        for (int b = 0; b < P->dim; ++b) s += S[3 * a + b] * v[b];
+        out[a] = a < P->dim ? s : 0.0;
+    }
+}
+
 /* Eq. 7 (pressure) and Eq. 33 (surface tension with the projected penalty),
  * the latter divided by m_i.  ap and as receive the two accelerations. */
 static void pressure_surface_acc(const ora_params *P, const state_t *S,
-                                 const pairs_t *pp, const double *gradC,
+                                 const pairs_t *pp, const double *gradC, const double *Bk,
                                  double *ap, double *as)
 {
     const int dim = P->dim;
@@ -884,9 +910,23 @@ static void pressure_surface_acc(const ora_params *P, const state_t *S,
                 surface_stress(P, gradC + 3 * j, &sj);
                 double Sij[9];
                 surface_pair_matrix(P, ki, kj, &si, &sj, gradC + 3 * i, gradC + 3 * j, e, pp->r[k], xi, Sij);
+                /* reading (surface_corr 1): the same-phase line takes the kernel
+                 * gradient corrected by the mean of the two particles' own-fluid
+                 * correction matrices (Eq. 15), so the divergence of the stress,
+                 * summed over one fluid only, is first-order consistent up to the
+                 * interface; the mean keeps the pair term antisymmetric */
+                double gW[3] = {gradW[0], gradW[1], gradW[2]};
+                if (Bk && kj == ki) {
+                    for (int a = 0; a < dim; ++a) {
+                        double t = 0.0;
+                        for (int b = 0; b < dim; ++b)
+                            t += 0.5 * (Bk[9 * i + 3 * a + b] + Bk[9 * j + 3 * a + b]) * gradW[b];
+                        gW[a] = t;
+                    }
+                }
                 for (int a = 0; a < dim; ++a) {
                     double s = 0.0;
-                    for (int b = 0; b < dim; ++b) s += Sij[3 * a + b] * gradW[b];
+                    for (int b = 0; b < dim; ++b) s += Sij[3 * a + b] * gW[b];
                     a_s[a] += s * Vj / rho_i;
                 }
             }
@@ -939,7 +979,7 @@ static void continuity_rate(const ora_params *P, const state_t *S, const pairs_t
 /* ------------------------------------------------------------------------ */
 /* Eq. 15: B_i = -(sum_j r_ij (x) grad_i W_ij V_j)^-1, a dim x dim matrix. */
 static void correction_matrix(const ora_params *P, const state_t *S, const pairs_t *pp,
-                              double *B)
+                              double *B, int own_fluid)
 {
     const int dim = P->dim;
 #pragma omp parallel for schedule(static)
@@ -947,6 +987,8 @@ static void correction_matrix(const ora_params *P, const state_t *S, const pairs
         double M[9] = {0};
         for (int64_t k = pp->row[i]; k < pp->row[i + 1]; ++k) {
             int64_t j = pp->col[k];
+            /* own_fluid: the sum of Eq. 15 over the neighbours of i's fluid only */
+            if (own_fluid && S->kind[j] != S->kind[i]) continue;
             double Vj = volume_of(P, S, j);
             for (int a = 0; a < dim; ++a)
                 for (int b = 0; b < dim; ++b)
@@ -1069,13 +1111,36 @@ int ora_forces(const ora_params *P, int64_t n, const double *pos, const double *
     pairs_t pp;
     if (pairs_build(P, n, pos, &pp) != 0) return 3;
     color_gradient(P, &S, &pp, gradC);
-    pressure_surface_acc(P, &S, &pp, gradC, ap, as);
+    double *Bk = 0;
+    if (P->surface_corr == 1) {
+        Bk = (double *)malloc(sizeof(double) * 9 * (size_t)(n > 0 ? n : 1));
+        correction_matrix(P, &S, &pp, Bk, 1);
+    }
+    pressure_surface_acc(P, &S, &pp, gradC, Bk, ap, as);
+    free(Bk);
     viscous_acc(P, &S, &pp, av);
     continuity_rate(P, &S, &pp, drho);
     double *B = (double *)malloc(sizeof(double) * 9 * (size_t)(n > 0 ? n : 1));
-    correction_matrix(P, &S, &pp, B);
+    correction_matrix(P, &S, &pp, B, 0);
     tvf_shift(P, &S, &pp, B, dr);
     free(B);
+    pairs_free(&pp);
+    return 0;
+}
+
+/* The correction matrix of Eq. 15 of every particle at one state, summed over
+ * all neighbours (B, as the transport velocity uses it) and over the
+ * neighbours of the particle's own fluid (Bk, the surface_corr reading); 9
+ * entries each, row-major. */
+int ora_correction_matrices(const ora_params *P, int64_t n, const double *pos, const double *vel,
+                            const double *rho, const int32_t *kind, double *B, double *Bk)
+{
+    set_threads(P);
+    state_t S = {n, (double *)pos, (double *)vel, (double *)rho, kind};
+    pairs_t pp;
+    if (pairs_build(P, n, pos, &pp) != 0) return 3;
+    correction_matrix(P, &S, &pp, B, 0);
+    correction_matrix(P, &S, &pp, Bk, 1);
     pairs_free(&pp);
     return 0;
 }
@@ -1109,6 +1174,7 @@ int ora_run(const ora_params *P, int64_t n, double *pos, double *vel, double *rh
     double *av = (double *)calloc(n3, sizeof(double));
     double *drho = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
     double *Bm = (double *)calloc(n3 * 3, sizeof(double));
+    double *Bk = P->surface_corr == 1 ? (double *)calloc(n3 * 3, sizeof(double)) : 0;
     double *dr = (double *)calloc(n3, sizeof(double));
     int32_t present[2] = {phase_present(&S, 0), phase_present(&S, 1)};
     int64_t max_sub = P->max_substeps > 0 ? P->max_substeps : 1000000;
@@ -1126,8 +1192,9 @@ int ora_run(const ora_params *P, int64_t n, double *pos, double *vel, double *rh
         pairs_t pp;
         if (pairs_build(P, n, snap, &pp) != 0) { status = 3; break; }
         viscous_acc(P, &S, &pp, av);
+        if (Bk) correction_matrix(P, &S, &pp, Bk, 1);
         if (P->tvf_alpha > 0.0) {
-            correction_matrix(P, &S, &pp, Bm);
+            correction_matrix(P, &S, &pp, Bm, 0);
             tvf_shift(P, &S, &pp, Bm, dr);
             for (int64_t i = 0; i < n; ++i)
                 for (int d = 0; d < dim; ++d) pos[3 * i + d] = wrap_coord(P, d, pos[3 * i + d] + dr[3 * i + d]);
@@ -1145,7 +1212,7 @@ int ora_run(const ora_params *P, int64_t n, double *pos, double *vel, double *rh
             double dt = last ? rem : dt_ac;
 
             color_gradient(P, &S, &pp, gradC);
-            pressure_surface_acc(P, &S, &pp, gradC, ap, as);
+            pressure_surface_acc(P, &S, &pp, gradC, Bk, ap, as);
 #pragma omp parallel for schedule(static)
             for (int64_t i = 0; i < n; ++i) {
                 if (!is_fluid(kind[i])) continue;
@@ -1175,7 +1242,7 @@ int ora_run(const ora_params *P, int64_t n, double *pos, double *vel, double *rh
     if (gradC_out) memcpy(gradC_out, gradC, sizeof(double) * (size_t)n * 3);
     if (av_out) memcpy(av_out, av, sizeof(double) * (size_t)n * 3);
     info->status = status;
-    free(snap); free(gradC); free(ap); free(as); free(av); free(drho); free(Bm); free(dr);
+    free(snap); free(gradC); free(ap); free(as); free(av); free(drho); free(Bm); free(Bk); free(dr);
     return status;
 }
 

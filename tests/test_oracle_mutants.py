@@ -57,6 +57,11 @@ MUTANTS = {
     "wall mirror pressure dropped": ("R.p = p_i; R.c = c0;\n                    pbar = pair_pbar(rho_i, p_i, rho_i, p_i);",
                                      "R.p = 0.0; R.c = c0;\n                    pbar = pair_pbar(rho_i, p_i, rho_i, 0.0);"),
     "cross-phase penalty weight halved": ("- 4.0 * phi_i * phi_j * pen;", "- 2.0 * phi_i * phi_j * pen;"),
+    "own-fluid correction from i alone": (
+        "t += 0.5 * (Bk[9 * i + 3 * a + b] + Bk[9 * j + 3 * a + b]) * gradW[b];",
+        "t += Bk[9 * i + 3 * a + b] * gradW[b];"),
+    "own-fluid correction over every neighbour": (
+        "if (own_fluid && S->kind[j] != S->kind[i]) continue;", "(void)own_fluid;"),
     "cross-phase stress weights swapped": (
         ": 2.0 * phi_j * si->Pi[3 * a + b] + 2.0 * phi_i * sj->Pi[3 * a + b])",
         ": 2.0 * phi_i * si->Pi[3 * a + b] + 2.0 * phi_j * sj->Pi[3 * a + b])"),

@@ -240,3 +240,67 @@ def test_cross_phase_stress_weights_agree_at_density_ratio_one_and_conserve_mome
             assert np.array_equal(res[0], res[1])
         else:
             assert not np.allclose(res[0], res[1])
+
+
+# ---------------------------------------------------------------------------
+# The own-fluid correction reading of the same-phase line (surface_corr = 1):
+# S_ij (B^k_i + B^k_j)/2 grad_i W_ij, B^k Eq. 15's correction matrix summed
+# over the particle's own fluid.
+# ---------------------------------------------------------------------------
+def mixed_cluster(seed, n_a=9, n_b=7):
+    rng = np.random.default_rng(seed)
+    dx = 0.1
+    pos = np.zeros((n_a + n_b, 3))
+    pos[:, :2] = rng.uniform(0.0, 3 * dx, size=(n_a + n_b, 2))
+    kind = np.array([0] * n_a + [1] * n_b, dtype=np.int32)
+    return dx, pos, kind, rng
+
+
+def test_own_fluid_correction_matrix():
+    """B^k equals Eq. 15's B where every neighbour is of the particle's own
+    fluid, and differs from it where the other fluid is near."""
+    case_pos = np.array([[x, y, 0.0] for x in np.arange(8) * 0.1 for y in np.arange(8) * 0.1])
+    kind = np.where(case_pos[:, 0] < 0.35, 0, 1).astype(np.int32)
+    rho = np.where(kind == 0, 3.0, 1.0)
+    P = oracle.make_params(2, 0.1, 0.13, 10.0, 1.0, rho0=(3.0, 1.0), eta=(0.1, 0.1), n=len(case_pos))
+    B, Bk = oracle.correction_matrices(P, case_pos, np.zeros_like(case_pos), rho, kind)
+    far = np.abs(case_pos[:, 0] - 0.35) > 0.3          # no other-fluid neighbour within 2h = 0.26
+    near = np.abs(case_pos[:, 0] - 0.35) < 0.1
+    assert far.any() and near.any()
+    assert np.array_equal(B[far], Bk[far])
+    assert np.abs(B[near] - Bk[near]).max() > 0.1
+
+
+def test_own_fluid_correction_conserves_momentum_and_is_wired():
+    """At density ratio 1000 the corrected pair term stays antisymmetric
+    (the mean of the two matrices), so the total surface force of a jittered
+    cluster vanishes; and each particle's a^s equals the sum of the pair
+    matrix applied to (B^k_i + B^k_j)/2 e_ij for same-phase pairs and to e_ij
+    for the others, times W'(r) V_j / rho_i."""
+    dx, pos, kind, rng = mixed_cluster(31)
+    n = len(pos)
+    rho0 = (1000.0, 1.0)
+    rho = np.where(kind == 0, rho0[0], rho0[1]) * (1.0 + 0.01 * rng.normal(size=n))
+    h = 1.3 * dx
+    P = oracle.make_params(2, dx, h, 10.0, 0.8, rho0=rho0, eta=(0.1, 0.1), n=n, tvf_alpha=0.0, surface_corr=1)
+    out = oracle.forces(P, pos, np.zeros((n, 3)), rho, kind)
+    a_s, gC = out["a_s"], out["gradC"]
+    m = np.where(kind == 0, rho0[0], rho0[1]) * dx * dx
+    assert np.abs((m[:, None] * a_s).sum(axis=0)).max() <= 1e-12 * np.abs(m[:, None] * a_s).max()
+    _, Bk = oracle.correction_matrices(P, pos, np.zeros((n, 3)), rho, kind)
+    mass = np.where(kind == 0, rho0[0], rho0[1]) * dx * dx
+    for i in range(n):
+        a = np.zeros(2)
+        for j in range(n):
+            rv = pos[i, :2] - pos[j, :2]
+            r = float(np.linalg.norm(rv))
+            if j == i or not (0.0 < r < 2 * h):
+                continue
+            e = rv / r
+            v = 0.5 * (Bk[i, :2, :2] + Bk[j, :2, :2]) @ e if kind[i] == kind[j] else e
+            Sv = oracle.surface_pair_apply(P, kind[i], kind[j], gC[i, :2], gC[j, :2], e, r, v)
+            a += Sv * oracle.kernel_dW(2, h, r) * (mass[j] / rho[j]) / rho[i]
+        assert a_s[i, :2] == pytest.approx(a, rel=1e-11, abs=1e-12 * np.abs(a_s).max())
+    plain = oracle.forces(oracle.make_params(2, dx, h, 10.0, 0.8, rho0=rho0, eta=(0.1, 0.1), n=n, tvf_alpha=0.0),
+                          pos, np.zeros((n, 3)), rho, kind)["a_s"]
+    assert not np.allclose(plain, a_s)

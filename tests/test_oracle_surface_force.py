@@ -55,3 +55,33 @@ def test_density_ratio_1000_printed_and_own_weights():
     liq_own, gas_own = radial_fractions(1000, stress_weights=1)
     assert liq_own == pytest.approx(liq, abs=0.005)
     assert 0.4 < gas_own < 0.6
+
+
+def test_own_fluid_correction_recovers_the_csf_force_at_density_ratio_1000():
+    """With the same-phase line's kernel gradient corrected by the own-fluid
+    matrices (surface_corr = 1) the liquid's divergence is no longer
+    truncated at the interface: measured 0.977 of CSF at ratio 1000 (0.964
+    with the penalty), where the printed form gives 0.70; at ratio 1, where
+    the cross-phase line already completes each fluid's sum, it overshoots
+    (0.60 + 0.57)."""
+    def frac(ratio, **kw):
+        case = sphcases.small_droplet(2, 40, R_frac=0.25, rho_l=float(ratio), rho_g=1.0, mu_l=0.05, mu_g=0.05,
+                                      c0=20.0)
+        pos, vel, rho, kind = case.flat()
+        P = oracle.params_for_case(case, surface_corr=1, **kw)
+        a_s = oracle.forces(P, pos, vel, rho, kind)["a_s"]
+        rho0 = np.asarray(case.fluid_props()[0])
+        out = []
+        for k in (0, 1):
+            sel = kind == k
+            r = pos[sel, :2] - 0.5
+            rhat = r / np.linalg.norm(r, axis=1)[:, None]
+            out.append(rho0[k] * case.dx ** 2 * np.sum(a_s[sel, :2] * rhat, axis=1).sum()
+                       / (-2.0 * math.pi * case.gamma))
+        return out
+    liq, gas = frac(1000, xi=0.0)
+    assert liq == pytest.approx(0.977, abs=0.01) and abs(gas) < 0.01
+    liq_p, _ = frac(1000)
+    assert liq_p == pytest.approx(0.964, abs=0.01)
+    l1, g1 = frac(1, xi=0.0)
+    assert l1 + g1 == pytest.approx(1.17, abs=0.02)
