@@ -91,6 +91,13 @@ extern "C" {
  * ratio 1 */
 #define SPHST_STRESS_PRINTED 0
 #define SPHST_STRESS_OWN     1
+/* kernel gradient of the same-phase line of Eq. 33: PRINTED grad_i W_ij;
+ * OWN_FLUID (B^k_i + B^k_j)/2 grad_i W_ij with B^k the correction matrix of
+ * Eq. 15 summed over the particle's own fluid (formed once per advection
+ * step), so that each fluid's stress divergence stays first-order consistent
+ * up to the interface */
+#define SPHST_SURFACE_CORR_PRINTED   0
+#define SPHST_SURFACE_CORR_OWN_FLUID 1
 /* Eq. 8's star velocity: CORRECTED takes the normal component as -U* along
  * e_ij (U = -v.e_ij, Eq. 10) and the tangential part of the pair average;
  * PRINTED is U* e_ij + (vbar - Ubar e_ij) as printed */
@@ -181,6 +188,7 @@ typedef struct {
                                blocks stride over that list.  Speed only:
                                both give the same bits.                      */
     int32_t stress_weights; /* SPHST_STRESS_* (cross-phase surface stress)     */
+    int32_t surface_corr;   /* SPHST_SURFACE_CORR_* (same-phase surface line)  */
 } sphst_case_params;
 
 typedef struct {

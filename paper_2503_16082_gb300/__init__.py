@@ -30,6 +30,7 @@ PENALTY_NN, PENALTY_EE, PENALTY_SCALAR = 0, 1, 2
 PENALTY_SCOPE_BOTH, PENALTY_SCOPE_CROSS_ONLY = 0, 1
 WALL_MIRROR, WALL_NO_SUCTION = 0, 1
 STRESS_PRINTED, STRESS_OWN = 0, 1
+SURFACE_CORR_PRINTED, SURFACE_CORR_OWN_FLUID = 0, 1
 # one engine with neighbour lists holds at most 2^26 particles (a list entry
 # is j << 6 | cell code in 32 bits; sphst_batch_step rejects more)
 MAX_LIST_ENGINE_PARTICLES = 1 << 26
@@ -50,7 +51,7 @@ class CaseParams(C.Structure):
                 ("periodic", C.c_int32), ("vstar_form", C.c_int32),
                 ("period_lo", C.c_double * 3), ("period_hi", C.c_double * 3),
                 ("lanes", C.c_int32), ("penalty_scope", C.c_int32), ("wall_form", C.c_int32),
-                ("work_lists", C.c_int32), ("stress_weights", C.c_int32)]
+                ("work_lists", C.c_int32), ("stress_weights", C.c_int32), ("surface_corr", C.c_int32)]
 
 
 class PhaseProps(C.Structure):

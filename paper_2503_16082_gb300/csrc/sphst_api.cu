@@ -166,6 +166,7 @@ CaseDesc make_desc(const CaseRec *c) {
     d.penalty_scope = c->P.penalty_scope;
     d.wall_form = c->P.wall_form;
     d.stress_weights = c->P.stress_weights;
+    d.surface_corr = c->P.surface_corr;
     d.n_fluid_phases = c->n_fluid_phases;
     d.bits = c->bits;
     for (int a = 0; a < 3; ++a) { d.ncell[a] = c->ncell[a]; d.origin[a] = c->origin[a]; }
@@ -202,7 +203,8 @@ int64_t footprint(const sphst_case_params *P, int64_t n) {
     const int64_t kmax = P->nbr_mode == SPHST_NBR_LIST
                              ? (P->max_neighbors > 0 ? P->max_neighbors : (P->dim == 3 ? 128 : 48)) : 0;
     // V4 arrays, scalars, ints, list (+ its pair geometry), band + band list
-    const int64_t per = 9 * 4 * tsz + 2 * tsz + 6 * 4 + 4 * kmax + (SPHST_LIST_GEO ? 4 * tsz * kmax : 0) + 4 + 1 + 8;
+    const int64_t per = 9 * 4 * tsz + 2 * tsz + 6 * 4 + 4 * kmax + (SPHST_LIST_GEO ? 4 * tsz * kmax : 0) + 4 + 1 + 8 +
+                        (P->surface_corr == 1 ? 2 * 4 * tsz : 0);   // own-fluid correction matrices
     // cell table: cells ~ n / 2.6^d per axis padded to a power of two
     const double side = std::pow((double)std::max<int64_t>(n, 1), 1.0 / P->dim) / 2.6 + 2.0 * P->grid_pad + 2.0;
     int bits = 0;
@@ -300,7 +302,7 @@ int sphst_create_case(const sphst_case_params *params, sphst_case *out) {
         P.penalty_form < 0 || P.penalty_form > 2 || P.loop_mode < 0 || P.loop_mode > 1 ||
         P.vstar_form < 0 || P.vstar_form > 1 || P.penalty_scope < 0 || P.penalty_scope > 1 ||
         P.wall_form < 0 || P.wall_form > 1 || P.work_lists < 0 || P.work_lists > 1 ||
-        P.stress_weights < 0 || P.stress_weights > 1) {
+        P.stress_weights < 0 || P.stress_weights > 1 || P.surface_corr < 0 || P.surface_corr > 1) {
         set_error("unknown reading, loop or work-list flag");
         return SPHST_ERR_INVALID_ARG;
     }

@@ -114,6 +114,7 @@ template <typename T> struct EngineT : Engine {
     // particle arrays
     V4<T> *pos = nullptr, *snap = nullptr, *vel = nullptr, *vel_new = nullptr;
     V4<T> *gradC = nullptr, *acc_visc = nullptr, *acc_surf = nullptr, *bmat = nullptr;
+    V4<T> *bk = nullptr;                             // own-fluid correction matrices (surface_corr)
     T *drho = nullptr, *drho_old = nullptr;        // drho_old: rebuild scratch (sorted copy)
     uint32_t *id = nullptr, *key = nullptr, *rank = nullptr, *perm = nullptr;
     uint32_t *fidx = nullptr, *fscan = nullptr;     // particle of each fluid rank; scan scratch
@@ -150,6 +151,7 @@ template <typename T> struct EngineT : Engine {
     int64_t n_ftiles = 0;
     int ncases = 0, block = 128, lanes = 1;
     bool any_tvf = false;
+    bool any_corr = false;                          // a case takes the own-fluid surface correction
     int loop_mode = SPHST_LOOP_GRAPH;
     std::vector<CaseDesc> h_desc;
     std::vector<CaseState> h_state;
@@ -217,6 +219,7 @@ template <typename T> struct EngineT : Engine {
             n_ftiles += (r->n_fluid + block - 1) / block;
             max_case_n = std::max(max_case_n, r->n);
             any_tvf = any_tvf || d.tvf_on;
+            any_corr = any_corr || d.surface_corr == 1;
             if (d.nbr_mode == 0) {
                 d.nbr_base = nbr_total;
                 nbr_total += (int64_t)d.nbr_k * r->n;
@@ -243,6 +246,7 @@ template <typename T> struct EngineT : Engine {
         size_t o_gc = take(nn * sizeof(V4<T>)), o_av = take(nn * sizeof(V4<T>));
         size_t o_as = take(nn * sizeof(V4<T>));
         size_t o_bm = take(2 * nn * sizeof(V4<T>));
+        size_t o_bk = take(any_corr ? 2 * nn * sizeof(V4<T>) : 0);
         size_t o_dr = take(nn * sizeof(T)), o_dro = take(nn * sizeof(T));
         size_t o_id = take(nn * 4), o_key = take(nn * 4), o_rank = take(nn * 4), o_perm = take(nn * 4);
         size_t o_st = take((size_t)(table_total + 1) * 4), o_bs = take((size_t)nb * 4);
@@ -273,6 +277,7 @@ template <typename T> struct EngineT : Engine {
         vel = (V4<T> *)(b + o_vel); vel_new = (V4<T> *)(b + o_veln);
         gradC = (V4<T> *)(b + o_gc); acc_visc = (V4<T> *)(b + o_av);
         acc_surf = (V4<T> *)(b + o_as); bmat = (V4<T> *)(b + o_bm);
+        bk = any_corr ? (V4<T> *)(b + o_bk) : nullptr;
         drho = (T *)(b + o_dr); drho_old = (T *)(b + o_dro);
         id = (uint32_t *)(b + o_id); key = (uint32_t *)(b + o_key);
         rank = (uint32_t *)(b + o_rank); perm = (uint32_t *)(b + o_perm);
@@ -491,7 +496,7 @@ template <typename T> struct EngineT : Engine {
         if (SPHST_LIST_GEO) SPH_CLASSES(2, k_list_geo, snap, lgeo);
         SPH_CK(cudaMemsetAsync(band_count, 0, 2 * sizeof(uint32_t), stream));
         SPH_CLASSES_F(2, k_band, snap, band, band_list + band_base[k_], band_count + k_);
-        if (any_tvf) SPH_CLASSES_F(4, k_sweep_M, snap, drho, bmat);
+        if (any_tvf || any_corr) SPH_CLASSES_F(4, k_sweep_M, snap, drho, bmat, bk);
         SPH_CLASSES_F(4, k_sweep_V, snap, drho, vel, bmat, acc_visc, pos);
         SPH_CK(cudaGetLastError());
         return SPHST_OK;
@@ -510,8 +515,8 @@ template <typename T> struct EngineT : Engine {
         k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, h, use_handle);
         launch_work_lists();
         launch_colour();
-        SPH_CLASSES_BAND(k_sweep_S, surface_lanes(), band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
-        SPH_CLASSES_LF(4, k_sweep_B, lanes, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo);
+        SPH_CLASSES_BAND(k_sweep_S, surface_lanes(), band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf, bk);
+        SPH_CLASSES_LF(4, k_sweep_B, lanes, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo, bk);
         SPH_CLASSES_LF(4, k_sweep_C, lanes, snap, vel_new, drho, vel, pos, lgeo);
         SPH_CK(cudaGetLastError());
         return SPHST_OK;
@@ -636,8 +641,8 @@ template <typename T> struct EngineT : Engine {
             cudaMemsetAsync(band_count, 0, 2 * sizeof(uint32_t), stream);
             SPH_CLASSES_F(2, k_band, snap, band, band_list + band_base[k_], band_count + k_);
         });
-        timed(1, any_tvf ? 2 * ncls : ncls, [&] {
-            if (any_tvf) SPH_CLASSES_F(4, k_sweep_M, snap, drho, bmat);
+        timed(1, (any_tvf || any_corr) ? 2 * ncls : ncls, [&] {
+            if (any_tvf || any_corr) SPH_CLASSES_F(4, k_sweep_M, snap, drho, bmat, bk);
             SPH_CLASSES_F(4, k_sweep_V, snap, drho, vel, bmat, acc_visc, pos);
         });
         for (;;) {
@@ -647,9 +652,9 @@ template <typename T> struct EngineT : Engine {
             });
             timed(3, ncls, [&] { launch_colour(); });
             timed(6, nlist, [&] {
-                SPH_CLASSES_BAND(k_sweep_S, surface_lanes(), band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf);
+                SPH_CLASSES_BAND(k_sweep_S, surface_lanes(), band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf, bk);
             });
-            timed(4, ncls, [&] { SPH_CLASSES_LF(4, k_sweep_B, lanes, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo); });
+            timed(4, ncls, [&] { SPH_CLASSES_LF(4, k_sweep_B, lanes, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo, bk); });
             timed(5, ncls, [&] { SPH_CLASSES_LF(4, k_sweep_C, lanes, snap, vel_new, drho, vel, pos, lgeo); });
             if (rc) break;
             int flag = 0;

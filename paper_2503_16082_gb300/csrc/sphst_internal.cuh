@@ -102,6 +102,7 @@ struct CaseDesc {
     int32_t penalty_scope;     // 1: the same-phase line of Eq. 33 carries no penalty
     int32_t wall_form;         // 1: wall pairs use max(P*, 0) (no suction)
     int32_t stress_weights;    // 1: cross-phase line 2 phi_i Pi_i + 2 phi_j Pi_j
+    int32_t surface_corr;      // 1: same-phase line with the own-fluid corrected gradient
     int32_t n_fluid_phases;
     int32_t bits;              // Morton bits per axis of the cell table
     int32_t ncell[3];

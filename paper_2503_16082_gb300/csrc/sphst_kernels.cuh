@@ -1127,17 +1127,23 @@ __device__ __forceinline__ void store_B(const Moment<T> &M, int64_t i, V4<T> *bm
 template <bool LIST, typename T, int D>
 __device__ __forceinline__ void sweep_M(const CaseDesc &d, const CasePhys<T> &cp, int64_t i,
                                         const uint32_t *starts, const uint32_t *nbr, const uint32_t *cnt, const V4<T> *snap, const T *drho,
-                                        V4<T> *bmat, int32_t *status) {
+                                        V4<T> *bmat, V4<T> *bk, int32_t *status) {
     const V4<T> si = ld4(snap + i);
     const uint32_t pki = w_bits(si.w);
-    if (phase_of(pki) == PH_WALL) return;
-    Moment<T> M;
+    const uint32_t ki = phase_of(pki);
+    if (ki == PH_WALL) return;
+    const bool own = bk != nullptr && d.surface_corr == 1;
+    Moment<T> M, Mk;
     const bool coinc = neighbors<LIST, T, D>(d, cp, starts, nbr, cnt, snap, i, si, pki,
         [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
-            M.template add<D>(d, cp, drho, j, phase_of(w_bits(sj.w)), rx, ry, rz, r2);
+            const uint32_t kj = phase_of(w_bits(sj.w));
+            M.template add<D>(d, cp, drho, j, kj, rx, ry, rz, r2);
+            // the same sum over i's own fluid (surface_corr reading of Eq. 33)
+            if (own && kj == ki) Mk.template add<D>(d, cp, drho, j, kj, rx, ry, rz, r2);
         });
     if (coinc) atomicCAS(status, 0, DEV_ERR_COINCIDENT);
     store_B<T, D>(M, i, bmat);
+    if (own) store_B<T, D>(Mk, i, bk);
 }
 
 // ---- V: viscous acceleration (Eq. 13) and transport shift (Eq. 14)
@@ -1263,7 +1269,8 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
                                           const uint8_t *band, const V4<T> *snap,
                                           const V4<T> *vel, const V4<T> *gradC,
                                           const V4<T> *acc_visc, V4<T> *acc_surf, V4<T> *vel_new,
-                                          const V4<T> *lgeo, uint32_t *phase_out, uint32_t sub = 0) {
+                                          const V4<T> *lgeo, uint32_t *phase_out, uint32_t sub = 0,
+                                          const V4<T> *bk = nullptr) {
     const V4<T> si = ld4(snap + i);
     const uint32_t pki = w_bits(si.w);
     const uint32_t ki = phase_of(pki);
@@ -1327,6 +1334,11 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
 
     // surface stress and penalty (Eqs. 24, 26, 30, 33); walls take no part
     const V4<T> gi = d.n_fluid_phases == 2 ? gradC[i] : V4<T>{0, 0, 0, 0};
+    // surface_corr reading: the own-fluid correction matrix of i (Eq. 15
+    // over i's fluid), symmetric: (b00, b01, b02, b11), (b12, b22)
+    const bool corr = bk != nullptr && d.surface_corr == 1;
+    V4<T> bi0{T(0), T(0), T(0), T(0)}, bi1{T(0), T(0), T(0), T(0)};
+    if (corr && PASS != 1) { bi0 = bk[2 * i]; bi1 = bk[2 * i + 1]; }
     const auto surface = [&](uint32_t j, const V4<T> &sj, T rx, T ry, T rz, T r2) {
         const uint32_t kj = phase_of(w_bits(sj.w));
         if (kj == PH_WALL) return;
@@ -1344,6 +1356,42 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
         const T inv_gj = if_j ? div_fast(T(1), gj.w) : T(0);
         const T njx = gj.x * inv_gj, njy = gj.y * inv_gj, njz = gj.z * inv_gj;
         const T gam_gj = if_j ? cp.gamma * gj.w : T(0);
+        if (corr && kj == ki) {
+            // same-phase line applied to the corrected kernel gradient
+            // W' (B^k_i + B^k_j)/2 e = W' v (C_ij = 0): S v with
+            // Pi v = gamma |gradC| (v - n (n.v)) and C-hat v of Eq. 30
+            const V4<T> bj0 = bk[2 * j], bj1 = bk[2 * j + 1];
+            const T m00 = T(0.5) * (bi0.x + bj0.x), m01 = T(0.5) * (bi0.y + bj0.y), m11 = T(0.5) * (bi0.w + bj0.w);
+            const T m02 = D == 3 ? T(0.5) * (bi0.z + bj0.z) : T(0), m12 = D == 3 ? T(0.5) * (bi1.x + bj1.x) : T(0);
+            const T m22 = D == 3 ? T(0.5) * (bi1.y + bj1.y) : T(0);
+            const T vx = m00 * ex + m01 * ey + m02 * ez, vy = m01 * ex + m11 * ey + m12 * ez;
+            const T vz = D == 3 ? m02 * ex + m12 * ey + m22 * ez : T(0);
+            const T niv = nix * vx + niy * vy + niz * vz, njv = njx * vx + njy * vy + njz * vz;
+            const T bx = T(0.5) * (gi.x + gj.x), by = T(0.5) * (gi.y + gj.y), bz = T(0.5) * (gi.z + gj.z);
+            const T b2 = bx * bx + by * by + bz * bz;
+            const T inv_bn = b2 > T(0) ? rsqrt_fast(b2) : T(0);
+            T cx, cy, cz;
+            if (d.penalty_form == 0) {            // -|gradCbar| r nbar (nbar.v)
+                const T fac = g.r * (bx * vx + by * vy + bz * vz) * inv_bn;
+                cx = -fac * bx; cy = -fac * by; cz = -fac * bz;
+            } else if (d.penalty_form == 1) {     // -|gradCbar| r e (e.v)
+                const T f = -(b2 * inv_bn * g.r) * (ex * vx + ey * vy + ez * vz);
+                cx = f * ex; cy = f * ey; cz = f * ez;
+            } else {                              // -(gradCbar . r_ij) v
+                const T f = -g.r * (bx * ex + by * ey + bz * ez);
+                cx = f * vx; cy = f * vy; cz = f * vz;
+            }
+            const T nic = nix * cx + niy * cy + niz * cz, njc = njx * cx + njy * cy + njz * cz;
+            const T qx = T(0.5) * (nix * nic + njx * njc), qy = T(0.5) * (niy * nic + njy * njc),
+                    qz = T(0.5) * (niz * nic + njz * njc);
+            const T pen_s = d.penalty_scope == 1 ? T(0) : cp.xi * cp.gamma * g.inv_r;
+            const T sx = gam_gi * (vx - nix * niv) + gam_gj * (vx - njx * njv) + pen_s * (cx - qx);
+            const T sy = gam_gi * (vy - niy * niv) + gam_gj * (vy - njy * njv) + pen_s * (cy - qy);
+            const T sz = gam_gi * (vz - niz * niv) + gam_gj * (vz - njz * njv) + pen_s * (cz - qz);
+            const T w = g.dW * Vj;
+            asx += sx * w; asy += sy * w; if (D == 3) asz += sz * w;
+            return;
+        }
         const T nie = nix * ex + niy * ey + niz * ez;
         const T nje = njx * ex + njy * ey + njz * ez;
         // Pi e = gamma |gradC| (e - n (n.e))   (Eq. 24)
@@ -1712,13 +1760,14 @@ __global__ void __launch_bounds__(256) k_list_geo(SweepArgs a, const V4<T> *snap
 }
 
 template <typename T, int D, bool LIST>
-__global__ void SPH_SWEEP_BOUNDS k_sweep_M(SweepArgs a, const V4<T> *snap, const T *drho, V4<T> *bmat) {
+__global__ void SPH_SWEEP_BOUNDS k_sweep_M(SweepArgs a, const V4<T> *snap, const T *drho, V4<T> *bmat,
+                                           V4<T> *bk) {
     const Tile t = a.tiles[a.tile0 + blockIdx.x];
     if ((int)threadIdx.x >= t.n || !a.st[t.c].active) return;
     const CaseDesc &d = a.desc[t.c];
-    if (!d.tvf_on) return;
+    if (!d.tvf_on && d.surface_corr != 1) return;
     const int64_t i = particle_at(a, t.begin + threadIdx.x);
-    sweep_M<LIST, T, D>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, bmat, &a.st[t.c].status);
+    sweep_M<LIST, T, D>(d, phys<T>(d), i, a.starts, a.nbr, a.cnt, snap, drho, bmat, bk, &a.st[t.c].status);
 }
 
 template <typename T, int D, bool LIST>
@@ -1787,7 +1836,7 @@ __global__ void SPH_SWEEPAS_BOUNDS k_sweep_A_band(SweepArgs a, const uint64_t *b
 template <typename T, int D, bool LIST, int L = 1>
 __global__ void SPH_SWEEPAS_BOUNDS k_sweep_S(SweepArgs a, const uint64_t *blist, const uint32_t *bcount,
                                            const uint8_t *band, const V4<T> *snap, const V4<T> *vel,
-                                           const V4<T> *gradC, V4<T> *acc_surf) {
+                                           const V4<T> *gradC, V4<T> *acc_surf, const V4<T> *bk) {
     const int64_t items = (int64_t)*bcount * L;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < items; t += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t e = blist[t / L];
@@ -1797,14 +1846,14 @@ __global__ void SPH_SWEEPAS_BOUNDS k_sweep_S(SweepArgs a, const uint64_t *blist,
         const CaseDesc &d = a.desc[c];
         uint32_t ph;
         sweep_B<LIST, 2, T, D, L>(d, phys<T>(d), T(0), i, a.starts, a.nbr, a.cnt, band, snap, vel, gradC, nullptr,
-                                  acc_surf, nullptr, nullptr, &ph, threadIdx.x % L);
+                                  acc_surf, nullptr, nullptr, &ph, threadIdx.x % L, bk);
     }
 }
 
 template <typename T, int D, bool LIST, int L = 1, int MODE = MODE_TILES>
 __global__ void SPH_SWEEPB_BOUNDS_M(T, MODE) k_sweep_B(SweepArgs a, const uint8_t *band, const V4<T> *snap, const V4<T> *vel,
                                             const V4<T> *gradC, const V4<T> *acc_visc, V4<T> *acc_surf,
-                                            V4<T> *vel_new, const V4<T> *lgeo) {
+                                            V4<T> *vel_new, const V4<T> *lgeo, const V4<T> *bk) {
     const auto item = [&](int64_t w) {
         const Tile t = work_tile<L, MODE == MODE_WORK>(a, w);
         if (!a.st[t.c].active) return;             // uniform per block
@@ -1816,7 +1865,8 @@ __global__ void SPH_SWEEPB_BOUNDS_M(T, MODE) k_sweep_B(SweepArgs a, const uint8_
             const int64_t i = particle_at(a, t.begin + li);
             const T dt = (T)a.st[t.c].dt;
             v2 = sweep_B<LIST, LIST ? 1 : 0, T, D, L>(d, phys<T>(d), dt, i, a.starts, a.nbr, a.cnt, band, snap, vel,
-                                                      gradC, acc_visc, acc_surf, vel_new, lgeo, &ph, threadIdx.x % L);
+                                                      gradC, acc_visc, acc_surf, vel_new, lgeo, &ph, threadIdx.x % L,
+                                                      LIST ? nullptr : bk);
         }
         unsigned long long m0 = ph == 0 ? (unsigned long long)__double_as_longlong(v2) : 0ull;
         unsigned long long m1 = ph == 1 ? (unsigned long long)__double_as_longlong(v2) : 0ull;

@@ -55,6 +55,8 @@ def launch(args) -> dict:
         kw["wall_form"] = args.wall_form
     if getattr(args, "stress_weights", 0):
         kw["stress_weights"] = args.stress_weights
+    if getattr(args, "surface_corr", 0):
+        kw["surface_corr"] = args.surface_corr
     if getattr(args, "limiter", None) is not None:
         kw["limiter"] = args.limiter
     if args.block:
@@ -246,6 +248,8 @@ def main(argv=None):
                     help="wall pairs: 0 mirror state as it comes, 1 no suction (max(P*, 0))")
     ap.add_argument("--stress-weights", type=int, default=0, choices=[0, 1],
                     help="cross-phase surface stress: 0 2phi_j Pi_i + 2phi_i Pi_j as printed, 1 each by its own phi")
+    ap.add_argument("--surface-corr", type=int, default=0, choices=[0, 1],
+                    help="same-phase surface line: 0 grad W as printed, 1 corrected by the own-fluid matrices of Eq. 15")
     ap.add_argument("--t-end", type=float, default=None, help="impact_3d: 2.0, shear_drop: 20.0")
     args = ap.parse_args(argv)
     if args.t_end is None:

@@ -145,6 +145,8 @@ def test_fp32_one_advection_step(dim):
     (dict(penalty_scope=1), dict(penalty_scope=1)),
     (dict(wall_form=1), dict(wall_form=1)),
     (dict(stress_weights=1), dict(stress_weights=1)),
+    (dict(surface_corr=1), dict(surface_corr=1)),
+    (dict(surface_corr=1, nbr_mode=1), dict(surface_corr=1)),
 ])
 def test_fp64_readings_flags(opts, ora):
     case = small(2)
