@@ -515,7 +515,7 @@ template <typename T> struct EngineT : Engine {
         k_dt<<<1, 256, 0, stream>>>(ncases, d_desc, d_state, d_loop_flag, h, use_handle);
         launch_work_lists();
         launch_colour();
-        SPH_CLASSES_BAND(k_sweep_S, surface_lanes(), band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf, bk);
+        SPH_CLASSES_BAND(k_sweep_S, surface_lanes(), band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf, bk, drho);
         SPH_CLASSES_LF(4, k_sweep_B, lanes, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo, bk);
         SPH_CLASSES_LF(4, k_sweep_C, lanes, snap, vel_new, drho, vel, pos, lgeo);
         SPH_CK(cudaGetLastError());
@@ -652,7 +652,7 @@ template <typename T> struct EngineT : Engine {
             });
             timed(3, ncls, [&] { launch_colour(); });
             timed(6, nlist, [&] {
-                SPH_CLASSES_BAND(k_sweep_S, surface_lanes(), band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf, bk);
+                SPH_CLASSES_BAND(k_sweep_S, surface_lanes(), band_list + band_base[k_], band_count + k_, band, snap, vel, gradC, acc_surf, bk, drho);
             });
             timed(4, ncls, [&] { SPH_CLASSES_LF(4, k_sweep_B, lanes, band, snap, vel, gradC, acc_visc, acc_surf, vel_new, lgeo, bk); });
             timed(5, ncls, [&] { SPH_CLASSES_LF(4, k_sweep_C, lanes, snap, vel_new, drho, vel, pos, lgeo); });

@@ -1270,7 +1270,7 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
                                           const V4<T> *vel, const V4<T> *gradC,
                                           const V4<T> *acc_visc, V4<T> *acc_surf, V4<T> *vel_new,
                                           const V4<T> *lgeo, uint32_t *phase_out, uint32_t sub = 0,
-                                          const V4<T> *bk = nullptr) {
+                                          const V4<T> *bk = nullptr, const T *drho_s = nullptr) {
     const V4<T> si = ld4(snap + i);
     const uint32_t pki = w_bits(si.w);
     const uint32_t ki = phase_of(pki);
@@ -1346,7 +1346,10 @@ __device__ __forceinline__ double sweep_B(const CaseDesc &d, const CasePhys<T> &
         if (gi.w == T(0) && gj.w == T(0)) return;                // every surface term vanishes
         const PairGeo<T> g = geo(cp, r2);
         const T ex = rx * g.inv_r, ey = ry * g.inv_r, ez = D == 3 ? rz * g.inv_r : T(0);
-        const T rho_j = sel(kj, cp.rho0[0], cp.rho0[1]) + vel[j].w;
+        // the density deviation of j: the 4-byte array in the surface sweep
+        // (the same value as vel[j].w, fewer bytes through L1)
+        const T drj_s = PASS == 2 ? drho_s[j] : vel[j].w;
+        const T rho_j = sel(kj, cp.rho0[0], cp.rho0[1]) + drj_s;
         const T Vj = div_fast(sel(kj, cp.mass[0], cp.mass[1]), rho_j);
         const bool if_i = gi.w * cp.h > cp.nhat_eps;
         const T inv_gi = if_i ? div_fast(T(1), gi.w) : T(0);
@@ -1836,7 +1839,7 @@ __global__ void SPH_SWEEPAS_BOUNDS k_sweep_A_band(SweepArgs a, const uint64_t *b
 template <typename T, int D, bool LIST, int L = 1>
 __global__ void SPH_SWEEPAS_BOUNDS k_sweep_S(SweepArgs a, const uint64_t *blist, const uint32_t *bcount,
                                            const uint8_t *band, const V4<T> *snap, const V4<T> *vel,
-                                           const V4<T> *gradC, V4<T> *acc_surf, const V4<T> *bk) {
+                                           const V4<T> *gradC, V4<T> *acc_surf, const V4<T> *bk, const T *drho) {
     const int64_t items = (int64_t)*bcount * L;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < items; t += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t e = blist[t / L];
@@ -1846,7 +1849,7 @@ __global__ void SPH_SWEEPAS_BOUNDS k_sweep_S(SweepArgs a, const uint64_t *blist,
         const CaseDesc &d = a.desc[c];
         uint32_t ph;
         sweep_B<LIST, 2, T, D, L>(d, phys<T>(d), T(0), i, a.starts, a.nbr, a.cnt, band, snap, vel, gradC, nullptr,
-                                  acc_surf, nullptr, nullptr, &ph, threadIdx.x % L, bk);
+                                  acc_surf, nullptr, nullptr, &ph, threadIdx.x % L, bk, drho);
     }
 }
 
