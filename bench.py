@@ -42,15 +42,25 @@ METRIC = "particle-substeps/s"
 
 # ncu summaries record the DRAM traffic of a kernel together with a hash of
 # the kernel sources it was taken on; the bench reports it only while the
-# sources are unchanged
+# sources are unchanged.  The hash covers the code, not the comments: line
+# comments are dropped and each line's whitespace is normalised first.
 KERNEL_SOURCES = ("paper_2503_16082_gb300/csrc/sphst_kernels.cuh", "paper_2503_16082_gb300/csrc/sphst_internal.cuh")
+
+
+def _code_of(text: str) -> str:
+    lines = []
+    for line in text.splitlines():
+        code = re.sub(r"//.*", "", line).strip()
+        if code:
+            lines.append(" ".join(code.split()))
+    return "\n".join(lines)
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            h.update(_code_of(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

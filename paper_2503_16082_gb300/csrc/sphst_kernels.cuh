@@ -7,19 +7,25 @@
 // frozen configuration and the interface band.
 //
 // Pair sweeps (gather-only: every particle's sum is owned by one thread, or by
-// a group of 2-4 lanes that split its list and add their parts in a fixed
+// a group of 2-8 lanes that split its list and add their parts in a fixed
 // order, so there are no atomics on particle data):
-//   M  correction matrix B_i (Eq. 15)                     once per advection step
+//   M  correction matrix B_i (Eq. 15; also over the own fluid for the
+//      surface_corr reading)                             once per advection step
 //   V  viscous acceleration (Eq. 13) + transport shift (Eq. 14)  once per advection step
-//   A  colour gradient (Eq. 22)                           every acoustic substep
+//   A  colour gradient (Eq. 22); with the list over the interface band only
+//                                                         every acoustic substep
 //   S  surface stress + penalty (Eqs. 24, 26, 30, 33) of the interface band
 //                                                         every substep (list cases)
 //   B  pressure (Eqs. 7-12) (+ the surface terms with the cell walk) + kick
 //                                                         every substep
 //   C  continuity (Eq. 6) + drift                         every substep
-// The list build, the band and M, V, A, B, C run over the fluid particles
-// only (their ranks after each reorder).  Time-step control (Eqs. 16-18)
-// runs in FP64 in one-thread-per-case kernels.
+// The list build, the band and M, V, B, C (and A with the cell walk) run
+// over the fluid particles only (their ranks after each reorder); A and S of
+// the list classes stride over the band list.  Time-step control (Eqs.
+// 16-18) runs in FP64 in one-thread-per-case kernels.  A one-case engine
+// launches A, B and C with the case's constants in the launch parameters
+// (MODE_ONE); their sums are explicitly rounded, so the results do not depend
+// on that choice.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -934,8 +940,8 @@ __global__ void k_copy_back(int64_t n, const V4<T> *pos_t, const V4<T> *vel_t, c
 
 // ---- fluid ranks: after the reorder, the sorted positions of the fluid
 // particles, walls left out (an exclusive scan of the fluid flags, then a
-// scatter).  The list build, the band and sweeps M, V, A, B and C run their
-// tiles over these ranks, so no lane of theirs idles on a wall particle (16%
+// scatter).  The list build, the band and sweeps M, V, B and C (and A with
+// the cell walk) run their tiles over these ranks, so no lane of theirs idles on a wall particle (16%
 // of the 3D drop, interleaved with the fluid near the walls by the Morton
 // order).  Each case's fluid particles take the ranks after the previous
 // cases' ones, whose count is fixed.
@@ -1624,7 +1630,7 @@ template <int L, bool WORK> __device__ __forceinline__ Tile work_tile(const Swee
 }
 
 // particle of tile position q: the position itself, or the fluid particle of
-// that rank (the list build, the band, sweeps M, V, A, B and C)
+// that rank (the list build, the band, sweeps M, V, B and C, A with the cell walk)
 __device__ __forceinline__ int64_t particle_at(const SweepArgs &a, int64_t q) {
     return a.fidx ? (int64_t)a.fidx[q] : q;
 }
@@ -1795,11 +1801,12 @@ __global__ void SPH_SWEEP_BOUNDS k_sweep_V(SweepArgs a, const V4<T> *snap, const
                         &a.st[t.c].status);
 }
 
-// Sweeps A, B and C take L lanes per particle (L = 1, 2, 4, 8; list classes):
-// L blocks share one tile, block b takes its part b % L of blockDim / L
-// particles, and lane threadIdx % L of a particle's group walks every L-th
-// list entry.  local_index gives the particle's index within its tile.
-// Sweep S does the same per entry of its band list.
+// Sweeps B and C (and A with the cell walk) take L lanes per particle (L = 1,
+// 2, 4, 8; list classes): L blocks share one tile, block b takes its part
+// b % L of blockDim / L particles, and lane threadIdx % L of a particle's
+// group walks every L-th list entry.  local_index gives the particle's index
+// within its tile.  Sweeps S and A of the list classes do the same per entry
+// of their band list.
 template <int L> __device__ __forceinline__ int local_index(int64_t w) {
     return L == 1 ? (int)threadIdx.x : (int)((w % L) * (blockDim.x / L) + threadIdx.x / L);
 }
