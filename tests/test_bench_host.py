@@ -23,9 +23,12 @@ def test_recorded_counters_follow_the_source_hash(tmp_path, monkeypatch):
     assert bench.recorded_traffic("s.md", "k_sweep_B", "warp_instructions_per_launch") == 99
     assert bench.recorded_traffic("s.md", "k_sweep_C") is None
     assert bench.recorded_traffic("missing.md", "k_sweep_B") is None
-    # a changed kernel source invalidates every recorded counter
+    # a comment does not change the code the counters were taken on; a
+    # changed line of code invalidates every recorded counter
     src = tmp_path / bench.KERNEL_SOURCES[0]
-    src.write_bytes(src.read_bytes() + b"\n// changed\n")
+    src.write_bytes(src.read_bytes() + b"\n// a comment\n")
+    assert bench.kernel_source_hash() == h
+    src.write_bytes(src.read_bytes() + b"\nconstexpr int kChanged = 1;\n")
     assert bench.kernel_source_hash() != h
     assert bench.recorded_traffic("s.md", "k_sweep_B") is None
 
