@@ -103,6 +103,15 @@ def device_roofs():
             "issue_per_s": sm * ISSUE_PER_SM * ghz * 1e9}
 
 
+# Launch shape of a workload's line where it differs from the library's
+# default of 128 threads per block (speed only: with one lane per particle
+# no particle's sums depend on the block size, and the results are the same
+# bit for bit).  The 3D drop in FP32 with the list: 256 threads 1.547e9
+# particle-substeps/s against 1.516e9 with 128 (sweep C 0.244 against
+# 0.255 ms per launch, B the same), 160: 1.532e9, 192: 1.517e9.
+TUNED_BLOCK = {("oscillating_3d", 32, "list"): 256}
+
+
 def workload(name: str):
     if name == "oscillating_3d":
         return sphcases.oscillating_3d()
@@ -723,6 +732,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if not args.block and not args.lanes:
+        args.block = TUNED_BLOCK.get((args.workload, args.precision, args.nbr), 0)
     if args.mode == "batch":
         return run_batch(args)
     if args.mode == "serve":

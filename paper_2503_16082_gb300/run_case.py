@@ -39,11 +39,13 @@ def main(argv=None):
                     help="host: launch every kernel on its own (profilers cannot see "
                          "kernels inside a graph with a conditional node)")
     ap.add_argument("--nbr", default="list", choices=["list", "cells"])
+    ap.add_argument("--block", type=int, default=0, help="threads per block (0: library default)")
     args = ap.parse_args(argv)
     spec = WORKLOADS[args.workload]() if args.dx is None else WORKLOADS[args.workload](dx=args.dx)
     h = S.case_from_spec(spec, precision=args.precision,
                          loop_mode=S.LOOP_HOST if args.loop == "host" else S.LOOP_GRAPH,
-                         nbr_mode=S.NBR_CELLS if args.nbr == "cells" else S.NBR_LIST)
+                         nbr_mode=S.NBR_CELLS if args.nbr == "cells" else S.NBR_LIST,
+                         **({"block": args.block} if args.block else {}))
     t0 = time.perf_counter()
     info = S.step(h, args.adv, check=False)
     wall = time.perf_counter() - t0

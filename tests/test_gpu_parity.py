@@ -337,3 +337,22 @@ def test_neighbor_overflow_is_reported():
     info = S.step(h, 1, check=False)
     assert info["rc"] == S.ERR_NEIGHBORS
     S.destroy(h)
+
+
+@pytest.mark.parametrize("block", [64, 160, 256])
+def test_block_size_changes_no_bit(block):
+    # one lane per particle: no particle's sums depend on the tile size, so
+    # the timed line's 256-thread blocks (and any other size) give the
+    # default 128's fields bit for bit, in the one-case mode (3D, FP32)
+    case = small(3, n_side=14)
+    out = {}
+    for b in (128, block):
+        h = gpu_case(case, 32, block=b)
+        S.step(h, 2)
+        out[b] = [S.read_fields(h, f, 3) for f in (S.FIELD_POS, S.FIELD_VEL, S.FIELD_RHO, S.FIELD_GRADC)], \
+            S.case_info(h)
+        S.destroy(h)
+    (fa, ia), (fb, ib) = out[128], out[block]
+    assert ia["n_sub"] == ib["n_sub"] and ia["t"] == ib["t"]
+    for a, b in zip(fa, fb):
+        assert np.array_equal(a, b)
