@@ -110,6 +110,11 @@ def device_roofs():
 # particle-substeps/s against 1.516e9 with 128 (sweep C 0.244 against
 # 0.255 ms per launch, B the same), 160: 1.532e9, 192: 1.517e9.
 TUNED_BLOCK = {("oscillating_3d", 32, "list"): 256}
+# the same for the batched workload (one engine of 512 cases): 256 threads
+# 1.513-1.515e9 against 1.497-1.500e9 with 128, the work-list variant
+# 1.443e9 against 1.394e9; its cases stepped one by one stay at the
+# library's default (676 against 666 M particle-substeps/s at 256)
+BATCH_BLOCK = 256
 
 
 def workload(name: str):
@@ -511,7 +516,7 @@ def run_reference(args, dist: Dist):
 
 # ------------------------------------------------------ batched and served
 def batch_measure(precision: int = 32, n_cases: int = 512, steps: int = 20, warmup: int = 3,
-                  plain_sample: int = 32, cpu: bool = True, cpu_cases: int = 16):
+                  plain_sample: int = 32, cpu: bool = True, cpu_cases: int = 16, block: int = BATCH_BLOCK):
     """The batched workload: independent 2D/3D droplet cases advanced
     together in one engine (one graph per advection step), against the same
     cases stepped one at a time through the single-case path.  Each case's
@@ -528,10 +533,11 @@ def batch_measure(precision: int = 32, n_cases: int = 512, steps: int = 20, warm
     # coarse 3D drops with strong tension cluster beyond the default list
     # capacity of 128 neighbours; the batch uses 192
     kw = [dict(max_neighbors=192 if c.dim == 3 else 0) for c in cases]
-    state_bytes = sum(S.footprint_bytes(S.params_from_spec(c, precision, **k), c.n) for c, k in zip(cases, kw))
+    kw_batch = [dict(k, **({"block": block} if block else {})) for k in kw]
+    state_bytes = sum(S.footprint_bytes(S.params_from_spec(c, precision, **k), c.n) for c, k in zip(cases, kw_batch))
 
     def run(work_lists: int):
-        hs = [S.case_from_spec(c, precision=precision, work_lists=work_lists, **k) for c, k in zip(cases, kw)]
+        hs = [S.case_from_spec(c, precision=precision, work_lists=work_lists, **k) for c, k in zip(cases, kw_batch)]
         b = S.batch_create(precision)
         for h in hs:
             S.batch_add(b, h)
@@ -611,12 +617,13 @@ def batch_measure(precision: int = 32, n_cases: int = 512, steps: int = 20, warm
             "cpu_baseline": cpu_line, "timing": "host clock around synchronising step calls",
             "dtype": "f32" if precision == 32 else "f64", "data": "synthetic",
             "config": {"workload": f"batch_cases seed {sphcases.BATCH_SEED}", "step": "one advection step of every case",
+                       "block": block or 128, "plain_block": 128,
                        "l2": f"inputs larger than L2 ({state_bytes / 1e9:.1f} GB of case state vs 129 MB L2)"}}
 
 
 def run_batch(args):
     line = batch_measure(args.precision, args.cases, args.steps, args.warmup, args.plain_sample,
-                         cpu=not args.no_cpu_baseline)
+                         cpu=not args.no_cpu_baseline, block=args.block or BATCH_BLOCK)
     line["mode"] = "batch"
     print(json.dumps(line), flush=True)
 
