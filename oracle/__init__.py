@@ -8,12 +8,14 @@ this module only builds it with gcc and marshals numpy arrays through ctypes.
 ``SPH_ORACLE_LIB`` may name a separately built library of the same source;
 the pin-strength test uses it to load copies with planted mistakes.
 
-Parity unpinned (see the header of ``sph_oracle.c``): the same-phase penalty
-term away from special cases is fixed only by agreement with the CUDA path
-and the integral observables; the integrator and the wall's mirror pressure
-and volume are pinned by acoustic modes, v* = v_w at a wall by the water
-hammer, the wall's dissipative term by a fluid particle beside one wall
-particle, the cross-phase penalty by an isolated pair.
+Pins (see the header of ``sph_oracle.c``): every term of Eq. 33 for a
+single pair, the cross-phase line by an isolated pair of different fluids and
+the same-phase line by three pairs that reduce by hand (``ora_surface_pair``,
+the routine the force loop calls); the integrator and the wall's mirror
+pressure and volume by acoustic modes, v* = v_w at a wall by the water hammer,
+the wall's dissipative term by a fluid particle beside one wall particle.  No
+single term is unpinned; the scheme as a whole over many substeps is checked
+through its integral observables (Laplace jump, oscillation periods).
 """
 from __future__ import annotations
 
