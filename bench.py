@@ -417,10 +417,12 @@ def run_ours(args, dist: Dist):
 # ------------------------------------------------------ CPU oracle sample
 SAMPLE_SUBSTEPS = 4
 # acoustic substeps per advection step of each workload, as the GPU measures
-# them over the bench's timed steps (the default 20 after 5 warm-up steps):
-# the reference arm rates the oracle at this many substeps per advection
-# step, since it cannot afford whole advection steps of the full case
-SUBSTEPS_PER_STEP = {"oscillating_3d": 37.75, "laplace_2d": 25.2, "impact_3d": 3.0}
+# them over the bench's timed steps (the 3D drop: the default 20 after the
+# default 3 warm-up steps; the 2D static drop: 20 after 5; the impact: 5
+# after 3): the reference arm rates the oracle at this many substeps per
+# advection step, since it cannot afford whole advection steps of the full
+# case
+SUBSTEPS_PER_STEP = {"oscillating_3d": 36.25, "laplace_2d": 31.45, "impact_3d": 3.0}
 
 
 _ALL_THREADS = []
