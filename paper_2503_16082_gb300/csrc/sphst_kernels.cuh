@@ -45,38 +45,24 @@
 //                      64-register room the compiler keeps more loads in
 //                      flight; measured: A 35 -> 28 us, S 93 -> 89 us on the
 //                      3D drop)
-//   SPHST_LIST_UNROLL  unroll factor of the neighbour-list loop
 //   SPHST_LIST_PREFETCH 1: load list entry k+1 while pair k is evaluated;
 //                      2: entries k+1 and k+2 (measured: a general ring of
 //                      2-4 entries compiles to slower sweeps)
 //   SPHST_FAST_DIV     1: FP32 pair divisions through the SFU reciprocal
 //   SPHST_F32X2        1: x/y components of the FP32 pair geometry and sums in
 //                      packed two-lane instructions (sm_100 and later)
-//   SPHST_L2_HINTS     1: list words evict-first in L2 (and not kept in L1),
-//                      gathered neighbour data evict-last (measured: sweep B
-//                      unchanged, sweep C 40% slower; off)
-//   SPHST_PIPE         1: sweeps B and C load the next neighbour's position and
-//                      state while the current pair is evaluated
 //   SPHST_LIST_NOALLOC 1: the list words are read without allocating L1 lines
 //                      (measured +1% on the 3D drop)
 //   SPHST_LIST_SORTED  1: the neighbour list holds each part in increasing j
 //                      (cells by table index); 0: in the cell walk's order
-//   SPHST_GEO_L2PF     >0: with SPHST_LIST_GEO, L2 prefetch of the stored
-//                      geometry that many entries ahead
 #ifndef SPHST_LIST_PREFETCH
 #define SPHST_LIST_PREFETCH 2
 #endif
 #ifndef SPHST_FAST_DIV
 #define SPHST_FAST_DIV 1
 #endif
-#ifndef SPHST_PIPE
-#define SPHST_PIPE 0
-#endif
 #ifndef SPHST_F32X2
 #define SPHST_F32X2 1
-#endif
-#ifndef SPHST_L2_HINTS
-#define SPHST_L2_HINTS 0
 #endif
 #ifndef SPHST_LIST_LDCS
 #define SPHST_LIST_LDCS 1
@@ -89,12 +75,6 @@
 #endif
 #ifndef SPHST_SWEEPAS_MINB
 #define SPHST_SWEEPAS_MINB 4
-#endif
-#ifndef SPHST_GEO_L2PF
-#define SPHST_GEO_L2PF 0
-#endif
-#ifndef SPHST_LIST_UNROLL
-#define SPHST_LIST_UNROLL 1
 #endif
 #ifndef SPHST_SWEEPB_MINB
 #define SPHST_SWEEPB_MINB 4
@@ -138,8 +118,6 @@
                                                          : (SPHST_SWEEPB_MINB > 0 ? SPHST_SWEEPB_MINB : 1))
 
 namespace sphst {
-
-constexpr int kListUnroll = SPHST_LIST_UNROLL;
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
@@ -232,45 +210,17 @@ __device__ __forceinline__ L2<double> neg_code_off2(uint32_t bx, uint32_t by, do
 // a ? x1 : x0 for the two fluid phases' constants (no indexed loads)
 template <typename T> __device__ __forceinline__ T sel(uint32_t k, T x0, T x1) { return k ? x1 : x0; }
 
-// L2 eviction priorities for the list walks (per-load cache policies, no
-// device setting involved): the neighbour list is streamed once per sweep
-// and marked evict-first, the particle data it points to is gathered ~80
-// times and marked evict-last, so the stream does not push it out of L2.
-struct L2Pol { uint64_t stream, keep; };
-__device__ __forceinline__ L2Pol l2_policies() {
-    L2Pol p{0, 0};
-#if SPHST_L2_HINTS
-    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p.stream));
-    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p.keep));
-#endif
-    return p;
-}
-__device__ __forceinline__ uint32_t ld_list(const uint32_t *p, const L2Pol &pol) {
-#if SPHST_L2_HINTS
-    uint32_t v;
-    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol.stream));
-    return v;
-#elif SPHST_LIST_NOALLOC
-    // the streamed list words do not take L1 lines from the gathered data
-    (void)pol;
+// A list word of the per-substep walks.  The list is streamed once per sweep
+// while the neighbour records it points to are gathered ~80 times; its words
+// are read without allocating L1 lines (SPHST_LIST_NOALLOC), so they take none
+// from the gathered data (else as evict-first loads).
+__device__ __forceinline__ uint32_t ld_list_walk(const uint32_t *p) {
+#if SPHST_LIST_NOALLOC
     uint32_t v;
     asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
 #else
-    (void)pol;
     return __ldcs(p);
-#endif
-}
-template <typename T> __device__ __forceinline__ V4<T> ld4_keep(const V4<T> *p, const L2Pol &) { return ld4(p); }
-template <> __device__ __forceinline__ V4<float> ld4_keep<float>(const V4<float> *p, const L2Pol &pol) {
-#if SPHST_L2_HINTS
-    V4<float> v;
-    asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(pol.keep));
-    return v;
-#else
-    (void)pol;
-    return ld4(p);
 #endif
 }
 
@@ -470,31 +420,30 @@ __device__ __forceinline__ void walk_list(const CaseDesc &d, const CasePhys<T> &
     const uint32_t *p = nbr + d.nbr_base + (i - d.p_begin) + (int64_t)sub * stride;
     const uint32_t c = PART == PART_OTHER ? cnt[i] >> 16 : cnt[i] & CNT_MASK;
     const T cs = cp.cs;
-    const L2Pol pol = l2_policies();
 #if SPHST_LIST_PREFETCH >= 2
-    uint32_t next = sub < c ? ld_list(p, pol) : 0u;
-    uint32_t next2 = sub + L < c ? ld_list(p + L * stride, pol) : 0u;
+    uint32_t next = sub < c ? ld_list_walk(p) : 0u;
+    uint32_t next2 = sub + L < c ? ld_list_walk(p + L * stride) : 0u;
     p += L * stride;
 #elif SPHST_LIST_PREFETCH
-    uint32_t next = sub < c ? ld_list(p, pol) : 0u;
+    uint32_t next = sub < c ? ld_list_walk(p) : 0u;
 #endif
-#pragma unroll kListUnroll
+#pragma unroll 1
     for (uint32_t k = sub; k < c; k += L) {
 #if SPHST_LIST_PREFETCH >= 2
         const uint32_t e = next;            // entries k + L and k + 2L in flight
         next = next2;
         p += L * stride;
-        if (k + 2 * L < c) next2 = ld_list(p, pol);
+        if (k + 2 * L < c) next2 = ld_list_walk(p);
 #elif SPHST_LIST_PREFETCH
         const uint32_t e = next;
         p += L * stride;
-        if (k + L < c) next = ld_list(p, pol);
+        if (k + L < c) next = ld_list_walk(p);
 #else
-        const uint32_t e = ld_list(p, pol);
+        const uint32_t e = ld_list_walk(p);
         p += L * stride;
 #endif
         const uint32_t j = e >> NBR_SHIFT;
-        const V4<T> sj = ld4_keep(snap + j, pol);
+        const V4<T> sj = ld4(snap + j);
         // s_i - o cs with o in {-1, 0, 1}: o cs is exact, so the FMA rounds
         // once, exactly like the cell walk's subtraction
         const T rx = sub_rn(fma_rn(-code_off(e & 3u, T()), cs, si.x), sj.x);
@@ -507,8 +456,6 @@ __device__ __forceinline__ void walk_list(const CaseDesc &d, const CasePhys<T> &
 }
 
 // The list walk with one more per-neighbour array: f(j, s_j, aux_j, r_ij, r^2).
-// With SPHST_PIPE the entry two ahead and the position and aux word of the
-// next neighbour are in flight while the current pair is evaluated.
 template <typename T, int D, int L = 1, typename F>
 __device__ __forceinline__ void walk_list_aux(const CaseDesc &d, const CasePhys<T> &cp,
                                               const uint32_t *__restrict__ nbr,
@@ -520,7 +467,6 @@ __device__ __forceinline__ void walk_list_aux(const CaseDesc &d, const CasePhys<
     const uint32_t *p = nbr + d.nbr_base + (i - d.p_begin) + (int64_t)sub * stride;
     const uint32_t c = cnt[i] & CNT_MASK;
     const T cs = cp.cs;
-    const L2Pol pol = l2_policies();
     const auto pair = [&](uint32_t e, const V4<T> &sj, const V4<T> &aj) {
         // (s_i - o cs) - s_j per axis, each step rounded once as in the cell walk
         const L2<T> t = fma2(neg_code_off2(e & 3u, (e >> 2) & 3u, T()), l2(cs, cs), l2(si.x, si.y));
@@ -530,54 +476,30 @@ __device__ __forceinline__ void walk_list_aux(const CaseDesc &d, const CasePhys<
         if (D == 3) rz = sub_rn(fma_rn(-code_off((e >> 4) & 3u, T()), cs, si.z), sj.z);
         f(e >> NBR_SHIFT, sj, aj, rx, ry, rz, norm2<T, D>(rx, ry, rz));
     };
-#if SPHST_PIPE
-    if constexpr (L == 1) {               // the two-deep pipeline walks one list per thread
-    if (c == 0) return;
-    uint32_t e = ld_list(p, pol);
-    p += stride;
-    uint32_t e_next = c > 1 ? ld_list(p, pol) : 0u;
-    p += stride;
-    V4<T> sj = ld4_keep(snap + (e >> NBR_SHIFT), pol), aj = ld4_keep(aux + (e >> NBR_SHIFT), pol);
-#pragma unroll 1
-    for (uint32_t k = 0; k < c; ++k) {
-        const uint32_t ec = e;
-        const V4<T> sc = sj, ac = aj;
-        if (k + 1 < c) {
-            e = e_next;
-            sj = ld4_keep(snap + (e >> NBR_SHIFT), pol);
-            aj = ld4_keep(aux + (e >> NBR_SHIFT), pol);
-            if (k + 2 < c) e_next = ld_list(p, pol);
-            p += stride;
-        }
-        pair(ec, sc, ac);
-    }
-    return;
-    }
-#endif
 #if SPHST_LIST_PREFETCH >= 2
-    uint32_t next = sub < c ? ld_list(p, pol) : 0u;
-    uint32_t next2 = sub + L < c ? ld_list(p + L * stride, pol) : 0u;
+    uint32_t next = sub < c ? ld_list_walk(p) : 0u;
+    uint32_t next2 = sub + L < c ? ld_list_walk(p + L * stride) : 0u;
     p += L * stride;
 #elif SPHST_LIST_PREFETCH
-    uint32_t next = sub < c ? ld_list(p, pol) : 0u;
+    uint32_t next = sub < c ? ld_list_walk(p) : 0u;
 #endif
-#pragma unroll kListUnroll
+#pragma unroll 1
     for (uint32_t k = sub; k < c; k += L) {
 #if SPHST_LIST_PREFETCH >= 2
         const uint32_t e = next;            // entries k + L and k + 2L in flight
         next = next2;
         p += L * stride;
-        if (k + 2 * L < c) next2 = ld_list(p, pol);
+        if (k + 2 * L < c) next2 = ld_list_walk(p);
 #elif SPHST_LIST_PREFETCH
         const uint32_t e = next;
         p += L * stride;
-        if (k + L < c) next = ld_list(p, pol);
+        if (k + L < c) next = ld_list_walk(p);
 #else
-        const uint32_t e = ld_list(p, pol);
+        const uint32_t e = ld_list_walk(p);
         p += L * stride;
 #endif
         const uint32_t j = e >> NBR_SHIFT;
-        pair(e, ld4_keep(snap + j, pol), ld4_keep(aux + j, pol));
+        pair(e, ld4(snap + j), ld4(aux + j));
     }
 }
 
@@ -650,7 +572,7 @@ __device__ __forceinline__ void walk_geo(const CaseDesc &d, const uint32_t *__re
     uint32_t next = c ? ld_list(p) : 0u;
 #endif
     V4<T> g1 = c ? ld_geo(q) : V4<T>{};
-#pragma unroll kListUnroll
+#pragma unroll 1
     for (uint32_t k = 0; k < c; ++k) {
 #if SPHST_LIST_PREFETCH
         const uint32_t e = next;
@@ -659,9 +581,6 @@ __device__ __forceinline__ void walk_geo(const CaseDesc &d, const uint32_t *__re
 #else
         const uint32_t e = ld_list(p);
         p += stride;
-#endif
-#if SPHST_GEO_L2PF > 0
-        if (k + SPHST_GEO_L2PF < c) asm volatile("prefetch.global.L2 [%0];" ::"l"(q + SPHST_GEO_L2PF * stride));
 #endif
         const V4<T> G = g1;                       // geometry one entry ahead
         if (k + 1 < c) g1 = ld_geo(q + stride);
