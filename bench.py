@@ -88,6 +88,22 @@ FP64_PEAK_TFLOPS = 1.25      # nominal FP64 (non-tensor) rate of a GB300
 FLOPS_PAIR_B = 59            # geometry + Riemann pressure, every pair (sweep B)
 FLOPS_PAIR_B_SURF = 110      # surface stress + penalty, pairs touching the interface (sweep S)
 L2_BYTES = 129 * 10**6       # L2 of a GB300; a case smaller than twice this is flushed between timed steps
+HBM_FALLBACK_GBS = 6800.0    # one earlier copy-bandwidth measurement on a GB300, used without a measured one
+
+
+def hbm_roof(traffic_bytes: int, launch_s: float, root: str | None = None) -> dict:
+    """A kernel's DRAM bytes per launch (ncu) over its live launch time,
+    against the HBM copy bandwidth measured on this machine's GPUs (the driver's
+    MEASURED_PEAKS.json beside this file), else a fallback figure."""
+    path = os.path.join(root or ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            peak, src = float(json.load(f)["hbm_gbs"]), "measured copy bandwidth (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, TypeError, ValueError):
+        peak, src = HBM_FALLBACK_GBS, "fallback: an earlier GB300 copy measurement"
+    gbs = traffic_bytes / launch_s / 1e9
+    return {"achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+            "peak_source": src}
 
 
 def device_roofs():
@@ -351,6 +367,11 @@ def run_ours(args, dist: Dist):
                 "device": {k: roofs[k] for k in ("sm_count", "max_sm_clock_mhz", "cc")},
                 "flops_per_launch": flops, "pairs": pairs, "pairs_surface": pairs_surf,
                 "avg_launch_ms": round(b_avg * 1e3, 4)}
+    # the HBM roof beside the ALU one: the recorded DRAM bytes of one launch
+    # over its live duration (the list sweeps reuse their neighbours' records
+    # from L1 and L2, so HBM is not what holds them)
+    if roofline["traffic"]:
+        roofline["hbm"] = hbm_roof(roofline["traffic"], b_avg)
     # the issue roof beside the ALU one: warp instructions of one launch (ncu,
     # recorded with the traffic) over its live duration, against one warp
     # instruction per scheduler per cycle (SMs x 4 x peak SM clock)

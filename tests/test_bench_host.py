@@ -40,3 +40,13 @@ def test_committed_profile_matches_the_sources():
     assert bench.recorded_traffic("sweeps_oscillating_3d_f32_list.md", "k_sweep_B",
                                   "warp_instructions_per_launch") > 0
 
+
+
+def test_hbm_roof_reads_the_measured_peak_else_the_fallback(tmp_path):
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6000.0}')
+    r = bench.hbm_roof(3 * 10**8, 1e-4, root=str(tmp_path))           # 300 MB in 0.1 ms = 3000 GB/s
+    assert r["achieved"] == 3000.0 and r["peak"] == 6000.0 and r["frac"] == 0.5
+    assert r["peak_source"].startswith("measured")
+    (tmp_path / "MEASURED_PEAKS.json").write_text("{}")
+    r = bench.hbm_roof(3 * 10**8, 1e-4, root=str(tmp_path))
+    assert r["peak"] == bench.HBM_FALLBACK_GBS and r["peak_source"].startswith("fallback")
