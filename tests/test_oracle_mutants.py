@@ -13,8 +13,9 @@ pressure dropped, the wall volume doubled, v* = v_i instead of the wall's
 velocity in the continuity equation, the wall's normal velocity not
 mirrored in the Riemann state, the cross-phase penalty weight
 4 phi_i phi_j halved (Eq. 33), the same-phase penalty of Eq. 33 halved or
-dropped, its projection T-bar replaced by N-bar, and the contraction of
-Eq. 30 transposed (A^T A for A A^T).  An unmodified copy passes the same
+dropped, its projection T-bar replaced by N-bar, the contraction of
+Eq. 30 transposed (A^T A for A A^T), and the surface stress of Eq. 24 made
+20% weak.  An unmodified copy passes the same
 harness."""
 import os
 import subprocess
@@ -68,6 +69,8 @@ MUTANTS = {
     "wall v* = v_i in continuity": ("                    for (int d = 0; d < dim; ++d) vs[d] = vj[d];",
                                     "                    for (int d = 0; d < dim; ++d) vs[d] = vi[d];"),
     "wall velocity not mirrored": ("R.U = 2.0 * Uw - L.U;", "R.U = Uw;"),
+    "surface stress 20% weak": ("st->Pi[3 * a + b] = iface ? P->gamma * (I - nn) * gn : 0.0;",
+                                "st->Pi[3 * a + b] = iface ? 0.8 * P->gamma * (I - nn) * gn : 0.0;"),
     "wall volume doubled": ("return P->dim == 2 ? P->dx * P->dx : P->dx * P->dx * P->dx;",
                             "return P->dim == 2 ? 2.0 * P->dx * P->dx : 2.0 * P->dx * P->dx * P->dx;"),
 }
