@@ -93,8 +93,8 @@ HBM_FALLBACK_GBS = 6800.0    # one earlier copy-bandwidth measurement on a GB300
 
 def hbm_roof(traffic_bytes: int, launch_s: float, root: str | None = None) -> dict:
     """A kernel's DRAM bytes per launch (ncu) over its live launch time,
-    against the HBM copy bandwidth measured on this machine's GPUs (the driver's
-    MEASURED_PEAKS.json beside this file), else a fallback figure."""
+    against the measured HBM copy bandwidth of this GPU model
+    (MEASURED_PEAKS.json beside this file), else a fallback figure."""
     path = os.path.join(root or ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
