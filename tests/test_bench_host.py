@@ -50,3 +50,20 @@ def test_hbm_roof_reads_the_measured_peak_else_the_fallback(tmp_path):
     (tmp_path / "MEASURED_PEAKS.json").write_text("{}")
     r = bench.hbm_roof(3 * 10**8, 1e-4, root=str(tmp_path))
     assert r["peak"] == bench.HBM_FALLBACK_GBS and r["peak_source"].startswith("fallback")
+
+
+def test_reference_arm_prints_its_line_on_the_host():
+    # the reference arm times the oracle on the host cores only; on the 2D
+    # static drop (7.4k particles) one timed step takes a few seconds
+    import json
+    import subprocess
+    import sys
+    here = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "laplace_2d",
+                        "--steps", "1", "--warmup", "3"], cwd=here, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["config"]["workload"] == "laplace_2d" and line["higher_is_better"] is True
